@@ -1,0 +1,168 @@
+/*
+ * dvm.h -- C ABI of libdvm, the GB300 (sm_103a) implementation of the fast
+ * kinetic schemes FKS and HOFKS for the discrete-velocity BGK equation of
+ * Dimarco & Loubere, "Towards an ultra efficient kinetic scheme, Part II: the
+ * high order case" (arXiv:1212.0204).
+ *
+ * Model (Sections 2-3): f(x, v, t) on a uniform Cartesian cell grid in d = 1..3
+ * space dimensions and a tensor grid of N_v discrete velocities v_k = k dv in
+ * the same number of velocity dimensions, relaxing towards the conservative
+ * discrete Maxwellian E[U] with relaxation time tau.
+ *
+ * Conventions shared by every entry point:
+ *  - Status: every function returns an int; 0 (DVM_OK) on success, a negative
+ *    dvm_status otherwise.  Errors are sticky per handle: after a failure the
+ *    handle rejects further work with the same code; dvm_last_error() gives a
+ *    one-line message.
+ *  - Streams: all device work is enqueued on the CUDA stream given to
+ *    dvm_create (or dvm_set_stream); NULL means the legacy default stream.
+ *    Calls that return data to the host synchronise that stream.
+ *  - Pointers: "device" pointers are CUDA device addresses, "host" pointers are
+ *    ordinary (pageable or pinned) host memory; an on_device flag says which.
+ *    The library never frees a caller buffer.
+ *  - Cell order: c = x + nx[0] * (y + nx[1] * z), x fastest.
+ *    Velocity order: k = kx + nv[0] * (ky + nv[1] * kz), kx fastest, with
+ *    v_i = (kmin[i] + k_i) * dv.
+ *  - Moments U (Eq. DM): structure of arrays, FP64, (d+2) rows of N_c values:
+ *    rho, rho u_1 .. rho u_d, E with E = rho |u|^2 / 2 + d rho theta / 2
+ *    (Eq. E, gas constant R = 1 so theta = T).
+ */
+#ifndef DVM_H
+#define DVM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DVM_OK = 0,
+  DVM_ERR_ARG = -1,         /* invalid argument or configuration */
+  DVM_ERR_OOM = -2,         /* device allocation failed or workspace too small */
+  DVM_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  DVM_ERR_NONFINITE = -4,   /* a moment became NaN or infinite */
+  DVM_ERR_NONPHYSICAL = -5, /* rho <= 0 or theta <= 0 in some cell */
+  DVM_ERR_TIMEOUT = -6,     /* a bounded device-side wait gave up */
+  DVM_ERR_STATE = -7,       /* call out of order (e.g. step before a state is set) */
+  DVM_ERR_CFL = -8          /* Euler sub-steps needed exceed the launch cap */
+} dvm_status;
+
+typedef enum { DVM_BC_PERIODIC = 0, DVM_BC_OUTFLOW = 1 } dvm_bc;
+typedef enum { DVM_FKS = 0, DVM_HOFKS = 1, DVM_HOFKS_UNLIMITED = 2 } dvm_scheme;
+typedef enum { DVM_F64 = 0, DVM_F32 = 1, DVM_BF16S = 2 } dvm_precision;
+
+/* Spatial grid (Section 4): cell centres x0 + (j + 1/2) dx per dimension. */
+typedef struct {
+  int dim;       /* d = 1, 2 or 3 */
+  int nx[3];     /* cells per dimension; entries beyond dim must be 1 */
+  double x0[3];  /* lower corner of the domain */
+  double dx;     /* uniform cell size */
+} dvm_grid;
+
+/* Velocity grid (Section 3) with a = 0: v_i = k_i dv, k_i = kmin_i ..
+ * kmin_i + n_i - 1.  The time step is dt = dx / (shift_den * dv), so that a
+ * piece moves k_i / shift_den cells per step (exact transport, Section 4.2);
+ * shift_den = 1 gives integer shifts. */
+typedef struct {
+  int n[3];       /* velocities per dimension; entries beyond dim must be 1 */
+  int kmin[3];
+  double dv;
+  int shift_den;  /* p >= 1 */
+} dvm_vset;
+
+typedef struct {
+  dvm_grid grid;
+  dvm_vset vel;
+  double tau;               /* uniform relaxation time; INFINITY = free transport */
+  const double* tau_field;  /* NULL, or N_c host values overriding tau */
+  dvm_bc bc[3][2];          /* per dimension and face; both faces of a
+                               dimension must agree */
+  int scheme;               /* dvm_scheme; DVM_HOFKS is the paper's scheme */
+  int precision;            /* dvm_precision: storage type of f */
+  int euler_subcycles;      /* 0: Euler CFL rule of Eq. Time2 each step;
+                               > 0: that many MUSCL sub-steps per step */
+  int max_subcycles;        /* launch cap for the CFL rule; 0 = automatic */
+} dvm_config;
+
+typedef struct dvm_handle dvm_handle;
+
+/* Bytes of device workspace dvm_create needs for cfg (f, moments, Euler
+ * buffers, per-cell parameters, partial sums).  Returns DVM_ERR_ARG for an
+ * invalid configuration. */
+int dvm_workspace_bytes(const dvm_config* cfg, size_t* bytes);
+
+/* Create a solver.  workspace: NULL (the library allocates with cudaMalloc
+ * and frees in dvm_destroy) or a device buffer of at least
+ * dvm_workspace_bytes bytes, 256-byte aligned, owned by the caller and kept
+ * alive until dvm_destroy.  cuda_stream: a cudaStream_t or NULL.  The step
+ * of one time level is captured once into a CUDA graph here.  The state is
+ * empty until dvm_set_state_* is called.  tau_field is copied. */
+int dvm_create(const dvm_config* cfg, void* workspace, void* cuda_stream,
+               dvm_handle** out);
+void dvm_destroy(dvm_handle* h);
+int dvm_set_stream(dvm_handle* h, void* cuda_stream);
+const char* dvm_last_error(const dvm_handle* h);
+
+/* Initial state in thermodynamic equilibrium: f^0 = E[U^0] (Eq. minimMax,
+ * the projection of Eq. minim1 applied to the pointwise Maxwellian,
+ * Section 4.2 "first time step").  U: (d+2) x N_c FP64 moments, host or
+ * device.  Resets the step counter to 0.  DVM_ERR_NONPHYSICAL if some cell
+ * has rho <= 0 or theta <= 0. */
+int dvm_set_state_moments(dvm_handle* h, const double* U, int on_device);
+
+/* Same from primitive fields (Eqs. Mo, E): rho[N_c], u[d x N_c], T[N_c]. */
+int dvm_set_state_primitive(dvm_handle* h, const double* rho, const double* u,
+                            const double* T, int on_device);
+
+/* Advance nsteps time levels (FKS: Section 4.2, transport then relaxation;
+ * HOFKS: Section 4.3.1, relaxation, transport, U_M replaced by the MUSCL
+ * Euler moments U_E of Section 4.3.2 and the equilibrium part matched to
+ * U_E by Eq. minim_full).  Enqueues the captured graph nsteps times, then
+ * synchronises the stream and returns the device status word (first error
+ * wins: DVM_ERR_NONFINITE, DVM_ERR_NONPHYSICAL, DVM_ERR_CFL). */
+int dvm_step(dvm_handle* h, int nsteps);
+
+/* As dvm_step without the final synchronisation; the status is read later
+ * by dvm_sync_status. */
+int dvm_step_async(dvm_handle* h, int nsteps);
+int dvm_sync_status(dvm_handle* h);
+
+/* Moments U^n at t = n dt (for HOFKS the hybrid moments U_H of Eq. mom):
+ * (d+2) x N_c FP64 into the caller's buffer (host or device). */
+int dvm_moments(dvm_handle* h, double* out, int on_device);
+
+/* f^n at the cell centres, N_v x N_c FP64 (velocity-major), materialised
+ * from the piece storage (the library never moves f; see dvm_offsets). */
+int dvm_get_f(dvm_handle* h, double* out, int on_device);
+
+/* U_E, U_M and U_* of the last HOFKS step (Eqs. UK and mom), each
+ * (d+2) x N_c FP64 host arrays; any pointer may be NULL. */
+int dvm_last_parts(dvm_handle* h, double* UE, double* UM, double* Ustar);
+
+/* dt, step index n, MUSCL sub-steps and alpha (per direction) of the last
+ * step.  Synchronises the stream. */
+int dvm_info(dvm_handle* h, double* dt, long long* n, int* substeps,
+             double* alpha);
+
+/* Exact-transport offsets o_i(k_i, n) = floor((2 k_i n + p) / (2 p)), the
+ * number of cells the piece of velocity component k_i has moved after n
+ * steps (pieces half-open on the left), computed by the same device code the
+ * kinetic pass uses.  out: host int64 array of d x max_i(n_i) entries, row i
+ * holding dimension i. */
+int dvm_offsets(dvm_handle* h, long long n, long long* out);
+
+/* Checkpoint: the full state (step index, piece storage of f, moments and
+ * per-cell parameters) as an opaque host blob.  With buf == NULL, *bytes
+ * receives the size.  dvm_load restores it into a handle created with the
+ * same configuration; the run then continues bit for bit. */
+int dvm_save(dvm_handle* h, void* buf, size_t* bytes);
+int dvm_load(dvm_handle* h, const void* buf, size_t bytes);
+
+/* Kernel launches enqueued by one time step (the captured graph's nodes). */
+int dvm_launches_per_step(dvm_handle* h, int* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

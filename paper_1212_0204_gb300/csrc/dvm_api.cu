@@ -1,0 +1,614 @@
+// dvm_api.cu -- host side of the libdvm C ABI (include/dvm.h): configuration
+// checks, the device workspace, the captured CUDA graph of one time step,
+// state upload, read-back and checkpoints.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "dvm_internal.cuh"
+
+using namespace dvm;
+
+struct dvm_handle {
+  dvm_config cfg;
+  Geom g;
+  DevPtrs p;
+  cudaStream_t stream = nullptr;   // caller's stream
+  cudaStream_t cap = nullptr;      // private stream used only for graph capture
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool use_graph = true;
+  void* ws = nullptr;
+  bool own_ws = false;
+  size_t ws_bytes = 0;
+  long long* offs = nullptr;       // small device table for dvm_offsets
+  int* pinned_status = nullptr;
+  int status = 0;
+  std::string err;
+  bool state_set = false;
+  bool all_free = false;           // every lambda == 1 (tau = inf)
+  int launches = 0;
+};
+
+namespace {
+
+const long long kOffsWidth = kMaxV1;
+
+int fail(dvm_handle* h, int code, const std::string& msg) {
+  if (h) {
+    if (h->status == 0) h->status = code;
+    h->err = msg;
+  }
+  return code;
+}
+
+int cuda_check(dvm_handle* h, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return 0;
+  return fail(h, DVM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+size_t elem_size(int precision) {
+  return precision == DVM_F64 ? 8 : (precision == DVM_F32 ? 4 : 2);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Validate cfg and fill the geometry.  Returns 0 or DVM_ERR_ARG with msg.
+int make_geom(const dvm_config* cfg, Geom* g, std::string* msg) {
+  if (!cfg) { *msg = "null config"; return DVM_ERR_ARG; }
+  const int d = cfg->grid.dim;
+  if (d < 1 || d > 3) { *msg = "dim must be 1, 2 or 3"; return DVM_ERR_ARG; }
+  memset(g, 0, sizeof(Geom));
+  g->d = d;
+  g->nm = d + 2;
+  g->nc = 1;
+  g->nvel = 1;
+  for (int i = 0; i < 3; ++i) {
+    const int nx = cfg->grid.nx[i], nv = cfg->vel.n[i];
+    if (nx < 1 || nv < 1) { *msg = "grid and velocity counts must be >= 1"; return DVM_ERR_ARG; }
+    if (i >= d && (nx != 1 || nv != 1)) { *msg = "unused dimensions must have size 1"; return DVM_ERR_ARG; }
+    if (nv > kMaxV1) { *msg = "at most 256 velocities per dimension"; return DVM_ERR_ARG; }
+    g->nx[i] = nx;
+    g->nv[i] = nv;
+    g->kmin[i] = i < d ? cfg->vel.kmin[i] : 0;
+    g->nc *= nx;
+    g->nvel *= nv;
+    if (i < d) {
+      if (cfg->bc[i][0] != cfg->bc[i][1]) { *msg = "both faces of a dimension need the same boundary rule"; return DVM_ERR_ARG; }
+      if (cfg->bc[i][0] != DVM_BC_PERIODIC && cfg->bc[i][0] != DVM_BC_OUTFLOW) { *msg = "unknown boundary rule"; return DVM_ERR_ARG; }
+      g->bc[i] = cfg->bc[i][0];
+    } else {
+      g->bc[i] = DVM_BC_PERIODIC;
+    }
+  }
+  if (!(cfg->grid.dx > 0) || !(cfg->vel.dv > 0) || cfg->vel.shift_den < 1) {
+    *msg = "dx, dv must be > 0 and shift_den >= 1";
+    return DVM_ERR_ARG;
+  }
+  if (cfg->scheme < DVM_FKS || cfg->scheme > DVM_HOFKS_UNLIMITED) { *msg = "unknown scheme"; return DVM_ERR_ARG; }
+  if (cfg->precision < DVM_F64 || cfg->precision > DVM_BF16S) { *msg = "unknown precision"; return DVM_ERR_ARG; }
+  if (cfg->euler_subcycles < 0 || cfg->max_subcycles < 0) { *msg = "negative sub-step count"; return DVM_ERR_ARG; }
+  if (!cfg->tau_field && !(cfg->tau >= 0)) { *msg = "tau must be >= 0"; return DVM_ERR_ARG; }
+  g->dx = cfg->grid.dx;
+  g->dv = cfg->vel.dv;
+  g->p = cfg->vel.shift_den;
+  g->w = pow(cfg->vel.dv, d);
+  g->dt = cfg->grid.dx / (cfg->vel.shift_den * cfg->vel.dv);
+  g->scheme = cfg->scheme;
+  g->precision = cfg->precision;
+  g->forced_sub = cfg->euler_subcycles;
+  g->m_cap = cfg->euler_subcycles > 0 ? cfg->euler_subcycles : 0;
+  bool outflow = false;
+  for (int i = 0; i < d; ++i) outflow |= g->bc[i] == DVM_BC_OUTFLOW;
+  g->ghost_mode = outflow ? (d == 1 ? 1 : 2) : 0;
+  g->nsplit = kinetic_pass_splits(*g);
+  return 0;
+}
+
+struct Layout {
+  size_t F, ghost, U, lam, W0, W1, acc, prm, eqp, UM, Us, A, small, offs, total;
+};
+
+Layout layout(const Geom& g) {
+  Layout L;
+  const size_t nc = (size_t)g.nc, nv = (size_t)g.nvel, nm = (size_t)g.nm;
+  const size_t es = elem_size(g.precision);
+  const size_t tc = g.precision == DVM_F64 ? 8 : 4;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
+  L.F = take(es * nc * nv);
+  L.ghost = take(g.ghost_mode == 1 ? es * 2 * nv : (g.ghost_mode == 2 ? es * nc * nv : 0));
+  L.U = take(8 * nm * nc);
+  L.lam = take(8 * nc);
+  L.W0 = take(8 * nm * nc);
+  L.W1 = take(8 * nm * nc);
+  L.acc = take(8 * (size_t)g.nsplit * 2 * nm * nc);
+  L.prm = take(tc * (size_t)prm_rows(g.d) * nc);
+  L.eqp = take(8 * (size_t)prm_rows(g.d) * nc);
+  L.UM = take(8 * nm * nc);
+  L.Us = take(8 * nm * nc);
+  L.A = take(8 * kMaxM * kMaxM);
+  L.small = take(256);
+  L.offs = take(8 * 3 * kOffsWidth);
+  L.total = off;
+  return L;
+}
+
+// (C C^T)^{-1}, C with rows m_k dv^d, by Gauss-Jordan elimination with
+// partial pivoting.
+int invert_moment_matrix(const Geom& g, double* A) {
+  const int nm = g.nm;
+  double M[kMaxM][2 * kMaxM];
+  memset(M, 0, sizeof M);
+  for (long long k = 0; k < g.nvel; ++k) {
+    const int kk[3] = {(int)(k % g.nv[0]), (int)((k / g.nv[0]) % g.nv[1]),
+                       (int)(k / ((long long)g.nv[0] * g.nv[1]))};
+    double m[kMaxM];
+    double vv = 0.0;
+    m[0] = g.w;
+    for (int i = 0; i < g.d; ++i) {
+      const double v = (double)(g.kmin[i] + kk[i]) * g.dv;
+      m[1 + i] = v * g.w;
+      vv += v * v;
+    }
+    m[g.d + 1] = 0.5 * vv * g.w;
+    for (int i = 0; i < nm; ++i)
+      for (int j = 0; j < nm; ++j) M[i][j] += m[i] * m[j];
+  }
+  for (int i = 0; i < nm; ++i) M[i][nm + i] = 1.0;
+  for (int col = 0; col < nm; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < nm; ++r)
+      if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
+    if (!(fabs(M[piv][col]) > 0)) return DVM_ERR_ARG;
+    if (piv != col)
+      for (int j = 0; j < 2 * nm; ++j) { double t = M[col][j]; M[col][j] = M[piv][j]; M[piv][j] = t; }
+    const double inv = 1.0 / M[col][col];
+    for (int j = 0; j < 2 * nm; ++j) M[col][j] *= inv;
+    for (int r = 0; r < nm; ++r) {
+      if (r == col) continue;
+      const double f = M[r][col];
+      for (int j = 0; j < 2 * nm; ++j) M[r][j] -= f * M[col][j];
+    }
+  }
+  for (int i = 0; i < nm; ++i)
+    for (int j = 0; j < nm; ++j) A[i * nm + j] = M[i][nm + j];
+  return 0;
+}
+
+void bind(dvm_handle* h, char* base, const Layout& L) {
+  DevPtrs& p = h->p;
+  p.F = base + L.F;
+  p.ghost = h->g.ghost_mode ? base + L.ghost : nullptr;
+  p.U = (double*)(base + L.U);
+  p.lam = (double*)(base + L.lam);
+  p.W0 = (double*)(base + L.W0);
+  p.W1 = (double*)(base + L.W1);
+  p.acc = (double*)(base + L.acc);
+  p.prm = base + L.prm;
+  p.eqp = (double*)(base + L.eqp);
+  p.UM = (double*)(base + L.UM);
+  p.Us = (double*)(base + L.Us);
+  p.A = (double*)(base + L.A);
+  char* sm = base + L.small;
+  p.alpha = (double*)sm;                              // 3 doubles
+  p.alpha_bits = (unsigned long long*)(sm + 32);      // 3
+  p.step = (long long*)(sm + 64);
+  p.msub = (int*)(sm + 72);
+  p.status = (int*)(sm + 76);
+  p.counter = (unsigned int*)(sm + 80);
+  h->offs = (long long*)(base + L.offs);
+}
+
+// Kernels of one time step, in order.
+int enqueue_step(dvm_handle* h, cudaStream_t s) {
+  const Geom& g = h->g;
+  int n = 0;
+  if (g.scheme != DVM_FKS && !h->all_free) {
+    launch_alpha(g, h->p, s);
+    ++n;
+    for (int i = 0; i < g.m_cap; ++i, ++n) launch_muscl(g, h->p, i, s);
+  }
+  if (g.ghost_mode) {
+    launch_ghost(g, h->p, s);
+    ++n;
+  }
+  launch_kinetic_pass(g, h->p, s);
+  launch_finalize(g, h->p, s);
+  n += 2;
+  h->launches = n;
+  return cuda_check(h, cudaGetLastError(), "kernel launch");
+}
+
+void drop_graph(dvm_handle* h) {
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->exec = nullptr;
+  h->graph = nullptr;
+}
+
+int ensure_graph(dvm_handle* h) {
+  if (!h->use_graph || h->exec) return 0;
+  int rc = cuda_check(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal),
+                      "begin capture");
+  if (rc) return rc;
+  rc = enqueue_step(h, h->cap);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+  if (rc) return rc;
+  if ((rc = cuda_check(h, e, "end capture"))) return rc;
+  h->graph = graph;
+  return cuda_check(h, cudaGraphInstantiate(&h->exec, graph, 0), "graph instantiate");
+}
+
+int sync_status(dvm_handle* h) {
+  int rc = cuda_check(h, cudaMemcpyAsync(h->pinned_status, h->p.status, sizeof(int),
+                                         cudaMemcpyDeviceToHost, h->stream), "status copy");
+  if (rc) return rc;
+  if ((rc = cuda_check(h, cudaStreamSynchronize(h->stream), "stream sync"))) return rc;
+  const int st = *h->pinned_status;
+  if (st) {
+    const char* what = st == DVM_ERR_NONFINITE ? "non-finite moments"
+                     : st == DVM_ERR_NONPHYSICAL ? "rho <= 0 or theta <= 0 in some cell"
+                     : st == DVM_ERR_CFL ? "Euler sub-steps exceed the launch cap"
+                     : "device error";
+    return fail(h, st, what);
+  }
+  return 0;
+}
+
+int ready(dvm_handle* h) {
+  if (!h) return DVM_ERR_ARG;
+  return h->status;
+}
+
+// Shared tail of dvm_set_state_*: U is on the device in h->p.U.
+int init_from_moments(dvm_handle* h) {
+  const Geom& g = h->g;
+  cudaStream_t s = h->stream;
+  int rc;
+  if ((rc = cuda_check(h, cudaMemsetAsync(h->p.status, 0, sizeof(int), s), "memset"))) return rc;
+  if ((rc = cuda_check(h, cudaMemsetAsync(h->p.step, 0, sizeof(long long), s), "memset"))) return rc;
+  if ((rc = cuda_check(h, cudaMemsetAsync(h->p.alpha_bits, 0, 3 * sizeof(unsigned long long) + 0, s), "memset"))) return rc;
+  if ((rc = cuda_check(h, cudaMemsetAsync(h->p.counter, 0, sizeof(unsigned), s), "memset"))) return rc;
+  if ((rc = cuda_check(h, cudaMemsetAsync(h->p.alpha, 0, 3 * sizeof(double), s), "memset"))) return rc;
+  if ((rc = cuda_check(h, cudaMemsetAsync(h->p.msub, 0, sizeof(int), s), "memset"))) return rc;
+  launch_cell_params(g, h->p, 0, 1, s);
+  launch_init_f(g, h->p, s);
+  launch_cell_params(g, h->p, 1, 1, s);
+  if ((rc = cuda_check(h, cudaGetLastError(), "init launch"))) return rc;
+  if ((rc = sync_status(h))) return rc;
+  int cap = g.m_cap;
+  if (g.scheme != DVM_FKS && h->all_free) {
+    // free transport: U_E = 0 lives in W0 (msub = 0) and no Euler launches
+    cudaMemsetAsync(h->p.W0, 0, sizeof(double) * g.nm * g.nc, s);
+  } else if (g.scheme != DVM_FKS && g.forced_sub == 0) {
+    // launch cap from the sub-steps the initial state needs
+    Geom probe = g;
+    probe.m_cap = 1 << 30;
+    launch_alpha(probe, h->p, s);
+    int m0 = 0;
+    if ((rc = cuda_check(h, cudaMemcpyAsync(h->pinned_status, h->p.msub, sizeof(int), cudaMemcpyDeviceToHost, s), "copy"))) return rc;
+    if ((rc = cuda_check(h, cudaStreamSynchronize(s), "sync"))) return rc;
+    m0 = *h->pinned_status;
+    cap = h->cfg.max_subcycles > 0 ? h->cfg.max_subcycles : 2 * m0 + 4;
+    if (cap < 8) cap = 8;
+    cudaMemsetAsync(h->p.msub, 0, sizeof(int), s);
+  }
+  if (cap != h->g.m_cap) drop_graph(h);
+  h->g.m_cap = cap;
+  if ((rc = cuda_check(h, cudaStreamSynchronize(s), "sync"))) return rc;
+  h->state_set = true;
+  return 0;
+}
+
+// Copy n bytes from a host or device source into device memory.
+int upload(dvm_handle* h, void* dst, const void* src, size_t n, int on_device) {
+  return cuda_check(h, cudaMemcpyAsync(dst, src, n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream), "upload");
+}
+
+struct BlobHeader {
+  char magic[8];
+  int d, nm, precision, scheme;
+  int nx[3], nv[3];
+  long long step;
+  unsigned long long f_bytes, prm_bytes, mom_bytes;
+};
+
+}  // namespace
+
+extern "C" {
+
+int dvm_workspace_bytes(const dvm_config* cfg, size_t* bytes) {
+  Geom g;
+  std::string msg;
+  const int rc = make_geom(cfg, &g, &msg);
+  if (rc) return rc;
+  if (!bytes) return DVM_ERR_ARG;
+  *bytes = layout(g).total;
+  return 0;
+}
+
+int dvm_create(const dvm_config* cfg, void* workspace, void* cuda_stream, dvm_handle** out) {
+  if (!out) return DVM_ERR_ARG;
+  *out = nullptr;
+  dvm_handle* h = new dvm_handle();
+  std::string msg;
+  int rc = make_geom(cfg, &h->g, &msg);
+  if (rc) { delete h; return rc; }
+  h->cfg = *cfg;
+  h->cfg.tau_field = nullptr;
+  h->stream = (cudaStream_t)cuda_stream;
+  const char* ng = getenv("DVM_NO_GRAPH");
+  h->use_graph = !(ng && ng[0] == '1');
+  const Layout L = layout(h->g);
+  h->ws_bytes = L.total;
+  if (workspace) {
+    if (((uintptr_t)workspace & 255) != 0) { delete h; return DVM_ERR_ARG; }
+    h->ws = workspace;
+  } else {
+    if (cudaMalloc(&h->ws, L.total) != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return DVM_ERR_OOM;
+    }
+    h->own_ws = true;
+  }
+  bind(h, (char*)h->ws, L);
+  if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMallocHost((void**)&h->pinned_status, 64) != cudaSuccess) {
+    dvm_destroy(h);
+    return DVM_ERR_CUDA;
+  }
+  double A[kMaxM * kMaxM];
+  if (invert_moment_matrix(h->g, A)) { dvm_destroy(h); return DVM_ERR_ARG; }
+  std::vector<double> lam((size_t)h->g.nc);
+  bool all_free = true;
+  for (long long c = 0; c < h->g.nc; ++c) {
+    const double tau = cfg->tau_field ? cfg->tau_field[c] : cfg->tau;
+    if (!(tau >= 0)) { dvm_destroy(h); return DVM_ERR_ARG; }
+    lam[c] = exp(-h->g.dt / tau);
+    all_free &= lam[c] == 1.0;
+  }
+  h->all_free = all_free;
+  cudaStream_t s = h->stream;
+  if (cudaMemsetAsync(h->ws, 0, L.total, s) != cudaSuccess ||
+      cudaMemcpyAsync(h->p.A, A, sizeof(double) * h->g.nm * h->g.nm, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(h->p.lam, lam.data(), sizeof(double) * h->g.nc, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    dvm_destroy(h);
+    return DVM_ERR_CUDA;
+  }
+  *out = h;
+  return 0;
+}
+
+void dvm_destroy(dvm_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  drop_graph(h);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->pinned_status) cudaFreeHost(h->pinned_status);
+  if (h->own_ws && h->ws) cudaFree(h->ws);
+  delete h;
+}
+
+int dvm_set_stream(dvm_handle* h, void* cuda_stream) {
+  if (!h) return DVM_ERR_ARG;
+  h->stream = (cudaStream_t)cuda_stream;
+  return 0;
+}
+
+const char* dvm_last_error(const dvm_handle* h) {
+  return h ? h->err.c_str() : "null handle";
+}
+
+int dvm_set_state_moments(dvm_handle* h, const double* U, int on_device) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!U) return fail(h, DVM_ERR_ARG, "null moments");
+  if ((rc = upload(h, h->p.U, U, sizeof(double) * h->g.nm * h->g.nc, on_device))) return rc;
+  return init_from_moments(h);
+}
+
+int dvm_set_state_primitive(dvm_handle* h, const double* rho, const double* u, const double* T,
+                            int on_device) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!rho || !u || !T) return fail(h, DVM_ERR_ARG, "null primitive field");
+  const size_t nc = (size_t)h->g.nc;
+  double* tmp = nullptr;
+  const double *dr = rho, *du = u, *dT = T;
+  if (!on_device) {
+    // staging in the Euler buffers, which init overwrites anyway
+    tmp = h->p.W0;
+    if (3 + h->g.d > 2 * h->g.nm) return fail(h, DVM_ERR_ARG, "staging too small");
+    if ((rc = upload(h, tmp, rho, 8 * nc, 0))) return rc;
+    if ((rc = upload(h, tmp + nc, u, 8 * nc * h->g.d, 0))) return rc;
+    if ((rc = upload(h, tmp + nc * (1 + h->g.d), T, 8 * nc, 0))) return rc;
+    dr = tmp;
+    du = tmp + nc;
+    dT = tmp + nc * (1 + h->g.d);
+  }
+  launch_prim_to_cons(h->g, dr, du, dT, h->p.U, h->stream);
+  if ((rc = cuda_check(h, cudaGetLastError(), "prim launch"))) return rc;
+  return init_from_moments(h);
+}
+
+int dvm_step_async(dvm_handle* h, int nsteps) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!h->state_set) return fail(h, DVM_ERR_STATE, "step before a state was set");
+  if (nsteps < 0) return fail(h, DVM_ERR_ARG, "negative step count");
+  if ((rc = ensure_graph(h))) return rc;
+  for (int i = 0; i < nsteps; ++i) {
+    if (h->exec) {
+      if ((rc = cuda_check(h, cudaGraphLaunch(h->exec, h->stream), "graph launch"))) return rc;
+    } else if ((rc = enqueue_step(h, h->stream))) {
+      return rc;
+    }
+  }
+  return 0;
+}
+
+int dvm_sync_status(dvm_handle* h) {
+  int rc = ready(h);
+  if (rc) return rc;
+  return sync_status(h);
+}
+
+int dvm_step(dvm_handle* h, int nsteps) {
+  int rc = dvm_step_async(h, nsteps);
+  if (rc) return rc;
+  return sync_status(h);
+}
+
+int dvm_moments(dvm_handle* h, double* out, int on_device) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!out) return fail(h, DVM_ERR_ARG, "null output");
+  if ((rc = cuda_check(h, cudaMemcpyAsync(out, h->p.U, sizeof(double) * h->g.nm * h->g.nc,
+                                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                          h->stream), "moments copy"))) return rc;
+  return cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
+}
+
+int dvm_get_f(dvm_handle* h, double* out, int on_device) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!out) return fail(h, DVM_ERR_ARG, "null output");
+  const size_t bytes = sizeof(double) * (size_t)h->g.nc * (size_t)h->g.nvel;
+  double* dst = out;
+  if (!on_device) {
+    if ((rc = cuda_check(h, cudaMalloc(&dst, bytes), "f staging"))) return rc;
+  }
+  launch_materialize(h->g, h->p, dst, h->stream);
+  rc = cuda_check(h, cudaGetLastError(), "materialize");
+  if (!rc && !on_device)
+    rc = cuda_check(h, cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, h->stream), "f copy");
+  if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
+  if (!on_device) cudaFree(dst);
+  return rc;
+}
+
+int dvm_last_parts(dvm_handle* h, double* UE, double* UM, double* Ustar) {
+  int rc = ready(h);
+  if (rc) return rc;
+  int m = 0;
+  if ((rc = cuda_check(h, cudaMemcpyAsync(h->pinned_status, h->p.msub, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "copy"))) return rc;
+  if ((rc = cuda_check(h, cudaStreamSynchronize(h->stream), "sync"))) return rc;
+  m = *h->pinned_status;
+  const size_t b = sizeof(double) * h->g.nm * h->g.nc;
+  cudaStream_t s = h->stream;
+  if (UE) rc |= cuda_check(h, cudaMemcpyAsync(UE, (m & 1) ? h->p.W1 : h->p.W0, b, cudaMemcpyDeviceToHost, s), "copy");
+  if (UM) rc |= cuda_check(h, cudaMemcpyAsync(UM, h->p.UM, b, cudaMemcpyDeviceToHost, s), "copy");
+  if (Ustar) rc |= cuda_check(h, cudaMemcpyAsync(Ustar, h->p.Us, b, cudaMemcpyDeviceToHost, s), "copy");
+  if (rc) return h->status;
+  return cuda_check(h, cudaStreamSynchronize(s), "sync");
+}
+
+int dvm_info(dvm_handle* h, double* dt, long long* n, int* substeps, double* alpha) {
+  int rc = ready(h);
+  if (rc) return rc;
+  long long step = 0;
+  int m = 0;
+  double a[3] = {0, 0, 0};
+  cudaStream_t s = h->stream;
+  rc |= cuda_check(h, cudaMemcpyAsync(&step, h->p.step, sizeof step, cudaMemcpyDeviceToHost, s), "copy");
+  rc |= cuda_check(h, cudaMemcpyAsync(&m, h->p.msub, sizeof m, cudaMemcpyDeviceToHost, s), "copy");
+  rc |= cuda_check(h, cudaMemcpyAsync(a, h->p.alpha, sizeof a, cudaMemcpyDeviceToHost, s), "copy");
+  rc |= cuda_check(h, cudaStreamSynchronize(s), "sync");
+  if (rc) return h->status;
+  if (dt) *dt = h->g.dt;
+  if (n) *n = step;
+  if (substeps) *substeps = m;
+  if (alpha) memcpy(alpha, a, sizeof a);
+  return 0;
+}
+
+int dvm_offsets(dvm_handle* h, long long n, long long* out) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!out) return fail(h, DVM_ERR_ARG, "null output");
+  int width = 1;
+  for (int i = 0; i < h->g.d; ++i) width = h->g.nv[i] > width ? h->g.nv[i] : width;
+  launch_offsets(h->g, n, h->offs, width, h->stream);
+  if ((rc = cuda_check(h, cudaGetLastError(), "offsets launch"))) return rc;
+  if ((rc = cuda_check(h, cudaMemcpyAsync(out, h->offs, sizeof(long long) * h->g.d * width,
+                                          cudaMemcpyDeviceToHost, h->stream), "copy"))) return rc;
+  return cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
+}
+
+int dvm_save(dvm_handle* h, void* buf, size_t* bytes) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!bytes) return fail(h, DVM_ERR_ARG, "null size");
+  if (!h->state_set) return fail(h, DVM_ERR_STATE, "no state to save");
+  const Layout L = layout(h->g);
+  BlobHeader hd;
+  memset(&hd, 0, sizeof hd);
+  memcpy(hd.magic, "DVMSTAT1", 8);
+  hd.d = h->g.d; hd.nm = h->g.nm; hd.precision = h->g.precision; hd.scheme = h->g.scheme;
+  for (int i = 0; i < 3; ++i) { hd.nx[i] = h->g.nx[i]; hd.nv[i] = h->g.nv[i]; }
+  hd.f_bytes = elem_size(h->g.precision) * (size_t)h->g.nc * (size_t)h->g.nvel;
+  hd.prm_bytes = (h->g.precision == DVM_F64 ? 8 : 4) * (size_t)prm_rows(h->g.d) * (size_t)h->g.nc;
+  hd.mom_bytes = 8 * (size_t)h->g.nm * (size_t)h->g.nc;
+  const size_t total = sizeof hd + hd.f_bytes + hd.prm_bytes + hd.mom_bytes;
+  (void)L;
+  if (!buf) { *bytes = total; return 0; }
+  if (*bytes < total) return fail(h, DVM_ERR_ARG, "checkpoint buffer too small");
+  cudaStream_t s = h->stream;
+  rc |= cuda_check(h, cudaMemcpyAsync(&hd.step, h->p.step, 8, cudaMemcpyDeviceToHost, s), "copy");
+  char* b = (char*)buf + sizeof hd;
+  rc |= cuda_check(h, cudaMemcpyAsync(b, h->p.F, hd.f_bytes, cudaMemcpyDeviceToHost, s), "copy");
+  rc |= cuda_check(h, cudaMemcpyAsync(b + hd.f_bytes, h->p.prm, hd.prm_bytes, cudaMemcpyDeviceToHost, s), "copy");
+  rc |= cuda_check(h, cudaMemcpyAsync(b + hd.f_bytes + hd.prm_bytes, h->p.U, hd.mom_bytes, cudaMemcpyDeviceToHost, s), "copy");
+  rc |= cuda_check(h, cudaStreamSynchronize(s), "sync");
+  if (rc) return h->status;
+  memcpy(buf, &hd, sizeof hd);
+  *bytes = total;
+  return 0;
+}
+
+int dvm_load(dvm_handle* h, const void* buf, size_t bytes) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!buf || bytes < sizeof(BlobHeader)) return fail(h, DVM_ERR_ARG, "bad checkpoint");
+  BlobHeader hd;
+  memcpy(&hd, buf, sizeof hd);
+  bool ok = memcmp(hd.magic, "DVMSTAT1", 8) == 0 && hd.d == h->g.d && hd.precision == h->g.precision &&
+            hd.scheme == h->g.scheme;
+  for (int i = 0; i < 3; ++i) ok &= hd.nx[i] == h->g.nx[i] && hd.nv[i] == h->g.nv[i];
+  if (!ok || bytes < sizeof hd + hd.f_bytes + hd.prm_bytes + hd.mom_bytes)
+    return fail(h, DVM_ERR_ARG, "checkpoint does not match this configuration");
+  cudaStream_t s = h->stream;
+  const char* b = (const char*)buf + sizeof hd;
+  // the moments first: the cap of Euler sub-steps is derived from them
+  rc |= upload(h, h->p.U, b + hd.f_bytes + hd.prm_bytes, hd.mom_bytes, 0);
+  if (rc) return h->status;
+  if ((rc = init_from_moments(h))) return rc;
+  rc |= upload(h, h->p.F, b, hd.f_bytes, 0);
+  rc |= upload(h, h->p.prm, b + hd.f_bytes, hd.prm_bytes, 0);
+  rc |= cuda_check(h, cudaMemcpyAsync(h->p.step, &hd.step, 8, cudaMemcpyHostToDevice, s), "copy");
+  rc |= cuda_check(h, cudaStreamSynchronize(s), "sync");
+  return rc ? h->status : 0;
+}
+
+int dvm_launches_per_step(dvm_handle* h, int* launches) {
+  if (!h || !launches) return DVM_ERR_ARG;
+  if (!h->state_set) return fail(h, DVM_ERR_STATE, "no state yet");
+  int n = 0;
+  if (h->g.scheme != DVM_FKS && !h->all_free) n += 1 + h->g.m_cap;
+  if (h->g.ghost_mode) n += 1;
+  n += 2;
+  *launches = n;
+  return 0;
+}
+
+}  // extern "C"

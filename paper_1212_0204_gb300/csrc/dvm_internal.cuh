@@ -1,0 +1,144 @@
+// dvm_internal.cuh -- types and device helpers shared by the libdvm
+// translation units (never installed, never seen by callers).
+//
+// Storage of f ("piece storage"): F[k * Nc + q] holds the piecewise-constant
+// value of velocity k on piece q.  Pieces never move in memory; after n steps
+// the piece q of velocity component k_i sits in cell (q_i + o_i(k_i, n)) mod
+// N_i of every dimension i, with o the exact-transport offset of Section 4.2.
+// Transport is therefore pure index arithmetic folded into the loads of the
+// kinetic pass.
+//
+// Deferred linear term: the stored value differs from the true f by a term
+// that depends only on the cell the piece currently occupies,
+//   f = F + omega_s M_k[U_s] + m_k . beta_s     (s = the piece's cell),
+// with (omega, beta) = (0, dv^d nu) for HOFKS (the moment-matching correction
+// of Eq. minim_full) and (1 - lambda, (1 - lambda) dv^d mu) for FKS (the
+// equilibrium part of Eq. relaxdvm).  Applying that term when the piece is
+// next read, instead of when it is written, lets one pass over f compute the
+// moment sums and the update together: the write no longer has to wait for
+// the reduction over all velocities of the cell.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "dvm.h"
+
+namespace dvm {
+
+constexpr int kMaxD = 3;
+constexpr int kMaxM = 5;      // d + 2
+constexpr int kMaxV1 = 256;   // velocities per dimension
+constexpr int kMaxNP = 3 + 3 + 2 * 5;
+
+// Per-cell parameter rows (compute type), row r at prm[r * Nc + c]:
+//   0            lambda = exp(-dt / tau)
+//   1            L = log2(weight * rho / (2 pi theta)^{d/2})
+//   2 .. 1+d     u
+//   2+d          h = log2(e) / (2 theta)
+//   3+d ..       nu' = dv^d nu                      (d+2 rows)
+//   3+d+(d+2) .. mu'' = weight * dv^d mu            (d+2 rows)
+// The Maxwellian of the cell is M_k = exp2(L - h |v_k - u|^2) / weight.
+__host__ __device__ inline int prm_rows(int d) { return 3 + d + 2 * (d + 2); }
+__host__ __device__ inline int row_lam() { return 0; }
+__host__ __device__ inline int row_L() { return 1; }
+__host__ __device__ inline int row_u(int i) { return 2 + i; }
+__host__ __device__ inline int row_h(int d) { return 2 + d; }
+__host__ __device__ inline int row_nu(int d, int i) { return 3 + d + i; }
+__host__ __device__ inline int row_mu(int d, int i) { return 3 + d + (d + 2) + i; }
+
+struct Geom {
+  int d, nm;
+  int nx[3];
+  long long nc;
+  int nv[3];
+  int kmin[3];
+  long long nvel;
+  double dv, w, dt, dx;
+  int p;
+  int bc[3];          // DVM_BC_* per dimension
+  int scheme;         // DVM_FKS / DVM_HOFKS / DVM_HOFKS_UNLIMITED
+  int precision;      // DVM_F64 / DVM_F32 / DVM_BF16S
+  int forced_sub;     // > 0: fixed Euler sub-steps
+  int m_cap;          // launch cap of Euler sub-steps
+  int nsplit;         // velocity chunks of the kinetic pass
+  int ghost_mode;     // 0 none, 1 two boundary pieces per velocity (1D), 2 full copy
+};
+
+struct DevPtrs {
+  void* F;            // nvel x nc storage
+  void* ghost;
+  double* U;          // nm x nc
+  double* lam;        // nc
+  double* W0;         // nm x nc (Euler ping-pong)
+  double* W1;
+  double* acc;        // nsplit x 2nm x nc partial moment sums
+  void* prm;          // NP x nc, compute type
+  double* eqp;        // NP x nc, FP64 parameters of E[U] (initial state only)
+  double* UM;         // nm x nc, last step's U_M
+  double* Us;         // nm x nc, last step's U_*
+  double* A;          // nm x nm, (C C^T)^{-1}
+  double* alpha;      // 3, alpha of the last step
+  unsigned long long* alpha_bits;  // 3, running max (bit pattern of >= 0 doubles)
+  int* msub;          // Euler sub-steps of the current step
+  int* status;        // first error code
+  long long* step;    // step index n
+  unsigned int* counter;  // finished-block counter of the alpha reduction
+};
+
+// ---------------------------------------------------------------- helpers
+
+__host__ __device__ inline long long floor_div(long long a, long long b) {
+  long long q = a / b;
+  if ((a % b != 0) && ((a < 0) != (b < 0))) q -= 1;
+  return q;
+}
+
+// Exact-transport offset: round-half-up of k n / p (Section 4.2, pieces
+// half-open on the left).
+__host__ __device__ inline long long transport_offset(long long k, long long n, long long p) {
+  return floor_div(2 * k * n + p, 2 * p);
+}
+
+__host__ __device__ inline int wrap(long long x, int n) {
+  long long r = x % n;
+  return (int)(r < 0 ? r + n : r);
+}
+
+__device__ inline void set_status(int* status, int code) { atomicCAS(status, 0, code); }
+
+template <typename T> struct StoreT;
+template <> struct StoreT<double> {
+  __device__ static double load(const double* p) { return *p; }
+  __device__ static void store(double* p, double v) { *p = v; }
+};
+template <> struct StoreT<float> {
+  __device__ static float load(const float* p) { return *p; }
+  __device__ static void store(float* p, float v) { *p = v; }
+};
+template <> struct StoreT<__nv_bfloat16> {
+  __device__ static float load(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+  __device__ static void store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// ------------------------------------------------------- launch wrappers
+// dvm_cells.cu
+void launch_prim_to_cons(const Geom& g, const double* rho, const double* u, const double* T,
+                         double* U, cudaStream_t s);
+// mode: 0 = equilibrium weights (used to build f^0), 1 = parameters of the next step
+void launch_cell_params(const Geom& g, const DevPtrs& p, int mode, int initial, cudaStream_t s);
+void launch_init_f(const Geom& g, const DevPtrs& p, cudaStream_t s);
+void launch_alpha(const Geom& g, const DevPtrs& p, cudaStream_t s);
+void launch_muscl(const Geom& g, const DevPtrs& p, int substep, cudaStream_t s);
+void launch_ghost(const Geom& g, const DevPtrs& p, cudaStream_t s);
+void launch_finalize(const Geom& g, const DevPtrs& p, cudaStream_t s);
+void launch_materialize(const Geom& g, const DevPtrs& p, double* out, cudaStream_t s);
+void launch_offsets(const Geom& g, long long n, long long* out, int width, cudaStream_t s);
+// dvm_kinetic.cu
+void launch_kinetic_pass(const Geom& g, const DevPtrs& p, cudaStream_t s);
+int kinetic_pass_splits(const Geom& g);
+
+}  // namespace dvm

@@ -1,0 +1,259 @@
+"""ctypes binding of libdvm (include/dvm.h): argument marshalling only.
+
+Every step of the scheme runs in the CUDA library; this module converts Python
+values into the C structs and pointers of the ABI.  PyTorch supplies the device
+workspace (its caching allocator) and the CUDA stream.  There is no CPU
+fallback: if ``libdvm.so`` is missing or no GPU is visible, creating a solver
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdvm.so")
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_STATE, ERR_CFL = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8
+PERIODIC, OUTFLOW = 0, 1
+FKS, HOFKS, HOFKS_UNLIMITED = 0, 1, 2
+F64, F32, BF16S = 0, 1, 2
+
+# every symbol include/dvm.h declares (checked by the CPU tests)
+EXPORTS = [
+    "dvm_workspace_bytes", "dvm_create", "dvm_destroy", "dvm_set_stream", "dvm_last_error",
+    "dvm_set_state_moments", "dvm_set_state_primitive", "dvm_step", "dvm_step_async",
+    "dvm_sync_status", "dvm_moments", "dvm_get_f", "dvm_last_parts", "dvm_info", "dvm_offsets",
+    "dvm_save", "dvm_load", "dvm_launches_per_step",
+]
+
+
+class DvmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libdvm status {code}: {msg}")
+        self.code = code
+
+
+class _Grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nx", C.c_int * 3), ("x0", C.c_double * 3), ("dx", C.c_double)]
+
+
+class _VSet(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("kmin", C.c_int * 3), ("dv", C.c_double),
+                ("shift_den", C.c_int)]
+
+
+class _Config(C.Structure):
+    _fields_ = [("grid", _Grid), ("vel", _VSet), ("tau", C.c_double),
+                ("tau_field", C.POINTER(C.c_double)), ("bc", (C.c_int * 2) * 3),
+                ("scheme", C.c_int), ("precision", C.c_int), ("euler_subcycles", C.c_int),
+                ("max_subcycles", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libdvm.so (built by ``paper_1212_0204_gb300.build``); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+        L.dvm_workspace_bytes.argtypes = [C.POINTER(_Config), C.POINTER(C.c_size_t)]
+        L.dvm_create.argtypes = [C.POINTER(_Config), vp, vp, C.POINTER(vp)]
+        L.dvm_destroy.argtypes = [vp]
+        L.dvm_destroy.restype = None
+        L.dvm_set_stream.argtypes = [vp, vp]
+        L.dvm_last_error.argtypes = [vp]
+        L.dvm_last_error.restype = C.c_char_p
+        L.dvm_set_state_moments.argtypes = [vp, vp, ip]
+        L.dvm_set_state_primitive.argtypes = [vp, vp, vp, vp, ip]
+        L.dvm_step.argtypes = [vp, ip]
+        L.dvm_step_async.argtypes = [vp, ip]
+        L.dvm_sync_status.argtypes = [vp]
+        L.dvm_moments.argtypes = [vp, vp, ip]
+        L.dvm_get_f.argtypes = [vp, vp, ip]
+        L.dvm_last_parts.argtypes = [vp, vp, vp, vp]
+        L.dvm_info.argtypes = [vp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_int), dp]
+        L.dvm_offsets.argtypes = [vp, C.c_longlong, C.POINTER(C.c_longlong)]
+        L.dvm_save.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
+        L.dvm_load.argtypes = [vp, vp, C.c_size_t]
+        L.dvm_launches_per_step.argtypes = [vp, C.POINTER(C.c_int)]
+        _lib = L
+    return _lib
+
+
+def make_config(d, nx, dx, nv, kmin, dv, p=1, bc=None, tau=float("inf"), tau_field=None,
+                scheme=HOFKS, precision=F64, subcycles=0, max_subcycles=0, x0=None):
+    """Fill the C ``dvm_config``; returns (struct, keep-alive list)."""
+    pad = lambda t, v: list(t) + [v] * (3 - len(t))
+    cfg = _Config()
+    cfg.grid.dim = d
+    cfg.grid.nx[:] = pad(nx, 1)
+    cfg.grid.x0[:] = pad(x0 or (), 0.0)
+    cfg.grid.dx = dx
+    cfg.vel.n[:] = pad(nv, 1)
+    cfg.vel.kmin[:] = pad(kmin, 0)
+    cfg.vel.dv = dv
+    cfg.vel.shift_den = p
+    keep = []
+    if tau_field is not None:
+        arr = np.ascontiguousarray(tau_field, dtype=np.float64)
+        keep.append(arr)
+        cfg.tau_field = arr.ctypes.data_as(C.POINTER(C.c_double))
+        cfg.tau = 0.0
+    else:
+        cfg.tau = tau
+    bcs = pad(bc or (), PERIODIC)
+    for i in range(3):
+        cfg.bc[i][0] = bcs[i]
+        cfg.bc[i][1] = bcs[i]
+    cfg.scheme = scheme
+    cfg.precision = precision
+    cfg.euler_subcycles = subcycles
+    cfg.max_subcycles = max_subcycles
+    return cfg, keep
+
+
+def config_from_case(case, precision=F64, scheme=None, subcycles=None):
+    tau = case.tau
+    field = None if np.isscalar(tau) else tau
+    return make_config(case.d, case.nx, case.dx, case.nv, case.kmin, case.dv, case.p, case.bc,
+                       tau=float(tau) if field is None else 0.0, tau_field=field,
+                       scheme=case.scheme if scheme is None else scheme, precision=precision,
+                       subcycles=case.subcycles if subcycles is None else subcycles)
+
+
+def workspace_bytes(cfg) -> int:
+    n = C.c_size_t()
+    rc = lib().dvm_workspace_bytes(C.byref(cfg), C.byref(n))
+    if rc:
+        raise DvmError(rc, "invalid configuration")
+    return n.value
+
+
+class Solver:
+    """One libdvm handle.  Device memory comes from a torch uint8 tensor and work
+    runs on torch's current CUDA stream (or the one given)."""
+
+    def __init__(self, cfg, keep=(), stream=None, torch_workspace=True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libdvm needs a CUDA GPU; no CPU fallback exists")
+        self._torch = torch
+        self.cfg = cfg
+        self._keep = list(keep)
+        self.d = cfg.grid.dim
+        self.nm = self.d + 2
+        self.nc = int(np.prod([cfg.grid.nx[i] for i in range(3)]))
+        self.nvel = int(np.prod([cfg.vel.n[i] for i in range(3)]))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        ws_ptr = None
+        self._ws = None
+        if torch_workspace:
+            nbytes = workspace_bytes(cfg)
+            self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+            base = self._ws.data_ptr()
+            ws_ptr = (base + 255) & ~255
+        h = C.c_void_p()
+        rc = lib().dvm_create(C.byref(cfg), ws_ptr, C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if rc:
+            raise DvmError(rc, "dvm_create failed")
+        self._h = h
+
+    @classmethod
+    def from_case(cls, case, precision=F64, scheme=None, subcycles=None, **kw):
+        cfg, keep = config_from_case(case, precision, scheme, subcycles)
+        return cls(cfg, keep, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dvm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _check(self, rc):
+        if rc:
+            raise DvmError(rc, lib().dvm_last_error(self._h).decode())
+
+    # --------------------------------------------------------------- state
+    def set_moments(self, U):
+        t = self._torch
+        if isinstance(U, t.Tensor) and U.is_cuda:
+            U = U.to(t.float64).contiguous()
+            self._check(lib().dvm_set_state_moments(self._h, C.c_void_p(U.data_ptr()), 1))
+        else:
+            a = np.ascontiguousarray(U, dtype=np.float64).reshape(self.nm, self.nc)
+            self._check(lib().dvm_set_state_moments(self._h, a.ctypes.data_as(C.c_void_p), 0))
+
+    def set_primitive(self, rho, u, T):
+        a = [np.ascontiguousarray(x, dtype=np.float64) for x in (rho, u, T)]
+        ptrs = [x.ctypes.data_as(C.c_void_p) for x in a]
+        self._check(lib().dvm_set_state_primitive(self._h, *ptrs, 0))
+
+    def step(self, n=1):
+        self._check(lib().dvm_step(self._h, int(n)))
+
+    def step_async(self, n=1):
+        self._check(lib().dvm_step_async(self._h, int(n)))
+
+    def sync_status(self):
+        self._check(lib().dvm_sync_status(self._h))
+
+    # ----------------------------------------------------------- read-back
+    def moments(self, out=None):
+        t = self._torch
+        if out is not None and isinstance(out, t.Tensor) and out.is_cuda:
+            self._check(lib().dvm_moments(self._h, C.c_void_p(out.data_ptr()), 1))
+            return out
+        a = np.zeros((self.nm, self.nc))
+        self._check(lib().dvm_moments(self._h, a.ctypes.data_as(C.c_void_p), 0))
+        return a
+
+    def f(self):
+        a = np.zeros((self.nvel, self.nc))
+        self._check(lib().dvm_get_f(self._h, a.ctypes.data_as(C.c_void_p), 0))
+        return a
+
+    def parts(self):
+        shape = (self.nm, self.nc)
+        UE, UM, Us = np.zeros(shape), np.zeros(shape), np.zeros(shape)
+        p = lambda a: a.ctypes.data_as(C.c_void_p)
+        self._check(lib().dvm_last_parts(self._h, p(UE), p(UM), p(Us)))
+        return UE, UM, Us
+
+    def info(self):
+        dt, n, m = C.c_double(), C.c_longlong(), C.c_int()
+        alpha = np.zeros(3)
+        self._check(lib().dvm_info(self._h, C.byref(dt), C.byref(n), C.byref(m),
+                                   alpha.ctypes.data_as(C.POINTER(C.c_double))))
+        return {"dt": dt.value, "n": n.value, "m": m.value, "alpha": alpha}
+
+    def offsets(self, n):
+        width = max(self.cfg.vel.n[i] for i in range(self.d))
+        out = np.zeros((self.d, width), dtype=np.int64)
+        self._check(lib().dvm_offsets(self._h, int(n), out.ctypes.data_as(C.POINTER(C.c_longlong))))
+        return out
+
+    def save(self) -> bytes:
+        n = C.c_size_t()
+        self._check(lib().dvm_save(self._h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._check(lib().dvm_save(self._h, buf, C.byref(n)))
+        return buf.raw[:n.value]
+
+    def load(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        self._check(lib().dvm_load(self._h, buf, len(blob)))
+
+    def launches_per_step(self) -> int:
+        n = C.c_int()
+        self._check(lib().dvm_launches_per_step(self._h, C.byref(n)))
+        return n.value
