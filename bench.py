@@ -1,0 +1,344 @@
+#!/usr/bin/env python3
+"""Phase-space updates/s of the discrete-velocity BGK scheme (HOFKS) on GB300.
+
+    python bench.py [--gpus N --steps K --warmup W] [--workload NAME] [--impl reference]
+
+One step = one full time step of the hot path: alpha reduction, the MUSCL Euler
+sub-steps, the kinetic pass over all N_c x N_v phase-space points and the
+end-of-step cell update, replayed from the captured CUDA graph.  Inputs are
+seeded synthetic fields (``paper_1212_0204_gb300.workloads``) shaped like the
+paper's workloads; f (268 MB for the default 2D-2V case in FP32) is larger than
+L2, so no flush is needed between steps.
+
+Prints one JSON line on rank 0.  Under torchrun every rank runs an independent
+replica of the workload (weak scaling; the method has no exchange step on one
+problem per GPU) and ``value`` is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1212_0204_gb300 import workloads as W  # noqa: E402
+
+METRIC = "phase-space updates/s"
+UNIT = "updates/s"
+
+# name -> (case builder, precision, bytes of f per update: one read + one write)
+WORKLOADS = {
+    "quadrant_2d": (lambda: W.quadrant_2d(n=256, nv=32, tau=1e-3, steps=500), "f32"),
+    "density_wave_3d": (lambda: W.density_wave_3d(n=96, nv=24, tau=1e-4, steps=100), "f32"),
+    "density_wave_3d_64": (lambda: W.density_wave_3d(n=64, nv=24, tau=1e-4, steps=100), "f32"),
+    "quadrant_2d_f64": (lambda: W.quadrant_2d(n=256, nv=32, tau=1e-3, steps=500), "f64"),
+    "quadrant_2d_bf16": (lambda: W.quadrant_2d(n=256, nv=32, tau=1e-3, steps=500), "bf16"),
+    "sod_1d": (lambda: W.sod_1d(nx=200, nv=32, tau=1e-4), "f64"),
+}
+DESCR = {
+    "quadrant_2d": "2D-2V four-quadrant Riemann problem, 256x256 periodic cells x 32x32 velocities, "
+                   "tau=1e-3, HOFKS, FP32 f / FP64 moments",
+    "density_wave_3d": "3D-3V periodic density wave, 96^3 cells x 24^3 velocities, tau=1e-4, HOFKS, "
+                       "FP32 f / FP64 moments",
+    "density_wave_3d_64": "3D-3V periodic density wave, 64^3 cells x 24^3 velocities, tau=1e-4, HOFKS, "
+                          "FP32 f / FP64 moments",
+    "quadrant_2d_f64": "2D-2V four-quadrant Riemann problem, 256^2 x 32^2, HOFKS, FP64 f",
+    "quadrant_2d_bf16": "2D-2V four-quadrant Riemann problem, 256^2 x 32^2, HOFKS, BF16 f storage",
+    "sod_1d": "1D-1V Sod tube, 200 cells x 32 velocities, tau=1e-4, outflow, HOFKS, FP64",
+}
+BYTES_PER_UPDATE = {"f64": 16, "f32": 8, "bf16": 4}
+DTYPE = {"f64": "f64", "f32": "f32", "bf16": "bf16"}
+
+
+def conserved(case):
+    """Conserved moments (Eqs. Mo/E) from the recipe's primitive fields, host side."""
+    d = case.d
+    U = np.zeros((d + 2, case.ncells))
+    U[0] = case.rho
+    for i in range(d):
+        U[1 + i] = case.rho * case.u[i]
+    U[d + 1] = 0.5 * case.rho * (case.u ** 2).sum(0) + 0.5 * d * case.rho * case.T
+    return U
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kinetic_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("dvm_kinetic.cu", "dvm_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1212_0204_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes per kinetic-pass launch from the committed ncu summary, if it was
+    taken on the current kernel source and this workload; else None."""
+    path = os.path.join(ROOT, "profiles", "kinetic_pass_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = kinetic_source_hash()
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        kv = dict(tok.split("=", 1) for tok in line.split())
+        if kv.get("workload") == workload and kv.get("source") == src:
+            return float(kv["dram_bytes_per_launch"])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "20"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.05)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[2:]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def physical_gpu_index(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids) and ids[local_rank].strip().isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+def oracle_sample(case, budget_points: float):
+    """A bounded sample of the workload for the CPU oracle: same velocity grid and
+    initial-data recipe, fewer cells (a square/cubic sub-problem)."""
+    if case.name == "quadrant_2d":
+        n = int(max(8, min(case.nx[0], round((budget_points / case.nvel) ** 0.5))))
+        return W.quadrant_2d(n=n, nv=case.nv[0], tau=case.tau, steps=1, dv=case.dv), f"{n}x{n} cells"
+    if case.name == "density_wave_3d":
+        n = int(max(4, min(case.nx[0], round((budget_points / case.nvel) ** (1 / 3)))))
+        return (W.density_wave_3d(n=n, nv=case.nv[0], tau=case.tau, steps=1, dv=case.dv),
+                f"{n}^3 cells")
+    return case, f"{case.nx[0]} cells"
+
+
+def time_oracle(case, steps: int, warmup: int = 0):
+    import oracle
+    from tests.helpers import grid
+    g = grid(case)
+    s = oracle.Scheme(g, tau=case.tau)
+    s.set_moments(conserved(case))
+    if warmup:
+        s.step(warmup)
+    t0 = time.perf_counter()
+    s.step(steps)
+    dt = time.perf_counter() - t0
+    return case.points * steps / dt, dt
+
+
+def run_reference(args, case, descr, rank):
+    """Reference arm: the FP64 CPU oracle, untuned, on bounded samples of the workload."""
+    if rank != 0:
+        return 0
+    per_step_budget = 90.0 / max(1, args.steps + args.warmup)  # seconds, ~90 s total
+    sample, what = oracle_sample(case, per_step_budget * 8e6)
+    value, secs = time_oracle(sample, args.steps, args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": descr, "sample": what},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{what} x {case.nvel} velocities, {args.steps} steps "
+                                   f"after {args.warmup} warm-up steps, single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="quadrant_2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    make, prec = WORKLOADS[args.workload]
+    case = make()
+    if args.steps is None:
+        args.steps = case.steps
+    args.warmup = max(3, args.warmup)
+    descr = DESCR[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, case, descr, rank)
+
+    import torch
+    from paper_1212_0204_gb300 import dvm
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    precision = {"f64": dvm.F64, "f32": dvm.F32, "bf16": dvm.BF16S}[prec]
+    solver = dvm.Solver.from_case(case, precision=precision)
+    stream = solver.stream
+    U0 = torch.from_numpy(conserved(case)).contiguous().pin_memory()
+    solver.set_moments(U0)
+    solver.step(args.warmup)
+    launches = solver.launches_per_step()
+
+    # ---- device-timed region: K graph replays on the solver's stream
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(physical_gpu_index(local)) as clk:
+        barrier()
+        start.record(stream)
+        solver.step_async(args.steps)
+        stop.record(stream)
+        stop.synchronize()
+        barrier()
+    solver.sync_status()
+    ms = start.elapsed_time(stop)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = case.points * args.steps * world / (ms * 1e-3)
+
+    # ---- kinetic-pass roofline: the same steps, kinetic pass bracketed by events
+    solver.profile_begin()
+    solver.step_async(args.steps)
+    kin_ms, kin_n = solver.profile_end()
+    solver.sync_status()
+    bytes_alg = BYTES_PER_UPDATE[prec] * case.points
+    achieved = bytes_alg / (kin_ms / kin_n * 1e-3) / 1e9
+    peak, peak_kind = load_peaks()
+    traffic = recorded_traffic(args.workload)
+
+    # ---- end to end through the public API with host buffers
+    out = torch.empty((case.d + 2, case.ncells), dtype=torch.float64).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    solver.set_moments(U0)          # H2D of the initial moments, builds f^0
+    solver.step(args.steps)
+    solver.moments(out)             # D2H of the final moments
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    mom_bytes = 8 * (case.d + 2) * case.ncells
+    e2e = {"value": case.points * args.steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": mom_bytes / args.steps, "d2h_bytes_per_step": mom_bytes / args.steps,
+           "note": "initial moments uploaded and final moments read back once per K-step job"}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline:
+        sample, what = oracle_sample(case, 4e6)
+        v, secs = time_oracle(sample, steps=max(1, int(round(15.0 * 8e6 / sample.points))))
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{what} x {case.nvel} velocities, {secs:.1f} s of single-thread FP64 oracle"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
+        "config": {"workload": descr, "cells": case.ncells, "velocities": case.nvel,
+                   "points": case.points, "l2": "f larger than L2 (no flush)",
+                   "parallelism": f"{world} independent replica(s)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "kinetic_pass",
+                     "peak_source": peak_kind,
+                     "kernel_ms": kin_ms / kin_n, "bytes_per_launch": bytes_alg},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches * args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -162,6 +162,14 @@ int dvm_load(dvm_handle* h, const void* buf, size_t bytes);
 /* Kernel launches enqueued by one time step (the captured graph's nodes). */
 int dvm_launches_per_step(dvm_handle* h, int* launches);
 
+/* Kinetic-pass timing.  Between dvm_profile_begin and dvm_profile_end the
+ * steps are enqueued launch by launch (not through the graph) with a pair of
+ * CUDA events recorded on the handle's stream around every kinetic-pass
+ * launch.  dvm_profile_end synchronises the stream and returns the summed
+ * kinetic-pass time in milliseconds and the number of launches timed. */
+int dvm_profile_begin(dvm_handle* h);
+int dvm_profile_end(dvm_handle* h, double* kinetic_ms, int* launches);
+
 #ifdef __cplusplus
 }
 #endif

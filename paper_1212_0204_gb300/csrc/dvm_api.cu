@@ -32,6 +32,9 @@ struct dvm_handle {
   bool state_set = false;
   bool all_free = false;           // every lambda == 1 (tau = inf)
   int launches = 0;
+  bool profiling = false;          // bracket each kinetic pass with events
+  std::vector<cudaEvent_t> ev0, ev1;
+  int nprof = 0;
 };
 
 namespace {
@@ -204,8 +207,9 @@ void bind(dvm_handle* h, char* base, const Layout& L) {
   h->offs = (long long*)(base + L.offs);
 }
 
-// Kernels of one time step, in order.
-int enqueue_step(dvm_handle* h, cudaStream_t s) {
+// Kernels of one time step, in order; e0/e1 (optional) bracket the kinetic pass.
+int enqueue_step(dvm_handle* h, cudaStream_t s, cudaEvent_t e0 = nullptr,
+                 cudaEvent_t e1 = nullptr) {
   const Geom& g = h->g;
   int n = 0;
   if (g.scheme != DVM_FKS && !h->all_free) {
@@ -217,7 +221,9 @@ int enqueue_step(dvm_handle* h, cudaStream_t s) {
     launch_ghost(g, h->p, s);
     ++n;
   }
+  if (e0) cudaEventRecord(e0, s);
   launch_kinetic_pass(g, h->p, s);
+  if (e1) cudaEventRecord(e1, s);
   launch_finalize(g, h->p, s);
   n += 2;
   h->launches = n;
@@ -393,6 +399,8 @@ void dvm_destroy(dvm_handle* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   drop_graph(h);
+  for (cudaEvent_t e : h->ev0) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev1) cudaEventDestroy(e);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->pinned_status) cudaFreeHost(h->pinned_status);
   if (h->own_ws && h->ws) cudaFree(h->ws);
@@ -446,6 +454,20 @@ int dvm_step_async(dvm_handle* h, int nsteps) {
   if (rc) return rc;
   if (!h->state_set) return fail(h, DVM_ERR_STATE, "step before a state was set");
   if (nsteps < 0) return fail(h, DVM_ERR_ARG, "negative step count");
+  if (h->profiling) {
+    for (int i = 0; i < nsteps; ++i) {
+      if (h->nprof >= (int)h->ev0.size()) {
+        cudaEvent_t a, b;
+        if ((rc = cuda_check(h, cudaEventCreate(&a), "event"))) return rc;
+        if ((rc = cuda_check(h, cudaEventCreate(&b), "event"))) return rc;
+        h->ev0.push_back(a);
+        h->ev1.push_back(b);
+      }
+      if ((rc = enqueue_step(h, h->stream, h->ev0[h->nprof], h->ev1[h->nprof]))) return rc;
+      ++h->nprof;
+    }
+    return 0;
+  }
   if ((rc = ensure_graph(h))) return rc;
   for (int i = 0; i < nsteps; ++i) {
     if (h->exec) {
@@ -598,6 +620,31 @@ int dvm_load(dvm_handle* h, const void* buf, size_t bytes) {
   rc |= cuda_check(h, cudaMemcpyAsync(h->p.step, &hd.step, 8, cudaMemcpyHostToDevice, s), "copy");
   rc |= cuda_check(h, cudaStreamSynchronize(s), "sync");
   return rc ? h->status : 0;
+}
+
+int dvm_profile_begin(dvm_handle* h) {
+  int rc = ready(h);
+  if (rc) return rc;
+  h->profiling = true;
+  h->nprof = 0;
+  return 0;
+}
+
+int dvm_profile_end(dvm_handle* h, double* kinetic_ms, int* launches) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!h->profiling) return fail(h, DVM_ERR_STATE, "profiling was not started");
+  h->profiling = false;
+  if ((rc = cuda_check(h, cudaStreamSynchronize(h->stream), "sync"))) return rc;
+  double total = 0.0;
+  for (int i = 0; i < h->nprof; ++i) {
+    float ms = 0.f;
+    if ((rc = cuda_check(h, cudaEventElapsedTime(&ms, h->ev0[i], h->ev1[i]), "elapsed"))) return rc;
+    total += ms;
+  }
+  if (kinetic_ms) *kinetic_ms = total;
+  if (launches) *launches = h->nprof;
+  return 0;
 }
 
 int dvm_launches_per_step(dvm_handle* h, int* launches) {

@@ -27,7 +27,7 @@ EXPORTS = [
     "dvm_workspace_bytes", "dvm_create", "dvm_destroy", "dvm_set_stream", "dvm_last_error",
     "dvm_set_state_moments", "dvm_set_state_primitive", "dvm_step", "dvm_step_async",
     "dvm_sync_status", "dvm_moments", "dvm_get_f", "dvm_last_parts", "dvm_info", "dvm_offsets",
-    "dvm_save", "dvm_load", "dvm_launches_per_step",
+    "dvm_save", "dvm_load", "dvm_launches_per_step", "dvm_profile_begin", "dvm_profile_end",
 ]
 
 
@@ -84,6 +84,8 @@ def lib():
         L.dvm_save.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
         L.dvm_load.argtypes = [vp, vp, C.c_size_t]
         L.dvm_launches_per_step.argtypes = [vp, C.POINTER(C.c_int)]
+        L.dvm_profile_begin.argtypes = [vp]
+        L.dvm_profile_end.argtypes = [vp, dp, C.POINTER(C.c_int)]
         _lib = L
     return _lib
 
@@ -186,9 +188,10 @@ class Solver:
     # --------------------------------------------------------------- state
     def set_moments(self, U):
         t = self._torch
-        if isinstance(U, t.Tensor) and U.is_cuda:
-            U = U.to(t.float64).contiguous()
-            self._check(lib().dvm_set_state_moments(self._h, C.c_void_p(U.data_ptr()), 1))
+        if isinstance(U, t.Tensor):
+            assert U.dtype == t.float64 and U.is_contiguous()
+            self._check(lib().dvm_set_state_moments(self._h, C.c_void_p(U.data_ptr()),
+                                                    1 if U.is_cuda else 0))
         else:
             a = np.ascontiguousarray(U, dtype=np.float64).reshape(self.nm, self.nc)
             self._check(lib().dvm_set_state_moments(self._h, a.ctypes.data_as(C.c_void_p), 0))
@@ -210,8 +213,10 @@ class Solver:
     # ----------------------------------------------------------- read-back
     def moments(self, out=None):
         t = self._torch
-        if out is not None and isinstance(out, t.Tensor) and out.is_cuda:
-            self._check(lib().dvm_moments(self._h, C.c_void_p(out.data_ptr()), 1))
+        if out is not None and isinstance(out, t.Tensor):
+            assert out.dtype == t.float64 and out.is_contiguous()
+            self._check(lib().dvm_moments(self._h, C.c_void_p(out.data_ptr()),
+                                          1 if out.is_cuda else 0))
             return out
         a = np.zeros((self.nm, self.nc))
         self._check(lib().dvm_moments(self._h, a.ctypes.data_as(C.c_void_p), 0))
@@ -252,6 +257,15 @@ class Solver:
     def load(self, blob: bytes):
         buf = C.create_string_buffer(blob, len(blob))
         self._check(lib().dvm_load(self._h, buf, len(blob)))
+
+    def profile_begin(self):
+        self._check(lib().dvm_profile_begin(self._h))
+
+    def profile_end(self):
+        """(summed kinetic-pass milliseconds, launches timed) since profile_begin."""
+        ms, n = C.c_double(), C.c_int()
+        self._check(lib().dvm_profile_end(self._h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
 
     def launches_per_step(self) -> int:
         n = C.c_int()
