@@ -45,8 +45,13 @@ typedef enum {
   DVM_ERR_NONPHYSICAL = -5, /* rho <= 0 or theta <= 0 in some cell */
   DVM_ERR_TIMEOUT = -6,     /* a bounded device-side wait gave up */
   DVM_ERR_STATE = -7,       /* call out of order (e.g. step before a state is set) */
-  DVM_ERR_CFL = -8          /* Euler sub-steps needed exceed the launch cap */
+  DVM_ERR_CFL = -8,         /* Euler sub-steps needed exceed the launch cap */
+  DVM_ERR_TOO_LARGE = -9    /* problem larger than the fixed scratch of
+                               dvm_equilibrium_noalloc */
 } dvm_status;
+
+/* Size of the fixed device scratch array used by dvm_equilibrium_noalloc. */
+#define DVM_NOALLOC_SCRATCH_BYTES (8u << 20)
 
 typedef enum { DVM_BC_PERIODIC = 0, DVM_BC_OUTFLOW = 1 } dvm_bc;
 typedef enum { DVM_FKS = 0, DVM_HOFKS = 1, DVM_HOFKS_UNLIMITED = 2 } dvm_scheme;
@@ -169,6 +174,36 @@ int dvm_launches_per_step(dvm_handle* h, int* launches);
  * kinetic-pass time in milliseconds and the number of launches timed. */
 int dvm_profile_begin(dvm_handle* h);
 int dvm_profile_end(dvm_handle* h, double* kinetic_ms, int* launches);
+
+/* Allocation-free equilibrium.  The paper has no counterpart to this entry
+ * point: it exists for callers that cannot allocate device memory (a program
+ * that runs within a fixed device-memory budget set up in advance, or a host
+ * thread that must not enter the CUDA allocator, e.g. while other threads
+ * capture graphs).  It computes the same f = E[U] as the initial state built
+ * by dvm_set_state_moments (see dvm_get_f at step 0), with no handle and no
+ * workspace: its scratch (a status word, (C C^T)^{-1} and the per-cell
+ * equilibrium parameters) is a static device array of
+ * DVM_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps until
+ * the process exits.  It calls no cudaMalloc or cudaFree and no allocating
+ * library routine.
+ *   cfg:    grid and velocity set (tau, scheme, precision and boundaries are
+ *           ignored; the output is FP64).
+ *   U:      device pointer, (d+2) x N_c FP64 moments, caller-owned.
+ *   f:      device pointer, N_v x N_c FP64 output (velocity-major, cell
+ *           positions), caller-owned.
+ *   stream: cudaStream_t or NULL; the call synchronises it before returning.
+ * Size limit: 256 + 8 N_c (3d + 8) bytes must fit in the scratch, i.e. at most
+ * 61679 cells in 3D, 74896 in 2D and 95322 in 1D; larger problems return
+ * DVM_ERR_TOO_LARGE without launching anything.  Returns DVM_ERR_NONPHYSICAL
+ * or DVM_ERR_NONFINITE for bad moments, DVM_ERR_CUDA if a CUDA call fails.
+ * The first call on each device looks up the device address of the scratch
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one scratch array, which
+ * keeps the last call's contents; calls that overlap on the GPU (different
+ * streams or host threads at once) race on it and must be serialised by the
+ * caller. */
+int dvm_equilibrium_noalloc(const dvm_config* cfg, const double* U, double* f,
+                            void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -60,6 +60,10 @@ size_t elem_size(int precision) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+}  // namespace
+
+namespace dvm {
+
 // Validate cfg and fill the geometry.  Returns 0 or DVM_ERR_ARG with msg.
 int make_geom(const dvm_config* cfg, Geom* g, std::string* msg) {
   if (!cfg) { *msg = "null config"; return DVM_ERR_ARG; }
@@ -112,6 +116,10 @@ int make_geom(const dvm_config* cfg, Geom* g, std::string* msg) {
   return 0;
 }
 
+}  // namespace dvm
+
+namespace {
+
 struct Layout {
   size_t F, ghost, U, lam, W0, W1, acc, prm, eqp, UM, Us, A, small, offs, total;
 };
@@ -140,6 +148,10 @@ Layout layout(const Geom& g) {
   L.total = off;
   return L;
 }
+
+}  // namespace
+
+namespace dvm {
 
 // (C C^T)^{-1}, C with rows m_k dv^d, by Gauss-Jordan elimination with
 // partial pivoting.
@@ -182,6 +194,10 @@ int invert_moment_matrix(const Geom& g, double* A) {
     for (int j = 0; j < nm; ++j) A[i * nm + j] = M[i][nm + j];
   return 0;
 }
+
+}  // namespace dvm
+
+namespace {
 
 void bind(dvm_handle* h, char* base, const Layout& L) {
   DevPtrs& p = h->p;

@@ -4,6 +4,8 @@
 // the O(N_c N_v) work lives in dvm_kinetic.cu.
 #include <math.h>
 
+#include <mutex>
+
 #include "dvm_internal.cuh"
 
 namespace dvm {
@@ -521,3 +523,87 @@ void launch_offsets(const Geom& g, long long n, long long* out, int width, cudaS
 }
 
 }  // namespace dvm
+
+// ---------------------------------------------------------------------------
+// Allocation-free equilibrium (dvm_equilibrium_noalloc in dvm.h).
+//
+// For callers that may not allocate device memory (code inside a fixed
+// memory budget, or a host thread that must not call into the allocator):
+// the per-cell scratch of the f^0 = E[U] initialisation -- the status word,
+// (C C^T)^{-1} and the FP64 equilibrium parameters of every cell -- lives in
+// this file-scope device array instead of a workspace.  Every GPU that loads
+// the library holds it until the process exits.  Host code must not use the
+// symbol itself as a device address: its device address is looked up once
+// per device with cudaGetSymbolAddress.
+namespace dvm {
+namespace {
+
+constexpr size_t kNoAllocBytes = DVM_NOALLOC_SCRATCH_BYTES;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[256] = {};
+
+// Device address of the scratch array on the current device (looked up on the
+// first call per device).
+cudaError_t noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace dvm
+
+extern "C" int dvm_equilibrium_noalloc(const dvm_config* cfg, const double* U, double* f,
+                                       void* cuda_stream) {
+  using namespace dvm;
+  Geom g;
+  std::string msg;
+  if (make_geom(cfg, &g, &msg) != 0 || !U || !f) return DVM_ERR_ARG;
+  g.precision = DVM_F64;  // FP64 output, FP64 parameters
+  // scratch layout: [0, 256) status word and (C C^T)^{-1}; then the
+  // equilibrium parameters (prm_rows x Nc); then Nc doubles read as lambda
+  const size_t nc = (size_t)g.nc;
+  const size_t need = 256 + 8 * (size_t)prm_rows(g.d) * nc + 8 * nc;
+  if (need > kNoAllocBytes) return DVM_ERR_TOO_LARGE;
+  double A[kMaxM * kMaxM];
+  if (invert_moment_matrix(g, A) != 0) return DVM_ERR_ARG;
+  void* base = nullptr;
+  if (noalloc_scratch(&base) != cudaSuccess) return DVM_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  DevPtrs p;
+  memset(&p, 0, sizeof p);
+  char* b = (char*)base;
+  p.status = (int*)b;
+  p.A = (double*)(b + 64);
+  p.eqp = (double*)(b + 256);
+  p.lam = p.eqp + (size_t)prm_rows(g.d) * nc;
+  p.U = const_cast<double*>(U);
+  p.F = f;
+  // the status word must start at zero; everything else is written before it
+  // is read within this call
+  if (cudaMemsetAsync(p.status, 0, sizeof(int), s) != cudaSuccess ||
+      cudaMemcpyAsync(p.A, A, sizeof(double) * g.nm * g.nm, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemsetAsync(p.lam, 0, 8 * nc, s) != cudaSuccess)
+    return DVM_ERR_CUDA;
+  launch_cell_params(g, p, 0, 1, s);
+  launch_init_f(g, p, s);
+  int status = 0;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&status, p.status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return DVM_ERR_CUDA;
+  return status;
+}

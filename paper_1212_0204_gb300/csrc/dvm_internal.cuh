@@ -124,6 +124,10 @@ template <> struct StoreT<__nv_bfloat16> {
   __device__ static void store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
+// dvm_api.cu
+int make_geom(const dvm_config* cfg, Geom* g, std::string* msg);
+int invert_moment_matrix(const Geom& g, double* A);
+
 // ------------------------------------------------------- launch wrappers
 // dvm_cells.cu
 void launch_prim_to_cons(const Geom& g, const double* rho, const double* u, const double* T,

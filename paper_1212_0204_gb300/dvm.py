@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libdvm.so")
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_STATE, ERR_CFL = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
+ERR_TOO_LARGE = -9
 PERIODIC, OUTFLOW = 0, 1
 FKS, HOFKS, HOFKS_UNLIMITED = 0, 1, 2
 F64, F32, BF16S = 0, 1, 2
@@ -28,6 +29,7 @@ EXPORTS = [
     "dvm_set_state_moments", "dvm_set_state_primitive", "dvm_step", "dvm_step_async",
     "dvm_sync_status", "dvm_moments", "dvm_get_f", "dvm_last_parts", "dvm_info", "dvm_offsets",
     "dvm_save", "dvm_load", "dvm_launches_per_step", "dvm_profile_begin", "dvm_profile_end",
+    "dvm_equilibrium_noalloc",
 ]
 
 
@@ -86,6 +88,7 @@ def lib():
         L.dvm_launches_per_step.argtypes = [vp, C.POINTER(C.c_int)]
         L.dvm_profile_begin.argtypes = [vp]
         L.dvm_profile_end.argtypes = [vp, dp, C.POINTER(C.c_int)]
+        L.dvm_equilibrium_noalloc.argtypes = [C.POINTER(_Config), vp, vp, vp]
         _lib = L
     return _lib
 
@@ -129,6 +132,16 @@ def config_from_case(case, precision=F64, scheme=None, subcycles=None):
                        tau=float(tau) if field is None else 0.0, tau_field=field,
                        scheme=case.scheme if scheme is None else scheme, precision=precision,
                        subcycles=case.subcycles if subcycles is None else subcycles)
+
+
+def equilibrium_noalloc(cfg, U, f, stream=None) -> int:
+    """f = E[U] through the allocation-free entry point; U and f are CUDA tensors
+    (FP64, contiguous).  Returns the status code (0 on success)."""
+    import torch
+    assert U.is_cuda and f.is_cuda and U.dtype == torch.float64 and f.dtype == torch.float64
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return lib().dvm_equilibrium_noalloc(C.byref(cfg), C.c_void_p(U.data_ptr()),
+                                         C.c_void_p(f.data_ptr()), C.c_void_p(s.cuda_stream))
 
 
 def workspace_bytes(cfg) -> int:
