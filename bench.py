@@ -228,12 +228,21 @@ def main():
     ap.add_argument("--workload", default="quadrant_2d", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cells", type=int, default=None,
+                    help="override the cells per dimension (small profiling captures)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     make, prec = WORKLOADS[args.workload]
     case = make()
+    if args.cells:
+        import dataclasses
+        kw = {"n": args.cells} if case.d > 1 else {"nx": args.cells}
+        fn = {"quadrant_2d": W.quadrant_2d, "density_wave_3d": W.density_wave_3d,
+              "sod_1d": W.sod_1d}[case.name]
+        small = fn(**kw, nv=case.nv[0], tau=case.tau, steps=case.steps, dv=case.dv)
+        case = dataclasses.replace(small, name=case.name)
     if args.steps is None:
         args.steps = case.steps
     args.warmup = max(3, args.warmup)

@@ -37,6 +37,9 @@ def _stale(target: str, deps: list[str]) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
+    """Compile every csrc/*.cu for sm_103a and link libdvm.so.  Extra nvcc flags may
+    come from ``extra`` or the DVM_NVCC_EXTRA environment variable (space separated)."""
+    extra = list(extra or []) + os.environ.get("DVM_NVCC_EXTRA", "").split()
     os.makedirs(OBJ, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "dvm.h"))

@@ -121,7 +121,7 @@ int make_geom(const dvm_config* cfg, Geom* g, std::string* msg) {
 namespace {
 
 struct Layout {
-  size_t F, ghost, U, lam, W0, W1, acc, prm, eqp, UM, Us, A, small, offs, total;
+  size_t F, ghost, U, lam, W0, W1, acc, prm, eqp, UE, UM, Us, A, small, offs, total;
 };
 
 Layout layout(const Geom& g) {
@@ -140,6 +140,7 @@ Layout layout(const Geom& g) {
   L.acc = take(8 * (size_t)g.nsplit * 2 * nm * nc);
   L.prm = take(tc * (size_t)prm_rows(g.d) * nc);
   L.eqp = take(8 * (size_t)prm_rows(g.d) * nc);
+  L.UE = take(8 * nm * nc);
   L.UM = take(8 * nm * nc);
   L.Us = take(8 * nm * nc);
   L.A = take(8 * kMaxM * kMaxM);
@@ -205,11 +206,12 @@ void bind(dvm_handle* h, char* base, const Layout& L) {
   p.ghost = h->g.ghost_mode ? base + L.ghost : nullptr;
   p.U = (double*)(base + L.U);
   p.lam = (double*)(base + L.lam);
-  p.W0 = (double*)(base + L.W0);
-  p.W1 = (double*)(base + L.W1);
+  p.W0 = base + L.W0;
+  p.W1 = base + L.W1;
   p.acc = (double*)(base + L.acc);
   p.prm = base + L.prm;
   p.eqp = (double*)(base + L.eqp);
+  p.UE = (double*)(base + L.UE);
   p.UM = (double*)(base + L.UM);
   p.Us = (double*)(base + L.Us);
   p.A = (double*)(base + L.A);
@@ -220,6 +222,9 @@ void bind(dvm_handle* h, char* base, const Layout& L) {
   p.msub = (int*)(sm + 72);
   p.status = (int*)(sm + 76);
   p.counter = (unsigned int*)(sm + 80);
+  p.gbar = (unsigned int*)(sm + 96);                  // 2 unsigned
+  p.mlast = (int*)(sm + 104);
+  p.alpha_prev = (double*)(sm + 112);                 // 3 doubles
   h->offs = (long long*)(base + L.offs);
 }
 
@@ -228,10 +233,10 @@ int enqueue_step(dvm_handle* h, cudaStream_t s, cudaEvent_t e0 = nullptr,
                  cudaEvent_t e1 = nullptr) {
   const Geom& g = h->g;
   int n = 0;
-  if (g.scheme != DVM_FKS && !h->all_free) {
-    launch_alpha(g, h->p, s);
+  if (g.scheme != DVM_FKS && !g.skip_euler) {
+    const int rc = cuda_check(h, launch_euler(g, h->p, s), "Euler launch");
+    if (rc) return rc;
     ++n;
-    for (int i = 0; i < g.m_cap; ++i, ++n) launch_muscl(g, h->p, i, s);
   }
   if (g.ghost_mode) {
     launch_ghost(g, h->p, s);
@@ -299,31 +304,16 @@ int init_from_moments(dvm_handle* h) {
   if ((rc = cuda_check(h, cudaMemsetAsync(h->p.counter, 0, sizeof(unsigned), s), "memset"))) return rc;
   if ((rc = cuda_check(h, cudaMemsetAsync(h->p.alpha, 0, 3 * sizeof(double), s), "memset"))) return rc;
   if ((rc = cuda_check(h, cudaMemsetAsync(h->p.msub, 0, sizeof(int), s), "memset"))) return rc;
+  if ((rc = cuda_check(h, cudaMemsetAsync(h->p.mlast, 0, sizeof(int), s), "memset"))) return rc;
+  if ((rc = cuda_check(h, cudaMemsetAsync(h->p.alpha_prev, 0, 3 * sizeof(double), s), "memset"))) return rc;
+  if ((rc = cuda_check(h, cudaMemsetAsync(h->p.gbar, 0, 2 * sizeof(unsigned), s), "memset"))) return rc;
   launch_cell_params(g, h->p, 0, 1, s);
   launch_init_f(g, h->p, s);
   launch_cell_params(g, h->p, 1, 1, s);
+  // alpha, W = (1 - lambda) U^0 and the sub-step count of the first step
+  if (g.scheme != DVM_FKS) launch_alpha(g, h->p, s);
   if ((rc = cuda_check(h, cudaGetLastError(), "init launch"))) return rc;
   if ((rc = sync_status(h))) return rc;
-  int cap = g.m_cap;
-  if (g.scheme != DVM_FKS && h->all_free) {
-    // free transport: U_E = 0 lives in W0 (msub = 0) and no Euler launches
-    cudaMemsetAsync(h->p.W0, 0, sizeof(double) * g.nm * g.nc, s);
-  } else if (g.scheme != DVM_FKS && g.forced_sub == 0) {
-    // launch cap from the sub-steps the initial state needs
-    Geom probe = g;
-    probe.m_cap = 1 << 30;
-    launch_alpha(probe, h->p, s);
-    int m0 = 0;
-    if ((rc = cuda_check(h, cudaMemcpyAsync(h->pinned_status, h->p.msub, sizeof(int), cudaMemcpyDeviceToHost, s), "copy"))) return rc;
-    if ((rc = cuda_check(h, cudaStreamSynchronize(s), "sync"))) return rc;
-    m0 = *h->pinned_status;
-    cap = h->cfg.max_subcycles > 0 ? h->cfg.max_subcycles : 2 * m0 + 4;
-    if (cap < 8) cap = 8;
-    cudaMemsetAsync(h->p.msub, 0, sizeof(int), s);
-  }
-  if (cap != h->g.m_cap) drop_graph(h);
-  h->g.m_cap = cap;
-  if ((rc = cuda_check(h, cudaStreamSynchronize(s), "sync"))) return rc;
   h->state_set = true;
   return 0;
 }
@@ -388,6 +378,7 @@ int dvm_create(const dvm_config* cfg, void* workspace, void* cuda_stream, dvm_ha
   }
   double A[kMaxM * kMaxM];
   if (invert_moment_matrix(h->g, A)) { dvm_destroy(h); return DVM_ERR_ARG; }
+  kinetic_pass_prepare(h->g);
   std::vector<double> lam((size_t)h->g.nc);
   bool all_free = true;
   for (long long c = 0; c < h->g.nc; ++c) {
@@ -397,6 +388,9 @@ int dvm_create(const dvm_config* cfg, void* workspace, void* cuda_stream, dvm_ha
     all_free &= lam[c] == 1.0;
   }
   h->all_free = all_free;
+  h->g.skip_euler = all_free ? 1 : 0;
+  h->g.euler_blocks = euler_blocks(h->g);
+  h->g.m_cap = cfg->max_subcycles > 0 ? cfg->max_subcycles : (cfg->euler_subcycles > 0 ? cfg->euler_subcycles : 1 << 20);
   cudaStream_t s = h->stream;
   if (cudaMemsetAsync(h->ws, 0, L.total, s) != cudaSuccess ||
       cudaMemcpyAsync(h->p.A, A, sizeof(double) * h->g.nm * h->g.nm, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -451,7 +445,7 @@ int dvm_set_state_primitive(dvm_handle* h, const double* rho, const double* u, c
   const double *dr = rho, *du = u, *dT = T;
   if (!on_device) {
     // staging in the Euler buffers, which init overwrites anyway
-    tmp = h->p.W0;
+    tmp = (double*)h->p.W0;
     if (3 + h->g.d > 2 * h->g.nm) return fail(h, DVM_ERR_ARG, "staging too small");
     if ((rc = upload(h, tmp, rho, 8 * nc, 0))) return rc;
     if ((rc = upload(h, tmp + nc, u, 8 * nc * h->g.d, 0))) return rc;
@@ -544,7 +538,7 @@ int dvm_last_parts(dvm_handle* h, double* UE, double* UM, double* Ustar) {
   m = *h->pinned_status;
   const size_t b = sizeof(double) * h->g.nm * h->g.nc;
   cudaStream_t s = h->stream;
-  if (UE) rc |= cuda_check(h, cudaMemcpyAsync(UE, (m & 1) ? h->p.W1 : h->p.W0, b, cudaMemcpyDeviceToHost, s), "copy");
+  if (UE) rc |= cuda_check(h, cudaMemcpyAsync(UE, h->p.UE, b, cudaMemcpyDeviceToHost, s), "copy");
   if (UM) rc |= cuda_check(h, cudaMemcpyAsync(UM, h->p.UM, b, cudaMemcpyDeviceToHost, s), "copy");
   if (Ustar) rc |= cuda_check(h, cudaMemcpyAsync(Ustar, h->p.Us, b, cudaMemcpyDeviceToHost, s), "copy");
   if (rc) return h->status;
@@ -559,8 +553,8 @@ int dvm_info(dvm_handle* h, double* dt, long long* n, int* substeps, double* alp
   double a[3] = {0, 0, 0};
   cudaStream_t s = h->stream;
   rc |= cuda_check(h, cudaMemcpyAsync(&step, h->p.step, sizeof step, cudaMemcpyDeviceToHost, s), "copy");
-  rc |= cuda_check(h, cudaMemcpyAsync(&m, h->p.msub, sizeof m, cudaMemcpyDeviceToHost, s), "copy");
-  rc |= cuda_check(h, cudaMemcpyAsync(a, h->p.alpha, sizeof a, cudaMemcpyDeviceToHost, s), "copy");
+  rc |= cuda_check(h, cudaMemcpyAsync(&m, h->p.mlast, sizeof m, cudaMemcpyDeviceToHost, s), "copy");
+  rc |= cuda_check(h, cudaMemcpyAsync(a, h->p.alpha_prev, sizeof a, cudaMemcpyDeviceToHost, s), "copy");
   rc |= cuda_check(h, cudaStreamSynchronize(s), "sync");
   if (rc) return h->status;
   if (dt) *dt = h->g.dt;
@@ -667,7 +661,7 @@ int dvm_launches_per_step(dvm_handle* h, int* launches) {
   if (!h || !launches) return DVM_ERR_ARG;
   if (!h->state_set) return fail(h, DVM_ERR_STATE, "no state yet");
   int n = 0;
-  if (h->g.scheme != DVM_FKS && !h->all_free) n += 1 + h->g.m_cap;
+  if (h->g.scheme != DVM_FKS && !h->g.skip_euler) n += 1;
   if (h->g.ghost_mode) n += 1;
   n += 2;
   *launches = n;

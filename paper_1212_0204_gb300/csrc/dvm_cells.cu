@@ -2,6 +2,13 @@
 // Maxwellian parameters, the MUSCL Euler solver, the alpha reduction, the
 // end-of-step update, initial data and read-back.  These touch O(N_c) data;
 // the O(N_c N_v) work lives in dvm_kinetic.cu.
+//
+// Precision: the FP64 build does everything in FP64.  In the FP32/BF16
+// builds (FP32 f) the per-cell work that feeds f is done in FP32 where FP64
+// buys nothing beyond f's own rounding -- Maxwellian samples, the Euler
+// fluxes and state, logarithms -- and in FP64 where moments are combined:
+// partial sums, U^{n+1} = U_* + U_E, U - C M[U], nu and mu.  GB300's FP64
+// rate is about 1/60 of its FP32 rate, so this split matters.
 #include <math.h>
 
 #include <mutex>
@@ -15,10 +22,11 @@ constexpr int kBlock = 256;
 
 inline unsigned blocks_for(long long n, int b = kBlock) { return (unsigned)((n + b - 1) / b); }
 
+template <int D>
 __device__ inline void cell_coords(const Geom& g, long long c, int x[3]) {
   x[0] = (int)(c % g.nx[0]);
-  x[1] = (int)((c / g.nx[0]) % g.nx[1]);
-  x[2] = (int)(c / ((long long)g.nx[0] * g.nx[1]));
+  x[1] = D > 1 ? (int)((c / g.nx[0]) % g.nx[1]) : 0;
+  x[2] = D > 2 ? (int)(c / ((long long)g.nx[0] * g.nx[1])) : 0;
 }
 
 __device__ inline long long cell_index(const Geom& g, const int x[3]) {
@@ -28,23 +36,24 @@ __device__ inline long long cell_index(const Geom& g, const int x[3]) {
 // Primitive variables (Eqs. Mo and E): rho, u, theta.  Written without
 // contractions so that the value matches a plain IEEE evaluation bit for bit
 // (alpha and the number of Euler sub-steps depend on it).
-__device__ inline void primitives(int d, const double* U, double& rho, double u[3],
-                                  double& theta) {
+template <int D>
+__device__ inline void primitives(const double* U, double& rho, double u[3], double& theta) {
   rho = U[0];
   double u2 = 0.0;
-  for (int i = 0; i < 3; ++i) u[i] = 0.0;
-  for (int i = 0; i < d; ++i) {
+  u[0] = u[1] = u[2] = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
     u[i] = __ddiv_rn(U[1 + i], rho);
     u2 = __dadd_rn(u2, __dmul_rn(u[i], u[i]));
   }
-  theta = __ddiv_rn(__dsub_rn(__ddiv_rn(__dmul_rn(2.0, U[d + 1]), rho), u2), (double)d);
+  theta = __ddiv_rn(__dsub_rn(__ddiv_rn(__dmul_rn(2.0, U[D + 1]), rho), u2), (double)D);
 }
 
 // Sums over one velocity axis of g(k) = exp(-(v_k - u)^2 / (2 theta)) times
-// 1, v_k, v_k^2.  The Gaussian is evaluated from its peak outwards with the
-// two-term recurrence g(k+1) = g(k) r_k, r_{k+1} = r_k q, q = exp(-dv^2/theta)
-// (ratios of consecutive Gaussian samples on a uniform grid), so that one axis
-// costs three exponentials.
+// 1, v_k, v_k^2, in FP64.  The Gaussian is evaluated from its peak outwards
+// with the recurrence g(k+1) = g(k) r_k, r_{k+1} = r_k q, q = exp(-dv^2/theta)
+// (ratios of consecutive Gaussian samples on a uniform grid): three
+// exponentials per axis instead of one per velocity.
 __device__ void gauss_axis_sums(int n, int kmin, double dv, double u, double theta, double& G0,
                                 double& G1, double& G2) {
   const double h = 0.5 / theta;
@@ -77,140 +86,198 @@ __device__ void gauss_axis_sums(int n, int kmin, double dv, double u, double the
   }
 }
 
+// Same sums with FP32 samples exp2(-(v - u)^2 log2(e) / (2 theta)) and FP32
+// accumulation, for the FP32-storage builds.
+__device__ void gauss_axis_sums_f32(int n, int kmin, float dv, float u, float theta, double& G0,
+                                    double& G1, double& G2) {
+  const float h2 = 0.72134752044448170f / theta;  // log2(e) / 2
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  for (int k = 0; k < n; ++k) {
+    const float v = (kmin + k) * dv;
+    const float dd = v - u;
+    const float gk = exp2f(-h2 * dd * dd);
+    s0 += gk;
+    s1 = fmaf(v, gk, s1);
+    s2 = fmaf(v * v, gk, s2);
+  }
+  G0 = s0;
+  G1 = s1;
+  G2 = s2;
+}
+
 // mu = (C C^T)^{-1} (U - C M[U]) of Eq. minimMax, with C M[U] from the
 // separable factors of the Maxwellian.  Returns 0 or an error code.
+template <int D, bool F64>
 __device__ int cell_mu(const Geom& g, const double* A, const double* Uc, double mu[kMaxM],
                        double& rho, double u[3], double& theta) {
-  const int d = g.d, nm = g.nm;
-  for (int i = 0; i < nm; ++i)
+  constexpr int NM = D + 2;
+#pragma unroll
+  for (int i = 0; i < NM; ++i)
     if (!isfinite(Uc[i])) return DVM_ERR_NONFINITE;
-  primitives(d, Uc, rho, u, theta);
+  primitives<D>(Uc, rho, u, theta);
   if (!(rho > 0.0) || !(theta > 0.0)) return DVM_ERR_NONPHYSICAL;
   double G0[3], G1[3], G2[3];
-  for (int i = 0; i < d; ++i) gauss_axis_sums(g.nv[i], g.kmin[i], g.dv, u[i], theta, G0[i], G1[i], G2[i]);
-  const double pref = g.w * rho * pow(2.0 * M_PI * theta, -0.5 * d);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    if (F64) gauss_axis_sums(g.nv[i], g.kmin[i], g.dv, u[i], theta, G0[i], G1[i], G2[i]);
+    else gauss_axis_sums_f32(g.nv[i], g.kmin[i], (float)g.dv, (float)u[i], (float)theta, G0[i], G1[i], G2[i]);
+  }
+  const double pref = F64 ? g.w * rho * pow(2.0 * M_PI * theta, -0.5 * D)
+                          : g.w * rho * (double)powf(6.283185307179586f * (float)theta, -0.5f * D);
   double CM[kMaxM];
   double all = 1.0;
-  for (int i = 0; i < d; ++i) all *= G0[i];
+#pragma unroll
+  for (int i = 0; i < D; ++i) all *= G0[i];
   CM[0] = pref * all;
   double e = 0.0;
-  for (int j = 0; j < d; ++j) {
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
     double other = 1.0;
-    for (int i = 0; i < d; ++i)
+#pragma unroll
+    for (int i = 0; i < D; ++i)
       if (i != j) other *= G0[i];
     CM[1 + j] = pref * G1[j] * other;
     e += G2[j] * other;
   }
-  CM[d + 1] = 0.5 * pref * e;
+  CM[D + 1] = 0.5 * pref * e;
   double r[kMaxM];
-  for (int i = 0; i < nm; ++i) r[i] = Uc[i] - CM[i];
-  for (int i = 0; i < nm; ++i) {
+#pragma unroll
+  for (int i = 0; i < NM; ++i) r[i] = Uc[i] - CM[i];
+#pragma unroll
+  for (int i = 0; i < NM; ++i) {
     double s = 0.0;
-    for (int j = 0; j < nm; ++j) s += A[i * nm + j] * r[j];
+#pragma unroll
+    for (int j = 0; j < NM; ++j) s += A[i * NM + j] * r[j];
     mu[i] = s;
   }
   return 0;
 }
 
 // Kinetic-pass parameters of one cell (row layout in dvm_internal.cuh).
-template <typename TC>
+template <typename TC, int D>
 __device__ void write_params(const Geom& g, TC* prm, long long c, double lam, double weight,
                              double rho, const double u[3], double theta, const double* nu,
                              const double* mu) {
-  const int d = g.d, nm = g.nm;
+  constexpr int NM = D + 2;
   const long long nc = g.nc;
-  const double L = log2(weight) + log2(rho) - 0.5 * d * log2(2.0 * M_PI * theta);
-  prm[row_lam() * nc + c] = (TC)lam;
-  prm[row_L() * nc + c] = (TC)L;
-  for (int i = 0; i < d; ++i) prm[row_u(i) * nc + c] = (TC)u[i];
-  prm[row_h(d) * nc + c] = (TC)(M_LOG2E * 0.5 / theta);
-  for (int i = 0; i < nm; ++i) {
-    prm[row_nu(d, i) * nc + c] = (TC)(nu ? g.w * nu[i] : 0.0);
-    prm[row_mu(d, i) * nc + c] = (TC)(weight * g.w * mu[i]);
+  TC L, h;
+  if (sizeof(TC) == 8) {
+    L = (TC)(log2(weight) + log2(rho) - 0.5 * D * log2(2.0 * M_PI * theta));
+    h = (TC)(M_LOG2E * 0.5 / theta);
+  } else {
+    L = (TC)(log2f((float)weight) + log2f((float)rho) - 0.5f * D * log2f(6.283185307179586f * (float)theta));
+    h = (TC)(0.72134752044448170f / (float)theta);
+  }
+  prm[prm_at(row_lam(), c, nc)] = (TC)lam;
+  prm[prm_at(row_L(), c, nc)] = L;
+#pragma unroll
+  for (int i = 0; i < D; ++i) prm[prm_at(row_u(i), c, nc)] = (TC)u[i];
+  prm[prm_at(row_h(D), c, nc)] = h;
+  // the energy row holds the coefficient of |v|^2 (half that of |v|^2 / 2)
+#pragma unroll
+  for (int i = 0; i < NM; ++i) {
+    const double e = i == NM - 1 ? 0.5 : 1.0;
+    prm[prm_at(row_nu(D, i), c, nc)] = (TC)(nu ? e * g.w * nu[i] : 0.0);
+    prm[prm_at(row_mu(D, i), c, nc)] = (TC)(e * weight * g.w * mu[i]);
   }
 }
 
-template <typename TC>
+template <typename TC, int D>
 __global__ void k_cell_params(Geom g, DevPtrs p, int mode, int initial) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= g.nc) return;
   double Uc[kMaxM], mu[kMaxM], rho, u[3], theta;
-  for (int i = 0; i < g.nm; ++i) Uc[i] = p.U[i * g.nc + c];
-  const int rc = cell_mu(g, p.A, Uc, mu, rho, u, theta);
+#pragma unroll
+  for (int i = 0; i < D + 2; ++i) Uc[i] = p.U[i * g.nc + c];
+  const double lam = p.lam[c];
+  if (mode == 0) {  // E[U] itself, in FP64, to build f^0
+    const int rc = cell_mu<D, true>(g, p.A, Uc, mu, rho, u, theta);
+    if (rc) {
+      set_status(p.status, rc);
+      return;
+    }
+    write_params<double, D>(g, p.eqp, c, lam, 1.0, rho, u, theta, nullptr, mu);
+    return;
+  }
+  const int rc = cell_mu<D, sizeof(TC) == 8>(g, p.A, Uc, mu, rho, u, theta);
   if (rc) {
     set_status(p.status, rc);
     return;
   }
-  const double lam = p.lam[c];
-  if (mode == 0) {  // E[U] itself, in FP64, to build f^0
-    write_params(g, p.eqp, c, lam, 1.0, rho, u, theta, nullptr, mu);
-    return;
-  }
   // FKS: f^0 carries no deferred equilibrium yet
   const double weight = (g.scheme == DVM_FKS && initial) ? 0.0 : 1.0 - lam;
-  write_params(g, (TC*)p.prm, c, lam, weight, rho, u, theta, nullptr, mu);
+  write_params<TC, D>(g, (TC*)p.prm, c, lam, weight, rho, u, theta, nullptr, mu);
 }
+
+template <typename TS> struct ComputeOf { typedef float type; };
+template <> struct ComputeOf<double> { typedef double type; };
 
 // f^0 = E[U^0] at every phase-space point, from the FP64 equilibrium
 // parameters of every cell.
-template <typename TS, typename TC>
+template <typename TS, int D>
 __global__ void k_init_f(Geom g, DevPtrs p) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= g.nc * g.nvel) return;
   const long long c = idx % g.nc, k = idx / g.nc;
-  const int d = g.d;
   const double* prm = p.eqp;
   const long long nc = g.nc;
-  int kk[3] = {(int)(k % g.nv[0]), (int)((k / g.nv[0]) % g.nv[1]),
-               (int)(k / ((long long)g.nv[0] * g.nv[1]))};
-  double q = 0.0, vv = 0.0, lin = (double)prm[row_mu(d, 0) * nc + c];
-  for (int i = 0; i < d; ++i) {
+  const int kk[3] = {(int)(k % g.nv[0]), (int)((k / g.nv[0]) % g.nv[1]),
+                     (int)(k / ((long long)g.nv[0] * g.nv[1]))};
+  double q = 0.0, vv = 0.0, lin = prm[prm_at(row_mu(D, 0), c, nc)];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
     const double v = (double)(g.kmin[i] + kk[i]) * g.dv;
-    const double du = v - (double)prm[row_u(i) * nc + c];
+    const double du = v - prm[prm_at(row_u(i), c, nc)];
     q += du * du;
     vv += v * v;
-    lin += (double)prm[row_mu(d, 1 + i) * nc + c] * v;
+    lin += prm[prm_at(row_mu(D, 1 + i), c, nc)] * v;
   }
-  lin += (double)prm[row_mu(d, d + 1) * nc + c] * 0.5 * vv;
-  const double f = exp2((double)prm[row_L() * nc + c] - (double)prm[row_h(d) * nc + c] * q) + lin;
-  StoreT<TS>::store((TS*)p.F + k * nc + c, (TC)f);
+  lin += prm[prm_at(row_mu(D, D + 1), c, nc)] * vv;
+  const double f = exp2(prm[prm_at(row_L(), c, nc)] - prm[prm_at(row_h(D), c, nc)] * q) + lin;
+  StoreT<TS>::store((TS*)p.F + k * nc + c, (typename ComputeOf<TS>::type)f);
 }
 
+template <int D>
 __global__ void k_prim_to_cons(Geom g, const double* rho, const double* u, const double* T,
                                double* U) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= g.nc) return;
-  const int d = g.d;
   const double r = rho[c];
   double ke = 0.0;
   U[c] = r;
-  for (int i = 0; i < d; ++i) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
     const double ui = u[i * g.nc + c];
     U[(1 + i) * g.nc + c] = r * ui;
     ke += ui * ui;
   }
-  U[(d + 1) * g.nc + c] = 0.5 * r * ke + 0.5 * d * r * T[c];
+  U[(D + 1) * g.nc + c] = 0.5 * r * ke + 0.5 * D * r * T[c];
 }
 
-// alpha_i = max_c |u_i| + sqrt(gamma theta) (the largest eigenvalue of the
-// Euler system along i, one value per step), W = (1 - lambda) U, and in the
-// last block the number of Euler sub-steps from Eq. Time2.
-__global__ void __launch_bounds__(kBlock) k_alpha(Geom g, DevPtrs p) {
+// ------------------------------------------------------------ alpha and m
+
+// alpha_i contribution of one cell: |u_i| + sqrt(gamma theta), gamma = 1 + 2/d
+// (largest eigenvalue of the Euler system along i), evaluated without
+// contractions like the primitive variables.
+template <int D>
+__device__ inline void alpha_of(const double* Uc, double a[3]) {
+  double rho, u[3], theta;
+  primitives<D>(Uc, rho, u, theta);
+  const double gamma = __dadd_rn(1.0, __ddiv_rn(2.0, (double)D));
+  const double cs = sqrt(__dmul_rn(gamma, theta));
+  a[0] = a[1] = a[2] = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) a[i] = (rho > 0.0 && theta > 0.0) ? __dadd_rn(fabs(u[i]), cs) : 0.0;
+}
+
+// Block max of alpha, atomically merged; the last block to finish turns the
+// three maxima into the number of Euler sub-steps (Eq. Time2:
+// dt_E <= dx / (2 sum_i alpha_i)) and resets the reduction.
+template <int D>
+__device__ void alpha_reduce_and_substeps(const Geom& g, const DevPtrs& p, const double a[3]) {
   __shared__ double red[3][kBlock / 32];
   __shared__ bool last;
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const int d = g.d, nm = g.nm;
-  double a[3] = {0.0, 0.0, 0.0};
-  if (c < g.nc) {
-    double Uc[kMaxM], rho, u[3], theta;
-    for (int i = 0; i < nm; ++i) Uc[i] = p.U[i * g.nc + c];
-    primitives(d, Uc, rho, u, theta);
-    const double gamma = __dadd_rn(1.0, __ddiv_rn(2.0, (double)d));
-    const double cs = sqrt(__dmul_rn(gamma, theta));
-    for (int i = 0; i < d; ++i) a[i] = (rho > 0.0 && theta > 0.0) ? __dadd_rn(fabs(u[i]), cs) : 0.0;
-    const double w = 1.0 - p.lam[c];
-    for (int i = 0; i < nm; ++i) p.W0[i * g.nc + c] = w * Uc[i];
-  }
+#pragma unroll
   for (int i = 0; i < 3; ++i) {
     double v = a[i];
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -229,10 +296,12 @@ __global__ void __launch_bounds__(kBlock) k_alpha(Geom g, DevPtrs p) {
   if (!last || threadIdx.x != 0) return;
   __threadfence();
   double asum = 0.0;
+  *p.mlast = *p.msub;
   for (int i = 0; i < 3; ++i) {
     const double ai = __longlong_as_double((long long)atomicExch(&p.alpha_bits[i], 0ull));
+    p.alpha_prev[i] = p.alpha[i];
     p.alpha[i] = ai;
-    if (i < d) asum = __dadd_rn(asum, ai);
+    if (i < D) asum = __dadd_rn(asum, ai);
   }
   int m;
   if (g.forced_sub > 0) {
@@ -250,22 +319,44 @@ __global__ void __launch_bounds__(kBlock) k_alpha(Geom g, DevPtrs p) {
   *p.counter = 0u;
 }
 
+// alpha, W = (1 - lambda) U and the sub-step count from the current moments
+// (used once after a state is set; afterwards the end-of-step kernel does it).
+template <typename TW, int D>
+__global__ void __launch_bounds__(kBlock) k_alpha(Geom g, DevPtrs p) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double a[3] = {0.0, 0.0, 0.0};
+  if (c < g.nc) {
+    double Uc[kMaxM];
+#pragma unroll
+    for (int i = 0; i < D + 2; ++i) Uc[i] = p.U[i * g.nc + c];
+    alpha_of<D>(Uc, a);
+    const double w = 1.0 - p.lam[c];
+#pragma unroll
+    for (int i = 0; i < D + 2; ++i) ((TW*)p.W0)[i * g.nc + c] = (TW)(w * Uc[i]);
+  }
+  alpha_reduce_and_substeps<D>(g, p, a);
+}
+
+// ---------------------------------------------------------------- MUSCL
+
 // Euler flux along dir (Eq. sys1), gamma = 1 + 2/d; zero density carries no
 // flux (only reached for lambda = 1, where W = 0).
-template <typename TF>
-__device__ inline void euler_flux(int d, const TF* U, int dir, TF* F) {
+template <typename TF, int D>
+__device__ inline void euler_flux(const TF* U, int dir, TF* F) {
   const TF rho = U[0];
   TF u[3] = {TF(0), TF(0), TF(0)}, ke = TF(0);
   if (rho != TF(0)) {
-    for (int j = 0; j < d; ++j) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
       u[j] = U[1 + j] / rho;
       ke += TF(0.5) * U[1 + j] * u[j];
     }
   }
-  const TF pr = (TF(2) / TF(d)) * (U[d + 1] - ke);
+  const TF pr = (TF(2) / TF(D)) * (U[D + 1] - ke);
   F[0] = U[1 + dir];
-  for (int j = 0; j < d; ++j) F[1 + j] = U[1 + j] * u[dir] + (j == dir ? pr : TF(0));
-  F[d + 1] = (U[d + 1] + pr) * u[dir];
+#pragma unroll
+  for (int j = 0; j < D; ++j) F[1 + j] = U[1 + j] * u[dir] + (j == dir ? pr : TF(0));
+  F[D + 1] = (U[D + 1] + pr) * u[dir];
 }
 
 // van Leer limited slope b phi(a / b), phi(chi) = (|chi| + chi) / (1 + chi),
@@ -277,45 +368,43 @@ __device__ inline TF slope(TF a, TF b) {
   return ab > TF(0) ? (ab + ab) / (a + b) : TF(0);
 }
 
-// One forward-Euler MUSCL sub-step (Eq. discmom), unsplit over directions.
-// Face fluxes are evaluated in TF; the state stays FP64.
-template <typename TF, bool LIMITED>
-__global__ void __launch_bounds__(kBlock) k_muscl(Geom g, DevPtrs p, int substep) {
-  const int m = *p.msub;
-  if (substep >= m) return;
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= g.nc) return;
-  const int d = g.d, nm = g.nm;
-  const double* src = (substep & 1) ? p.W1 : p.W0;
-  double* dst = (substep & 1) ? p.W0 : p.W1;
-  int x[3];
-  cell_coords(g, c, x);
-  double acc[kMaxM] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int dir = 0; dir < d; ++dir) {
-    TF Us[5][kMaxM], Fs[5][kMaxM];
+// Flux difference psi_{c+1/2} - psi_{c-1/2} of Eq. discmom for one cell, summed
+// over directions, from the five-cell stencils (loads bypass L1: the buffers
+// are rewritten by other blocks between the sub-steps of one launch).
+template <typename TF, bool LIMITED, int D>
+__device__ inline void muscl_cell(const Geom& g, const TF* __restrict__ src, const int x[3],
+                                  const double* alpha, double acc[kMaxM]) {
+  constexpr int NM = D + 2;
+#pragma unroll
+  for (int dir = 0; dir < D; ++dir) {
+    TF Us[5][NM], Fs[5][NM];
+#pragma unroll
     for (int o = -2; o <= 2; ++o) {
       int y[3] = {x[0], x[1], x[2]};
       const int n = g.nx[dir];
+      const int t = x[dir] + o;
       if (g.bc[dir] == DVM_BC_PERIODIC) {
-        y[dir] = wrap((long long)x[dir] + o, n);
+        y[dir] = (t < 0 || t >= n) ? wrap(t, n) : t;
       } else {
-        const int t = x[dir] + o;
         y[dir] = t < 0 ? 0 : (t >= n ? n - 1 : t);
       }
       const long long cc = cell_index(g, y);
-      for (int i = 0; i < nm; ++i) Us[o + 2][i] = (TF)src[i * g.nc + cc];
-      euler_flux<TF>(d, Us[o + 2], dir, Fs[o + 2]);
+#pragma unroll
+      for (int i = 0; i < NM; ++i) Us[o + 2][i] = __ldcg(src + i * g.nc + cc);
+      euler_flux<TF, D>(Us[o + 2], dir, Fs[o + 2]);
     }
-    const TF al = (TF)p.alpha[dir];
-    for (int i = 0; i < nm; ++i) {
+    const TF al = (TF)alpha[dir];
+#pragma unroll
+    for (int i = 0; i < NM; ++i) {
       TF Gp[5], Gm[5];
+#pragma unroll
       for (int s = 0; s < 5; ++s) {
         Gp[s] = Fs[s][i] + al * Us[s][i];
         Gm[s] = Fs[s][i] - al * Us[s][i];
       }
-      // face j+1/2 between cells (1, 2) and (2, 3) of the 5-cell stencil
       TF psi[2];
-      for (int f = 0; f < 2; ++f) {
+#pragma unroll
+      for (int f = 0; f < 2; ++f) {  // faces between stencil cells (1,2) and (2,3)
         const int j = 1 + f;
         const TF sp = slope<TF, LIMITED>(Gp[j] - Gp[j - 1], Gp[j + 1] - Gp[j]);
         const TF sm = slope<TF, LIMITED>(Gm[j + 1] - Gm[j], Gm[j + 2] - Gm[j + 1]);
@@ -325,8 +414,65 @@ __global__ void __launch_bounds__(kBlock) k_muscl(Geom g, DevPtrs p, int substep
       acc[i] += (double)psi[1] - (double)psi[0];
     }
   }
+}
+
+// Grid-wide barrier of the cooperative Euler launch: arrive on a counter, the
+// last block to arrive advances the generation word.  The wait is bounded
+// (2^31 SM clock cycles, about a second); on timeout the status word gets
+// DVM_ERR_TIMEOUT and false is returned so that the kernel can leave.
+__device__ bool grid_sync(unsigned* bar, int* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    int good = 1;
+    if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == gen) {
+        if (clock64() - t0 > (1LL << 31)) {
+          set_status(status, DVM_ERR_TIMEOUT);
+          good = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// All m MUSCL sub-steps of one kinetic step (Section 4.3.2, forward Euler,
+// unsplit over directions) in one cooperative launch: W_0 -> W_1 -> ... with
+// a grid barrier between sub-steps.  The result U_E is W_{m mod 2}.
+template <typename TF, bool LIMITED, int D>
+__global__ void __launch_bounds__(kBlock) k_euler(Geom g, DevPtrs p) {
+  constexpr int NM = D + 2;
+  const int m = *p.msub;
   const double k = (g.dt / m) / g.dx;
-  for (int i = 0; i < nm; ++i) dst[i * g.nc + c] = src[i * g.nc + c] - k * acc[i];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int s = 0; s < m; ++s) {
+    const TF* src = (const TF*)((s & 1) ? p.W1 : p.W0);
+    TF* dst = (TF*)((s & 1) ? p.W0 : p.W1);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.nc; c += stride) {
+      int x[3];
+      cell_coords<D>(g, c, x);
+      double acc[kMaxM] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      muscl_cell<TF, LIMITED, D>(g, src, x, p.alpha, acc);
+#pragma unroll
+      for (int i = 0; i < NM; ++i)
+        dst[i * g.nc + c] = (TF)((double)__ldcg(src + i * g.nc + c) - k * acc[i]);
+    }
+    if (s + 1 < m && !grid_sync(p.gbar, p.status)) return;
+  }
 }
 
 // Outflow: snapshot of the boundary pieces of every velocity before the
@@ -345,91 +491,110 @@ __global__ void k_ghost1d(Geom g, DevPtrs p) {
 }
 
 // End of a step: U^{n+1}, the HOFKS correction nu = A (U_E - U_M)
-// (Eq. minim_full), checks, and the parameters of the next pass.
-template <typename TC, int SCHEME>
-__global__ void k_finalize(Geom g, DevPtrs p) {
+// (Eq. minim_full), checks, the parameters of the next pass, and for HOFKS
+// alpha, W = (1 - lambda) U^{n+1} and the sub-step count of the next step.
+template <typename TC, typename TW, int SCHEME, int D>
+__global__ void __launch_bounds__(kBlock) k_finalize(Geom g, DevPtrs p) {
+  constexpr int NM = D + 2;
+  constexpr bool HO = SCHEME != DVM_FKS;
+  constexpr int NACC = HO ? 2 * NM : NM;
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c == 0) *p.step += 1;
-  if (c >= g.nc) return;
-  const int nm = g.nm;
   const long long nc = g.nc;
-  double Un[kMaxM], nu[kMaxM];
-  const bool hofks = SCHEME != DVM_FKS;
-  const int nacc = hofks ? 2 * nm : nm;
-  double sums[2 * kMaxM];
-  for (int j = 0; j < nacc; ++j) {
-    double s = 0.0;
-    for (int sp = 0; sp < g.nsplit; ++sp) s += p.acc[((long long)sp * 2 * nm + j) * nc + c];
-    sums[j] = g.w * s;
-  }
-  if (hofks) {
-    const double* UE = (*p.msub & 1) ? p.W1 : p.W0;
-    double r[kMaxM];
-    for (int i = 0; i < nm; ++i) {
-      const double ue = UE[i * nc + c];
-      r[i] = ue - sums[nm + i];
-      Un[i] = sums[i] + ue;
-      p.Us[i * nc + c] = sums[i];
-      p.UM[i * nc + c] = sums[nm + i];
-    }
-    for (int i = 0; i < nm; ++i) {
+  double a[3] = {0.0, 0.0, 0.0};
+  if (c < nc) {
+    double Un[kMaxM], nu[kMaxM];
+    double sums[2 * kMaxM];
+#pragma unroll
+    for (int j = 0; j < NACC; ++j) {
       double s = 0.0;
-      for (int j = 0; j < nm; ++j) s += p.A[i * nm + j] * r[j];
-      nu[i] = s;
+      for (int sp = 0; sp < g.nsplit; ++sp) s += p.acc[((long long)sp * 2 * NM + j) * nc + c];
+      sums[j] = g.w * s;
     }
-  } else {
-    for (int i = 0; i < nm; ++i) {
-      Un[i] = sums[i];
-      p.Us[i * nc + c] = sums[i];
+    if (HO) {
+      const TW* UE = (const TW*)((*p.msub & 1) ? p.W1 : p.W0);
+      double r[kMaxM];
+#pragma unroll
+      for (int i = 0; i < NM; ++i) {
+        const double ue = g.skip_euler ? 0.0 : (double)UE[i * nc + c];
+        r[i] = ue - sums[NM + i];
+        Un[i] = sums[i] + ue;
+        p.UE[i * nc + c] = ue;
+        p.Us[i * nc + c] = sums[i];
+        p.UM[i * nc + c] = sums[NM + i];
+      }
+#pragma unroll
+      for (int i = 0; i < NM; ++i) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < NM; ++j) s += p.A[i * NM + j] * r[j];
+        nu[i] = s;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < NM; ++i) {
+        Un[i] = sums[i];
+        p.Us[i * nc + c] = sums[i];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NM; ++i) p.U[i * nc + c] = Un[i];
+    double mu[kMaxM], rho, u[3], theta;
+    const int rc = cell_mu<D, sizeof(TC) == 8>(g, p.A, Un, mu, rho, u, theta);
+    if (rc) {
+      set_status(p.status, rc);
+    } else {
+      const double lam = p.lam[c];
+      write_params<TC, D>(g, (TC*)p.prm, c, lam, 1.0 - lam, rho, u, theta, HO ? nu : nullptr, mu);
+      if (HO) {
+        alpha_of<D>(Un, a);
+        const double w = 1.0 - lam;
+#pragma unroll
+        for (int i = 0; i < NM; ++i) ((TW*)p.W0)[i * nc + c] = (TW)(w * Un[i]);
+      }
     }
   }
-  for (int i = 0; i < nm; ++i) p.U[i * nc + c] = Un[i];
-  double mu[kMaxM], rho, u[3], theta;
-  const int rc = cell_mu(g, p.A, Un, mu, rho, u, theta);
-  if (rc) {
-    set_status(p.status, rc);
-    return;
-  }
-  const double lam = p.lam[c];
-  write_params(g, (TC*)p.prm, c, lam, 1.0 - lam, rho, u, theta, hofks ? nu : nullptr, mu);
+  if (HO) alpha_reduce_and_substeps<D>(g, p, a);
 }
 
 // f at the cell centres: stored piece value plus the deferred term.
-template <typename TS, typename TC>
+template <typename TS, typename TC, int D>
 __global__ void k_materialize(Geom g, DevPtrs p, double* out) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= g.nc * g.nvel) return;
   const long long c = idx % g.nc, k = idx / g.nc;
-  const int d = g.d;
   const long long n = *p.step, nc = g.nc;
   const TC* prm = (const TC*)p.prm;
-  int x[3], kk[3] = {(int)(k % g.nv[0]), (int)((k / g.nv[0]) % g.nv[1]),
+  int x[3];
+  const int kk[3] = {(int)(k % g.nv[0]), (int)((k / g.nv[0]) % g.nv[1]),
                      (int)(k / ((long long)g.nv[0] * g.nv[1]))};
-  cell_coords(g, c, x);
+  cell_coords<D>(g, c, x);
   int q[3] = {0, 0, 0};
   double v[3] = {0.0, 0.0, 0.0}, vv = 0.0;
-  for (int i = 0; i < d; ++i) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
     const long long kg = g.kmin[i] + kk[i];
     q[i] = wrap((long long)x[i] - transport_offset(kg, n, g.p), g.nx[i]);
     v[i] = (double)kg * g.dv;
     vv += v[i] * v[i];
   }
-  vv *= 0.5;
   const long long slot = cell_index(g, q);
   double f = (double)StoreT<TS>::load((const TS*)p.F + k * nc + slot);
   if (g.scheme == DVM_FKS) {
-    double qq = 0.0, lin = (double)prm[row_mu(d, 0) * nc + c];
-    for (int i = 0; i < d; ++i) {
-      const double du = v[i] - (double)prm[row_u(i) * nc + c];
+    double qq = 0.0, lin = (double)prm[prm_at(row_mu(D, 0), c, nc)];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const double du = v[i] - (double)prm[prm_at(row_u(i), c, nc)];
       qq += du * du;
-      lin += (double)prm[row_mu(d, 1 + i) * nc + c] * v[i];
+      lin += (double)prm[prm_at(row_mu(D, 1 + i), c, nc)] * v[i];
     }
-    lin += (double)prm[row_mu(d, d + 1) * nc + c] * vv;
-    f += exp2((double)prm[row_L() * nc + c] - (double)prm[row_h(d) * nc + c] * qq) + lin;
+    lin += (double)prm[prm_at(row_mu(D, D + 1), c, nc)] * vv;
+    f += exp2((double)prm[prm_at(row_L(), c, nc)] - (double)prm[prm_at(row_h(D), c, nc)] * qq) + lin;
   } else {
-    double lin = (double)prm[row_nu(d, 0) * nc + c];
-    for (int i = 0; i < d; ++i) lin += (double)prm[row_nu(d, 1 + i) * nc + c] * v[i];
-    lin += (double)prm[row_nu(d, d + 1) * nc + c] * vv;
+    double lin = (double)prm[prm_at(row_nu(D, 0), c, nc)];
+#pragma unroll
+    for (int i = 0; i < D; ++i) lin += (double)prm[prm_at(row_nu(D, 1 + i), c, nc)] * v[i];
+    lin += (double)prm[prm_at(row_nu(D, D + 1), c, nc)] * vv;
     f += lin;
   }
   out[k * nc + c] = f;
@@ -442,46 +607,102 @@ __global__ void k_offsets(Geom g, long long n, long long* out, int width) {
   out[i * width + k] = transport_offset(g.kmin[i] + k, n, g.p);
 }
 
+// Dispatch on the run-time dimension: CALL sees the constant DD.
+#define DVM_BY_DIM(g, CALL)    \
+  do {                         \
+    if ((g).d == 1) {          \
+      constexpr int DD = 1;    \
+      CALL;                    \
+    } else if ((g).d == 2) {   \
+      constexpr int DD = 2;    \
+      CALL;                    \
+    } else {                   \
+      constexpr int DD = 3;    \
+      CALL;                    \
+    }                          \
+  } while (0)
+
+template <typename TF, bool LIM, int D>
+cudaError_t launch_euler_t(const Geom& g, const DevPtrs& p, cudaStream_t s, bool prepare,
+                           int* blocks) {
+  if (prepare) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_euler<TF, LIM, D>, kBlock, 0);
+    const long long nb = (long long)sms * (per_sm < 1 ? 1 : per_sm);
+    const long long need = (g.nc + kBlock - 1) / kBlock;
+    *blocks = (int)(nb < need ? nb : need);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)g.euler_blocks);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_euler<TF, LIM, D>, g, p);
+}
+
+cudaError_t euler_dispatch(const Geom& g, const DevPtrs& p, cudaStream_t s, bool prepare,
+                           int* blocks) {
+  const bool lim = g.scheme == DVM_HOFKS;
+  cudaError_t e = cudaSuccess;
+  if (g.precision == DVM_F64) {
+    if (lim) DVM_BY_DIM(g, e = (launch_euler_t<double, true, DD>(g, p, s, prepare, blocks)));
+    else DVM_BY_DIM(g, e = (launch_euler_t<double, false, DD>(g, p, s, prepare, blocks)));
+  } else {
+    if (lim) DVM_BY_DIM(g, e = (launch_euler_t<float, true, DD>(g, p, s, prepare, blocks)));
+    else DVM_BY_DIM(g, e = (launch_euler_t<float, false, DD>(g, p, s, prepare, blocks)));
+  }
+  return e;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ launchers
 
 void launch_prim_to_cons(const Geom& g, const double* rho, const double* u, const double* T,
                          double* U, cudaStream_t s) {
-  k_prim_to_cons<<<blocks_for(g.nc), kBlock, 0, s>>>(g, rho, u, T, U);
+  DVM_BY_DIM(g, (k_prim_to_cons<DD><<<blocks_for(g.nc), kBlock, 0, s>>>(g, rho, u, T, U)));
 }
 
 void launch_cell_params(const Geom& g, const DevPtrs& p, int mode, int initial, cudaStream_t s) {
   if (g.precision == DVM_F64)
-    k_cell_params<double><<<blocks_for(g.nc), kBlock, 0, s>>>(g, p, mode, initial);
+    DVM_BY_DIM(g, (k_cell_params<double, DD><<<blocks_for(g.nc), kBlock, 0, s>>>(g, p, mode, initial)));
   else
-    k_cell_params<float><<<blocks_for(g.nc), kBlock, 0, s>>>(g, p, mode, initial);
+    DVM_BY_DIM(g, (k_cell_params<float, DD><<<blocks_for(g.nc), kBlock, 0, s>>>(g, p, mode, initial)));
 }
 
 void launch_init_f(const Geom& g, const DevPtrs& p, cudaStream_t s) {
   const unsigned nb = blocks_for(g.nc * g.nvel);
   if (g.precision == DVM_F64)
-    k_init_f<double, double><<<nb, kBlock, 0, s>>>(g, p);
+    DVM_BY_DIM(g, (k_init_f<double, DD><<<nb, kBlock, 0, s>>>(g, p)));
   else if (g.precision == DVM_F32)
-    k_init_f<float, float><<<nb, kBlock, 0, s>>>(g, p);
+    DVM_BY_DIM(g, (k_init_f<float, DD><<<nb, kBlock, 0, s>>>(g, p)));
   else
-    k_init_f<__nv_bfloat16, float><<<nb, kBlock, 0, s>>>(g, p);
+    DVM_BY_DIM(g, (k_init_f<__nv_bfloat16, DD><<<nb, kBlock, 0, s>>>(g, p)));
 }
 
 void launch_alpha(const Geom& g, const DevPtrs& p, cudaStream_t s) {
-  k_alpha<<<blocks_for(g.nc), kBlock, 0, s>>>(g, p);
+  if (g.precision == DVM_F64)
+    DVM_BY_DIM(g, (k_alpha<double, DD><<<blocks_for(g.nc), kBlock, 0, s>>>(g, p)));
+  else
+    DVM_BY_DIM(g, (k_alpha<float, DD><<<blocks_for(g.nc), kBlock, 0, s>>>(g, p)));
 }
 
-void launch_muscl(const Geom& g, const DevPtrs& p, int substep, cudaStream_t s) {
-  const bool lim = g.scheme == DVM_HOFKS;
-  const unsigned nb = blocks_for(g.nc);
-  if (g.precision == DVM_F64) {
-    if (lim) k_muscl<double, true><<<nb, kBlock, 0, s>>>(g, p, substep);
-    else k_muscl<double, false><<<nb, kBlock, 0, s>>>(g, p, substep);
-  } else {
-    if (lim) k_muscl<float, true><<<nb, kBlock, 0, s>>>(g, p, substep);
-    else k_muscl<float, false><<<nb, kBlock, 0, s>>>(g, p, substep);
-  }
+int euler_blocks(const Geom& g) {
+  int blocks = 1;
+  euler_dispatch(g, DevPtrs{}, nullptr, true, &blocks);
+  return blocks < 1 ? 1 : blocks;
+}
+
+cudaError_t launch_euler(const Geom& g, const DevPtrs& p, cudaStream_t s) {
+  return euler_dispatch(g, p, s, false, nullptr);
 }
 
 void launch_ghost(const Geom& g, const DevPtrs& p, cudaStream_t s) {
@@ -498,24 +719,27 @@ void launch_ghost(const Geom& g, const DevPtrs& p, cudaStream_t s) {
 
 void launch_finalize(const Geom& g, const DevPtrs& p, cudaStream_t s) {
   const unsigned nb = blocks_for(g.nc);
-  const bool f64 = g.precision == DVM_F64;
-  if (g.scheme == DVM_FKS) {
-    if (f64) k_finalize<double, DVM_FKS><<<nb, kBlock, 0, s>>>(g, p);
-    else k_finalize<float, DVM_FKS><<<nb, kBlock, 0, s>>>(g, p);
+  if (g.precision == DVM_F64) {
+    if (g.scheme == DVM_FKS)
+      DVM_BY_DIM(g, (k_finalize<double, double, DVM_FKS, DD><<<nb, kBlock, 0, s>>>(g, p)));
+    else
+      DVM_BY_DIM(g, (k_finalize<double, double, DVM_HOFKS, DD><<<nb, kBlock, 0, s>>>(g, p)));
   } else {
-    if (f64) k_finalize<double, DVM_HOFKS><<<nb, kBlock, 0, s>>>(g, p);
-    else k_finalize<float, DVM_HOFKS><<<nb, kBlock, 0, s>>>(g, p);
+    if (g.scheme == DVM_FKS)
+      DVM_BY_DIM(g, (k_finalize<float, float, DVM_FKS, DD><<<nb, kBlock, 0, s>>>(g, p)));
+    else
+      DVM_BY_DIM(g, (k_finalize<float, float, DVM_HOFKS, DD><<<nb, kBlock, 0, s>>>(g, p)));
   }
 }
 
 void launch_materialize(const Geom& g, const DevPtrs& p, double* out, cudaStream_t s) {
   const unsigned nb = blocks_for(g.nc * g.nvel);
   if (g.precision == DVM_F64)
-    k_materialize<double, double><<<nb, kBlock, 0, s>>>(g, p, out);
+    DVM_BY_DIM(g, (k_materialize<double, double, DD><<<nb, kBlock, 0, s>>>(g, p, out)));
   else if (g.precision == DVM_F32)
-    k_materialize<float, float><<<nb, kBlock, 0, s>>>(g, p, out);
+    DVM_BY_DIM(g, (k_materialize<float, float, DD><<<nb, kBlock, 0, s>>>(g, p, out)));
   else
-    k_materialize<__nv_bfloat16, float><<<nb, kBlock, 0, s>>>(g, p, out);
+    DVM_BY_DIM(g, (k_materialize<__nv_bfloat16, float, DD><<<nb, kBlock, 0, s>>>(g, p, out)));
 }
 
 void launch_offsets(const Geom& g, long long n, long long* out, int width, cudaStream_t s) {

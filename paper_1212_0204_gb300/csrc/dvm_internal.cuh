@@ -32,17 +32,24 @@ namespace dvm {
 constexpr int kMaxD = 3;
 constexpr int kMaxM = 5;      // d + 2
 constexpr int kMaxV1 = 256;   // velocities per dimension
-constexpr int kMaxNP = 3 + 3 + 2 * 5;
+constexpr int kMaxNP = 16;
 
-// Per-cell parameter rows (compute type), row r at prm[r * Nc + c]:
+// Per-cell parameter rows (compute type), grouped four rows per 16-byte
+// block: row r of cell c at prm[((r / 4) * Nc + c) * 4 + r % 4], so that one
+// vector load returns four rows of a cell.  Rows:
 //   0            lambda = exp(-dt / tau)
 //   1            L = log2(weight * rho / (2 pi theta)^{d/2})
 //   2 .. 1+d     u
 //   2+d          h = log2(e) / (2 theta)
 //   3+d ..       nu' = dv^d nu                      (d+2 rows)
 //   3+d+(d+2) .. mu'' = weight * dv^d mu            (d+2 rows)
+// (the last row of nu' and of mu'' holds the coefficient of |v|^2, i.e. half
+// the energy component, so that m_k . nu = nu0 + nu.v + nu_E |v|^2)
 // The Maxwellian of the cell is M_k = exp2(L - h |v_k - u|^2) / weight.
-__host__ __device__ inline int prm_rows(int d) { return 3 + d + 2 * (d + 2); }
+__host__ __device__ inline int prm_rows(int d) { return 4 * ((3 + d + 2 * (d + 2) + 3) / 4); }
+__host__ __device__ inline long long prm_at(int row, long long c, long long nc) {
+  return ((long long)(row >> 2) * nc + c) * 4 + (row & 3);
+}
 __host__ __device__ inline int row_lam() { return 0; }
 __host__ __device__ inline int row_L() { return 1; }
 __host__ __device__ inline int row_u(int i) { return 2 + i; }
@@ -66,6 +73,8 @@ struct Geom {
   int m_cap;          // launch cap of Euler sub-steps
   int nsplit;         // velocity chunks of the kinetic pass
   int ghost_mode;     // 0 none, 1 two boundary pieces per velocity (1D), 2 full copy
+  int skip_euler;     // every lambda == 1: U_E = 0, no Euler launch
+  int euler_blocks;   // grid of the cooperative Euler launch (all co-resident)
 };
 
 struct DevPtrs {
@@ -73,20 +82,24 @@ struct DevPtrs {
   void* ghost;
   double* U;          // nm x nc
   double* lam;        // nc
-  double* W0;         // nm x nc (Euler ping-pong)
-  double* W1;
+  void* W0;           // nm x nc Euler state (ping-pong; FP64 or FP32)
+  void* W1;
   double* acc;        // nsplit x 2nm x nc partial moment sums
   void* prm;          // NP x nc, compute type
   double* eqp;        // NP x nc, FP64 parameters of E[U] (initial state only)
+  double* UE;         // nm x nc, last step's U_E (FP64 copy)
   double* UM;         // nm x nc, last step's U_M
   double* Us;         // nm x nc, last step's U_*
   double* A;          // nm x nm, (C C^T)^{-1}
-  double* alpha;      // 3, alpha of the last step
+  double* alpha;      // 3, alpha for the coming step
+  double* alpha_prev; // 3, alpha used by the last completed step
+  int* mlast;         // Euler sub-steps used by the last completed step
   unsigned long long* alpha_bits;  // 3, running max (bit pattern of >= 0 doubles)
   int* msub;          // Euler sub-steps of the current step
   int* status;        // first error code
   long long* step;    // step index n
   unsigned int* counter;  // finished-block counter of the alpha reduction
+  unsigned int* gbar;     // grid barrier of the Euler launch: count, generation
 };
 
 // ---------------------------------------------------------------- helpers
@@ -136,13 +149,15 @@ void launch_prim_to_cons(const Geom& g, const double* rho, const double* u, cons
 void launch_cell_params(const Geom& g, const DevPtrs& p, int mode, int initial, cudaStream_t s);
 void launch_init_f(const Geom& g, const DevPtrs& p, cudaStream_t s);
 void launch_alpha(const Geom& g, const DevPtrs& p, cudaStream_t s);
-void launch_muscl(const Geom& g, const DevPtrs& p, int substep, cudaStream_t s);
+int euler_blocks(const Geom& g);
+cudaError_t launch_euler(const Geom& g, const DevPtrs& p, cudaStream_t s);
 void launch_ghost(const Geom& g, const DevPtrs& p, cudaStream_t s);
 void launch_finalize(const Geom& g, const DevPtrs& p, cudaStream_t s);
 void launch_materialize(const Geom& g, const DevPtrs& p, double* out, cudaStream_t s);
 void launch_offsets(const Geom& g, long long n, long long* out, int width, cudaStream_t s);
 // dvm_kinetic.cu
 void launch_kinetic_pass(const Geom& g, const DevPtrs& p, cudaStream_t s);
+void kinetic_pass_prepare(const Geom& g);
 int kinetic_pass_splits(const Geom& g);
 
 }  // namespace dvm

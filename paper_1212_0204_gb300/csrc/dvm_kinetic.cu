@@ -8,6 +8,7 @@
 //   * writes the new value back into the same piece (in place).
 // One read and one write of f per phase-space point.
 #include <math.h>
+#include <stdlib.h>
 
 #include "dvm_internal.cuh"
 
@@ -15,6 +16,12 @@ namespace dvm {
 namespace {
 
 constexpr int kThreads = 256;
+
+// DVM_GENERIC_PASS=1 forces the generic kinetic pass (for comparison runs).
+bool getenv_generic() {
+  const char* e = getenv("DVM_GENERIC_PASS");
+  return e && e[0] == '1';
+}
 
 template <typename TC> __device__ inline TC fexp2(TC x);
 template <> __device__ inline float fexp2<float>(float x) { return exp2f(x); }
@@ -57,7 +64,7 @@ __global__ void __launch_bounds__(kThreads) k_kpass_generic(Geom g, DevPtrs p) {
   const TC* prm = (const TC*)p.prm;
   TS* F = (TS*)p.F;
   const TS* G = (const TS*)p.ghost;
-  const TC lam_c = prm[row_lam() * nc + c];
+  const TC lam_c = prm[prm_at(row_lam(), c, nc)];
 
   constexpr int NM = D + 2;
   constexpr int NACC = HOFKS ? 2 * NM : NM;
@@ -107,19 +114,19 @@ __global__ void __launch_bounds__(kThreads) k_kpass_generic(Geom g, DevPtrs p) {
     TC qq = TC(0);
 #pragma unroll
     for (int i = 0; i < D; ++i) {
-      const TC du = v[i] - prm[row_u(i) * nc + src];
+      const TC du = v[i] - prm[prm_at(row_u(i), src, nc)];
       qq += du * du;
     }
-    const TC M = fexp2<TC>(prm[row_L() * nc + src] - prm[row_h(D) * nc + src] * qq);
-    TC lin_mu = prm[row_mu(D, 0) * nc + src] + prm[row_mu(D, D + 1) * nc + src] * vv;
+    const TC M = fexp2<TC>(prm[prm_at(row_L(), src, nc)] - prm[prm_at(row_h(D), src, nc)] * qq);
+    TC lin_mu = prm[prm_at(row_mu(D, 0), src, nc)] + prm[prm_at(row_mu(D, D + 1), src, nc)] * (vv + vv);
 #pragma unroll
-    for (int i = 0; i < D; ++i) lin_mu += prm[row_mu(D, 1 + i) * nc + src] * v[i];
+    for (int i = 0; i < D; ++i) lin_mu += prm[prm_at(row_mu(D, 1 + i), src, nc)] * v[i];
     TC fnew;
     if (HOFKS) {
-      TC lin_nu = prm[row_nu(D, 0) * nc + src] + prm[row_nu(D, D + 1) * nc + src] * vv;
+      TC lin_nu = prm[prm_at(row_nu(D, 0), src, nc)] + prm[prm_at(row_nu(D, D + 1), src, nc)] * (vv + vv);
 #pragma unroll
-      for (int i = 0; i < D; ++i) lin_nu += prm[row_nu(D, 1 + i) * nc + src] * v[i];
-      const TC a = prm[row_lam() * nc + src] * (fv + lin_nu);  // T(lambda f^n)
+      for (int i = 0; i < D; ++i) lin_nu += prm[prm_at(row_nu(D, 1 + i), src, nc)] * v[i];
+      const TC a = prm[prm_at(row_lam(), src, nc)] * (fv + lin_nu);  // T(lambda f^n)
       const TC b = M + lin_mu;                                   // T((1-lambda) E^n)
       fnew = a + b;
       racc[0] += a;
@@ -153,6 +160,359 @@ __global__ void __launch_bounds__(kThreads) k_kpass_generic(Geom g, DevPtrs p) {
   for (int j = 0; j < NACC; ++j) out[j * nc] = acc[j] + (double)racc[j];
 }
 
+// ---------------------------------------------------------------------------
+// Windowed kinetic pass (FP32/BF16 storage, 2D and 3D, periodic, integer
+// shifts p = 1 so that delta_k = k).
+//
+// Warp = 32 consecutive x cells; each thread owns Y consecutive y cells of one
+// z plane.  For a fixed (kz, kx) the source of target (x, y_j) at velocity ky
+// is (x - kx, y_j - ky, z - kz): as ky decreases by one, every source moves
+// up one row, so the Y sources of a thread form a window that slides by one
+// cell per step.  The window's per-source parameters (folded with vx and vz)
+// live in registers; each step loads one new source (four 16-byte loads)
+// instead of Y.  The F loads of Y consecutive steps are issued together.
+// Velocity moments: FP32 within a row of ky (<= 256 terms, in practice 24-32),
+// FP32 across the kx of one kz plane, FP64 across planes and warps.
+struct Slot {
+  // M = exp2(c0 + c1 vy + c2 vy^2); lambda (f + nu'.m) = lambda f + a0 + a1 vy + a2 vy^2;
+  // mu''.m = b0 + b1 vy + b2 vy^2 (vx and vz folded in)
+  float lam, c0, c1, c2, a0, a1, a2, b0, b1, b2;
+};
+
+__device__ __forceinline__ float ex2_ftz(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Parameters of source cell src (grouped layout, four rows per float4),
+// folded with the fixed velocity components vx (and vz).
+template <int D>
+__device__ __forceinline__ Slot load_slot(const float4* __restrict__ pg, long long nc4, int src,
+                                          float vx, float vz, float vxz2) {
+  const float4 g0 = __ldg(pg + src);
+  const float4 g1 = __ldg(pg + nc4 + src);
+  const float4 g2 = __ldg(pg + 2 * nc4 + src);
+  const float4 g3 = __ldg(pg + 3 * nc4 + src);
+  float ux, uy, uz = 0.f, L, h, nu0, nux, nuy, nuz = 0.f, nu4, mu0, mux, muy, muz = 0.f, mu4;
+  const float lam = g0.x;
+  L = g0.y; ux = g0.z; uy = g0.w;
+  if (D == 3) {
+    // rows: 4 uz 5 h 6 nu0 7 nux | 8 nuy 9 nuz 10 nu4 11 mu0 | 12 mux 13 muy 14 muz 15 mu4
+    uz = g1.x; h = g1.y; nu0 = g1.z; nux = g1.w;
+    nuy = g2.x; nuz = g2.y; nu4 = g2.z; mu0 = g2.w;
+    mux = g3.x; muy = g3.y; muz = g3.z; mu4 = g3.w;
+  } else {
+    // rows: 4 h 5 nu0 6 nux 7 nuy | 8 nu4 9 mu0 10 mux 11 muy | 12 mu4
+    h = g1.x; nu0 = g1.y; nux = g1.z; nuy = g1.w;
+    nu4 = g2.x; mu0 = g2.y; mux = g2.z; muy = g2.w;
+    mu4 = g3.x;
+  }
+  float q = (vx - ux) * (vx - ux);
+  float bn = fmaf(nux, vx, nu0), bm = fmaf(mux, vx, mu0);
+  if (D == 3) {
+    q = fmaf(vz - uz, vz - uz, q);
+    bn = fmaf(nuz, vz, bn);
+    bm = fmaf(muz, vz, bm);
+  }
+  const float n4 = nu4, m4 = mu4;  // coefficients of |v|^2
+  Slot s;
+  s.lam = lam;
+  // -h (vx-ux)^2 - h (vz-uz)^2 - h (vy-uy)^2 + L as a quadratic in vy
+  s.c2 = -h;
+  s.c1 = 2.f * h * uy;
+  s.c0 = fmaf(-h, fmaf(uy, uy, q), L);
+  s.a0 = lam * fmaf(n4, vxz2, bn);
+  s.a1 = lam * nuy;
+  s.a2 = lam * n4;
+  s.b0 = fmaf(m4, vxz2, bm);
+  s.b1 = muy;
+  s.b2 = m4;
+  return s;
+}
+
+struct WinLaunch {
+  int S;       // warps per CTA, each on every S-th velocity pair (kz, kx)
+  int splits;  // velocity chunks across CTAs (partial-sum slices)
+};
+
+// Resident CTAs per SM the windowed pass is compiled for (register cap
+// 65536 / (128 * DVM_WIN_MINB)).
+#ifndef DVM_WIN_MINB
+#define DVM_WIN_MINB 4
+#endif
+
+// CTA = S = 4 warps on the same 32 x Y targets; warp s takes the velocity
+// pairs pb + s, pb + s + 4, ...: at any time the four warps read source rows
+// shifted by one column from each other, so their parameter loads share L1
+// lines.
+template <typename TS, int D, int Y, bool HOFKS>
+__global__ void __launch_bounds__(128, DVM_WIN_MINB) k_kpass_window(Geom g, DevPtrs p, WinLaunch wl) {
+  constexpr int NM = D + 2;
+  constexpr int NA = HOFKS ? 2 * NM : NM;
+  constexpr int NT = HOFKS ? 2 : 1;
+  constexpr int S = 4;
+  __shared__ int s_ox[kMaxV1], s_oy[kMaxV1], s_oz[kMaxV1];
+  // dynamic: FP64 sums per (moment, target) and lane, shared by the S warps,
+  // then each thread's FP32 sums of the current kz plane
+  extern __shared__ double s_dyn[];
+  double (*s_acc)[32] = reinterpret_cast<double (*)[32]>(s_dyn);
+  float (*s_mid)[128] = reinterpret_cast<float (*)[128]>(s_dyn + NA * Y * 32);
+  const int tid = threadIdx.x;
+  const long long n1 = *p.step + 1;
+  const int Nx = g.nx[0], Ny = g.nx[1], Nz = g.nx[2];
+  const int nvx = g.nv[0], nvy = g.nv[1], nvz = g.nv[2];
+  for (int t = tid; t < kMaxV1; t += 128) {
+    if (t < nvx) s_ox[t] = wrap((long long)(g.kmin[0] + t) * n1, Nx);
+    if (t < nvy) s_oy[t] = wrap((long long)(g.kmin[1] + t) * n1, Ny);
+    if (D == 3 && t < nvz) s_oz[t] = wrap((long long)(g.kmin[2] + t) * n1, Nz);
+  }
+  for (int i = 0; i < NA * Y; ++i) s_mid[i][tid] = 0.f;
+  for (int i = tid; i < NA * Y * 32; i += 128) s_acc[i / 32][i % 32] = 0.0;
+  __syncthreads();
+
+  const int lane = tid & 31, ws = tid >> 5;
+  const int xr = blockIdx.x * 32 + lane;
+  const bool xact = xr < Nx;
+  const int x = xact ? xr : Nx - 1;
+  const int y0 = blockIdx.y * Y;
+  const int z = D == 3 ? (int)(blockIdx.z % Nz) : 0;
+  const int split = D == 3 ? (int)(blockIdx.z / Nz) : (int)blockIdx.z;
+  const long long nc = g.nc;
+  const int plane = Nx * Ny;
+  const float dv = (float)g.dv;
+  const float4* __restrict__ pg = (const float4*)p.prm;
+  TS* __restrict__ F = (TS*)p.F;
+  bool tact[Y];
+#pragma unroll
+  for (int j = 0; j < Y; ++j) tact[j] = xact && (y0 + j < Ny);
+
+  float lam_c[Y];
+  if (!HOFKS) {
+#pragma unroll
+    for (int j = 0; j < Y; ++j) {
+      const int yy = y0 + j < Ny ? y0 + j : Ny - 1;
+      lam_c[j] = __ldg((const float*)pg + prm_at(row_lam(), x + Nx * yy + plane * z, nc));
+    }
+  }
+  // velocity pairs (kz, kx) of this CTA (whole kz planes in 3D, a multiple of
+  // S pairs); this warp takes every S-th one
+  const int npairs = nvx * (D == 3 ? nvz : 1);
+  const int per = npairs / wl.splits;
+  const int pb = split * per, pe = pb + per;
+  // first window row: y0 - (kmin_y + nvy - 1), wrapped once per thread
+  int sy_first = (y0 - (g.kmin[1] + nvy - 1)) % Ny;
+  if (sy_first < 0) sy_first += Ny;
+  const long long kystep = (long long)nvx * nc;  // F offset between consecutive ky
+
+  for (int base = pb; base < pe; base += S) {
+    const int pr = base + ws;
+    const int kx = pr % nvx;
+    const int kz = D == 3 ? pr / nvx : 0;
+    const int kxg = g.kmin[0] + kx, kzg = D == 3 ? g.kmin[2] + kz : 0;
+    const float vx = kxg * dv, vz = kzg * dv;
+    const float vxz2 = fmaf(vx, vx, vz * vz);
+    int sx = (x - kxg) % Nx;
+    if (sx < 0) sx += Nx;
+    int sz = 0, qz = 0;
+    if (D == 3) {
+      sz = (z - kzg) % Nz;
+      if (sz < 0) sz += Nz;
+      qz = z - s_oz[kz];
+      if (qz < 0) qz += Nz;
+    }
+    int qx = x - s_ox[kx];
+    if (qx < 0) qx += Nx;
+    const int src_base = sx + plane * sz;
+    const int dst_base = qx + plane * qz;
+    TS* __restrict__ Fb = F + ((long long)kx + (long long)nvx * nvy * kz) * nc + dst_base;
+    // window: slot i holds source row (sy_first + i), wrapped
+    Slot win[Y];
+    int rnext = sy_first;
+#pragma unroll
+    for (int i = 0; i < Y; ++i) {
+      win[i] = load_slot<D>(pg, nc, src_base + Nx * rnext, vx, vz, vxz2);
+      if (++rnext == Ny) rnext = 0;
+    }
+    float in0[NT][Y], in1[NT][Y], in2[NT][Y];
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+#pragma unroll
+      for (int j = 0; j < Y; ++j) in0[t][j] = in1[t][j] = in2[t][j] = 0.f;
+    for (int kb = nvy - 1; kb >= 0; kb -= Y) {
+      // the F loads of Y steps first: Y*Y independent loads in flight
+      float fv[Y][Y];
+      int row0[Y];
+#pragma unroll
+      for (int jj = 0; jj < Y; ++jj) {
+        const int ky = kb - jj;
+        int r = y0 - s_oy[ky];
+        if (r < 0) r += Ny;
+        row0[jj] = r;
+        const TS* Fk = Fb + (long long)ky * kystep;
+        if (r + Y <= Ny) {  // no periodic wrap among the Y rows (warp-uniform)
+          const TS* Fr = Fk + r * Nx;
+#pragma unroll
+          for (int j = 0; j < Y; ++j) fv[jj][j] = tact[j] ? StoreT<TS>::load(Fr + j * Nx) : 0.f;
+        } else {
+#pragma unroll
+          for (int j = 0; j < Y; ++j) {
+            fv[jj][j] = tact[j] ? StoreT<TS>::load(Fk + r * Nx) : 0.f;
+            if (++r == Ny) r = 0;
+          }
+        }
+      }
+#pragma unroll
+      for (int jj = 0; jj < Y; ++jj) {
+        const int ky = kb - jj;
+        const float vy = (g.kmin[1] + ky) * dv;
+        const float vy2 = vy * vy;
+        float fn[Y];
+#pragma unroll
+        for (int j = 0; j < Y; ++j) {
+          const Slot& sl = win[(jj + j) % Y];
+          const float M = ex2_ftz(fmaf(sl.c2, vy2, fmaf(sl.c1, vy, sl.c0)));
+          const float lm = fmaf(sl.b2, vy2, fmaf(sl.b1, vy, sl.b0));
+          if (HOFKS) {
+            const float a = fmaf(sl.lam, fv[jj][j], fmaf(sl.a2, vy2, fmaf(sl.a1, vy, sl.a0)));
+            const float b = M + lm;  // T((1 - lambda) E^n)
+            fn[j] = a + b;           // a = T(lambda f^n)
+            in0[0][j] += a;
+            in1[0][j] = fmaf(a, vy, in1[0][j]);
+            in2[0][j] = fmaf(a, vy2, in2[0][j]);
+            in0[NT - 1][j] += b;
+            in1[NT - 1][j] = fmaf(b, vy, in1[NT - 1][j]);
+            in2[NT - 1][j] = fmaf(b, vy2, in2[NT - 1][j]);
+          } else {
+            const float fs = fv[jj][j] + M + lm;  // transported f
+            fn[j] = lam_c[j] * fs;                // its lambda part; the rest is deferred
+            in0[0][j] += fs;
+            in1[0][j] = fmaf(fs, vy, in1[0][j]);
+            in2[0][j] = fmaf(fs, vy2, in2[0][j]);
+          }
+        }
+        TS* Fk = Fb + ky * kystep;
+        int r = row0[jj];
+        if (r + Y <= Ny) {
+          TS* Fr = Fk + r * Nx;
+#pragma unroll
+          for (int j = 0; j < Y; ++j)
+            if (tact[j]) StoreT<TS>::store(Fr + j * Nx, fn[j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < Y; ++j) {
+            if (tact[j]) StoreT<TS>::store(Fk + r * Nx, fn[j]);
+            if (++r == Ny) r = 0;
+          }
+        }
+        // slide: the slot just left by target 0 takes the next source row
+        if (ky > 0) {
+          win[jj % Y] = load_slot<D>(pg, nc, src_base + Nx * rnext, vx, vz, vxz2);
+          if (++rnext == Ny) rnext = 0;
+        }
+      }
+    }
+    // fold the row sums into the plane sums: m = (1, vx, vy, [vz], |v|^2/2)
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int o = t * NM;
+#pragma unroll
+      for (int j = 0; j < Y; ++j) {
+        const float s0 = in0[t][j];
+        s_mid[(o + 0) * Y + j][tid] += s0;
+        s_mid[(o + 1) * Y + j][tid] = fmaf(vx, s0, s_mid[(o + 1) * Y + j][tid]);
+        s_mid[(o + 2) * Y + j][tid] += in1[t][j];
+        if (D == 3) s_mid[(o + 3) * Y + j][tid] = fmaf(vz, s0, s_mid[(o + 3) * Y + j][tid]);
+        s_mid[(o + D + 1) * Y + j][tid] += 0.5f * fmaf(vxz2, s0, in2[t][j]);
+      }
+    }
+    // plane finished (same round for all S warps): their FP32 plane sums
+    // into the shared FP64 accumulators
+    if ((base + S) % nvx == 0 || base + S >= pe) {
+      __syncthreads();
+      for (int i = tid; i < NA * Y * 32; i += 128) {
+        const int e = i / 32, l = i % 32;
+        double v = 0.0;
+#pragma unroll
+        for (int w2 = 0; w2 < S; ++w2) v += (double)s_mid[e][l + 32 * w2];
+        s_acc[e][l] += v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int a = 0; a < NA * Y; ++a) s_mid[a][tid] = 0.f;
+    }
+  }
+  // this split's partial sums
+  __syncthreads();
+  for (int i = tid; i < NA * Y * 32; i += 128) {
+    const int e = i / 32, l = i % 32;
+    const int a = e / Y, j = e % Y;
+    const int xx = blockIdx.x * 32 + l;
+    if (xx >= Nx || y0 + j >= Ny) continue;
+    const long long cell = xx + (long long)Nx * (y0 + j) + (long long)plane * z;
+    p.acc[((long long)split * 2 * NM + a) * nc + cell] = s_acc[e][l];
+  }
+}
+
+constexpr int kWinY = 4;
+
+bool window_eligible(const Geom& g) {
+  if (g.d < 2 || g.precision == DVM_F64 || g.p != 1) return false;
+  for (int i = 0; i < g.d; ++i)
+    if (g.bc[i] != DVM_BC_PERIODIC) return false;
+  // 32-bit cell indices; rows wrap with one subtraction; the four warps of a
+  // CTA end every kz plane in the same round
+  return g.nv[1] % kWinY == 0 && g.nv[0] % 4 == 0 && g.nx[1] >= kWinY && g.nc < (1LL << 31);
+}
+
+// Velocity splits across CTAs: the smallest divisor (of the kz planes in 3D,
+// of nvx / 4 in 2D) that gives two waves of three CTAs per SM, at most 8.
+WinLaunch window_shape(const Geom& g) {
+  const long long tiles = ((g.nx[0] + 31) / 32) * ((g.nx[1] + kWinY - 1) / kWinY) * g.nx[2];
+  const long long target_ctas = 152LL * 3 * 2;
+  const int units = g.d == 3 ? g.nv[2] : g.nv[0] / 4;
+  int sp = 1;
+  for (int c = 1; c <= 8 && c <= units; ++c) {
+    if (units % c) continue;
+    sp = c;
+    if (tiles * c >= target_ctas) break;
+  }
+  WinLaunch wl;
+  wl.S = 4;
+  wl.splits = sp;
+  return wl;
+}
+
+constexpr size_t window_smem(int d, bool hofks) {
+  return (size_t)(hofks ? 2 : 1) * (d + 2) * kWinY * (32 * sizeof(double) + 128 * sizeof(float));
+}
+
+template <typename TS, int D, bool HO>
+void launch_window_t(const Geom& g, const DevPtrs& p, const WinLaunch& wl, cudaStream_t s, bool prepare) {
+  constexpr size_t sm = window_smem(D, HO);
+  if (prepare) {
+    cudaFuncSetAttribute(k_kpass_window<TS, D, kWinY, HO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm);
+    return;
+  }
+  dim3 grid((unsigned)((g.nx[0] + 31) / 32), (unsigned)((g.nx[1] + kWinY - 1) / kWinY),
+            (unsigned)(g.nx[2] * wl.splits));
+  k_kpass_window<TS, D, kWinY, HO><<<grid, 128, sm, s>>>(g, p, wl);
+}
+
+template <typename TS>
+void launch_window(const Geom& g, const DevPtrs& p, cudaStream_t s, bool prepare = false) {
+  const WinLaunch wl = window_shape(g);
+  const bool ho = g.scheme != DVM_FKS;
+  if (g.d == 2) {
+    if (ho) launch_window_t<TS, 2, true>(g, p, wl, s, prepare);
+    else launch_window_t<TS, 2, false>(g, p, wl, s, prepare);
+  } else {
+    if (ho) launch_window_t<TS, 3, true>(g, p, wl, s, prepare);
+    else launch_window_t<TS, 3, false>(g, p, wl, s, prepare);
+  }
+}
+
 template <typename TS, typename TC>
 void launch_generic(const Geom& g, const DevPtrs& p, cudaStream_t s) {
   dim3 grid((unsigned)((g.nc + kThreads - 1) / kThreads), (unsigned)g.nsplit);
@@ -169,6 +529,7 @@ void launch_generic(const Geom& g, const DevPtrs& p, cudaStream_t s) {
 // Velocity chunks: enough blocks for several waves on 152 SMs, at least 16
 // velocities per chunk.
 int kinetic_pass_splits(const Geom& g) {
+  if (window_eligible(g)) return window_shape(g).splits;
   const long long blocks = (g.nc + kThreads - 1) / kThreads;
   const long long want = 152LL * 8;
   long long s = (want + blocks - 1) / blocks;
@@ -179,7 +540,21 @@ int kinetic_pass_splits(const Geom& g) {
   return (int)s;
 }
 
+// Kernel attributes that must be set before the first launch (outside any
+// stream capture): dynamic shared memory of the windowed pass.
+void kinetic_pass_prepare(const Geom& g) {
+  if (!window_eligible(g)) return;
+  DevPtrs none{};
+  if (g.precision == DVM_F32) launch_window<float>(g, none, nullptr, true);
+  else launch_window<__nv_bfloat16>(g, none, nullptr, true);
+}
+
 void launch_kinetic_pass(const Geom& g, const DevPtrs& p, cudaStream_t s) {
+  if (window_eligible(g) && !getenv_generic()) {
+    if (g.precision == DVM_F32) launch_window<float>(g, p, s);
+    else launch_window<__nv_bfloat16>(g, p, s);
+    return;
+  }
   if (g.precision == DVM_F64) launch_generic<double, double>(g, p, s);
   else if (g.precision == DVM_F32) launch_generic<float, float>(g, p, s);
   else launch_generic<__nv_bfloat16, float>(g, p, s);
