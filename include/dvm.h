@@ -192,8 +192,9 @@ int dvm_profile_end(dvm_handle* h, double* kinetic_ms, int* launches);
  *   f:      device pointer, N_v x N_c FP64 output (velocity-major, cell
  *           positions), caller-owned.
  *   stream: cudaStream_t or NULL; the call synchronises it before returning.
- * Size limit: 256 + 8 N_c (3d + 8) bytes must fit in the scratch, i.e. at most
- * 61679 cells in 3D, 74896 in 2D and 95322 in 1D; larger problems return
+ * Size limit: 256 + 8 N_c (P + 1) bytes must fit in the scratch, P the padded
+ * count of per-cell parameter rows (12 in 1D, 16 in 2D and 3D), i.e. at most
+ * 61679 cells in 2D or 3D and 80657 in 1D; larger problems return
  * DVM_ERR_TOO_LARGE without launching anything.  Returns DVM_ERR_NONPHYSICAL
  * or DVM_ERR_NONFINITE for bad moments, DVM_ERR_CUDA if a CUDA call fails.
  * The first call on each device looks up the device address of the scratch

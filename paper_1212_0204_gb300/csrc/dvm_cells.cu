@@ -213,9 +213,11 @@ template <typename TS> struct ComputeOf { typedef float type; };
 template <> struct ComputeOf<double> { typedef double type; };
 
 // f^0 = E[U^0] at every phase-space point, from the FP64 equilibrium
-// parameters of every cell.
+// parameters of every cell, evaluated in the storage's compute type (FP64
+// for FP64 storage, FP32 otherwise).
 template <typename TS, int D>
 __global__ void k_init_f(Geom g, DevPtrs p) {
+  typedef typename ComputeOf<TS>::type TC;
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= g.nc * g.nvel) return;
   const long long c = idx % g.nc, k = idx / g.nc;
@@ -223,18 +225,19 @@ __global__ void k_init_f(Geom g, DevPtrs p) {
   const long long nc = g.nc;
   const int kk[3] = {(int)(k % g.nv[0]), (int)((k / g.nv[0]) % g.nv[1]),
                      (int)(k / ((long long)g.nv[0] * g.nv[1]))};
-  double q = 0.0, vv = 0.0, lin = prm[prm_at(row_mu(D, 0), c, nc)];
+  TC q = TC(0), vv = TC(0), lin = (TC)prm[prm_at(row_mu(D, 0), c, nc)];
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    const double v = (double)(g.kmin[i] + kk[i]) * g.dv;
-    const double du = v - prm[prm_at(row_u(i), c, nc)];
+    const TC v = (TC)((double)(g.kmin[i] + kk[i]) * g.dv);
+    const TC du = v - (TC)prm[prm_at(row_u(i), c, nc)];
     q += du * du;
     vv += v * v;
-    lin += prm[prm_at(row_mu(D, 1 + i), c, nc)] * v;
+    lin += (TC)prm[prm_at(row_mu(D, 1 + i), c, nc)] * v;
   }
-  lin += prm[prm_at(row_mu(D, D + 1), c, nc)] * vv;
-  const double f = exp2(prm[prm_at(row_L(), c, nc)] - prm[prm_at(row_h(D), c, nc)] * q) + lin;
-  StoreT<TS>::store((TS*)p.F + k * nc + c, (typename ComputeOf<TS>::type)f);
+  lin += (TC)prm[prm_at(row_mu(D, D + 1), c, nc)] * vv;
+  const TC e = (TC)prm[prm_at(row_L(), c, nc)] - (TC)prm[prm_at(row_h(D), c, nc)] * q;
+  const TC f = (sizeof(TC) == 8 ? (TC)exp2((double)e) : (TC)exp2f((float)e)) + lin;
+  StoreT<TS>::store((TS*)p.F + k * nc + c, f);
 }
 
 template <int D>
@@ -341,14 +344,20 @@ __global__ void __launch_bounds__(kBlock) k_alpha(Geom g, DevPtrs p) {
 
 // Euler flux along dir (Eq. sys1), gamma = 1 + 2/d; zero density carries no
 // flux (only reached for lambda = 1, where W = 0).
+// Division in the Euler solver: IEEE in the FP64 build, the fast
+// approximate quotient (two ulp) in the FP32-storage builds.
+__device__ inline double e_div(double a, double b) { return a / b; }
+__device__ inline float e_div(float a, float b) { return __fdividef(a, b); }
+
 template <typename TF, int D>
 __device__ inline void euler_flux(const TF* U, int dir, TF* F) {
   const TF rho = U[0];
   TF u[3] = {TF(0), TF(0), TF(0)}, ke = TF(0);
   if (rho != TF(0)) {
+    const TF ir = e_div(TF(1), rho);
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      u[j] = U[1 + j] / rho;
+      u[j] = U[1 + j] * ir;
       ke += TF(0.5) * U[1 + j] * u[j];
     }
   }
@@ -365,55 +374,7 @@ template <typename TF, bool LIMITED>
 __device__ inline TF slope(TF a, TF b) {
   if (!LIMITED) return b;
   const TF ab = a * b;
-  return ab > TF(0) ? (ab + ab) / (a + b) : TF(0);
-}
-
-// Flux difference psi_{c+1/2} - psi_{c-1/2} of Eq. discmom for one cell, summed
-// over directions, from the five-cell stencils (loads bypass L1: the buffers
-// are rewritten by other blocks between the sub-steps of one launch).
-template <typename TF, bool LIMITED, int D>
-__device__ inline void muscl_cell(const Geom& g, const TF* __restrict__ src, const int x[3],
-                                  const double* alpha, double acc[kMaxM]) {
-  constexpr int NM = D + 2;
-#pragma unroll
-  for (int dir = 0; dir < D; ++dir) {
-    TF Us[5][NM], Fs[5][NM];
-#pragma unroll
-    for (int o = -2; o <= 2; ++o) {
-      int y[3] = {x[0], x[1], x[2]};
-      const int n = g.nx[dir];
-      const int t = x[dir] + o;
-      if (g.bc[dir] == DVM_BC_PERIODIC) {
-        y[dir] = (t < 0 || t >= n) ? wrap(t, n) : t;
-      } else {
-        y[dir] = t < 0 ? 0 : (t >= n ? n - 1 : t);
-      }
-      const long long cc = cell_index(g, y);
-#pragma unroll
-      for (int i = 0; i < NM; ++i) Us[o + 2][i] = __ldcg(src + i * g.nc + cc);
-      euler_flux<TF, D>(Us[o + 2], dir, Fs[o + 2]);
-    }
-    const TF al = (TF)alpha[dir];
-#pragma unroll
-    for (int i = 0; i < NM; ++i) {
-      TF Gp[5], Gm[5];
-#pragma unroll
-      for (int s = 0; s < 5; ++s) {
-        Gp[s] = Fs[s][i] + al * Us[s][i];
-        Gm[s] = Fs[s][i] - al * Us[s][i];
-      }
-      TF psi[2];
-#pragma unroll
-      for (int f = 0; f < 2; ++f) {  // faces between stencil cells (1,2) and (2,3)
-        const int j = 1 + f;
-        const TF sp = slope<TF, LIMITED>(Gp[j] - Gp[j - 1], Gp[j + 1] - Gp[j]);
-        const TF sm = slope<TF, LIMITED>(Gm[j + 1] - Gm[j], Gm[j + 2] - Gm[j + 1]);
-        psi[f] = TF(0.5) * (Fs[j][i] + Fs[j + 1][i]) - TF(0.5) * al * (Us[j + 1][i] - Us[j][i]) +
-                 TF(0.25) * (sp - sm);
-      }
-      acc[i] += (double)psi[1] - (double)psi[0];
-    }
-  }
+  return ab > TF(0) ? e_div(ab + ab, a + b) : TF(0);
 }
 
 // Grid-wide barrier of the cooperative Euler launch: arrive on a counter, the
@@ -450,26 +411,157 @@ __device__ bool grid_sync(unsigned* bar, int* status) {
   return ok != 0;
 }
 
-// All m MUSCL sub-steps of one kinetic step (Section 4.3.2, forward Euler,
-// unsplit over directions) in one cooperative launch: W_0 -> W_1 -> ... with
-// a grid barrier between sub-steps.  The result U_E is W_{m mod 2}.
+// Tiles of the Euler sub-step: TX x TY cells of one z plane, one thread per
+// cell, staged with a two-cell halo in every active direction; the face
+// fluxes of the tile (one more face than cells along each direction) are
+// kept in shared memory as well.
+template <int D, typename TF>
+struct ETile {
+  static constexpr int TX = D == 1 ? 128 : 32;
+  static constexpr int TY = D == 1 ? 1 : 4;
+  static constexpr int SX = TX + 4;
+  static constexpr int SY = D >= 2 ? TY + 4 : 1;
+  static constexpr int SZ = D == 3 ? 5 : 1;
+  static constexpr int NS = SX * SY * SZ;   // staged cells
+  static constexpr int FX = TX + 1, FY = D >= 2 ? TY + 1 : 1, FZ = D == 3 ? 2 : 1;
+  static constexpr int NF = FX * FY * FZ;   // face slots per direction
+  static constexpr int CELLS = TX * TY;
+  static constexpr int THREADS = CELLS * D;  // one thread per (cell, direction)
+  static constexpr size_t SMEM = (size_t)(D + 2) * (NS + D * NF) * sizeof(TF);
+};
+
+__device__ inline int bc_index(int t, int n, int bc) {
+  if (bc == DVM_BC_PERIODIC) {
+    if (t >= 0 && t < n) return t;
+    const int r = t % n;  // 32-bit: |t| < n + 3
+    return r < 0 ? r + n : r;
+  }
+  return t < 0 ? 0 : (t >= n ? n - 1 : t);
+}
+
+// Numerical flux psi_{j+1/2} of Eq. discmom along dir, component by
+// component, from the four staged cells j-1, j, j+1, j+2 (index c of cell j,
+// stride st along dir).
 template <typename TF, bool LIMITED, int D>
-__global__ void __launch_bounds__(kBlock) k_euler(Geom g, DevPtrs p) {
+__device__ inline void face_flux(const TF* sw, int ns, int c, int st, int dir, TF al, TF psi[D + 2]) {
   constexpr int NM = D + 2;
+  TF Us[4][NM], Fs[4][NM];
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+#pragma unroll
+    for (int i = 0; i < NM; ++i) Us[o][i] = sw[i * ns + c + (o - 1) * st];
+    euler_flux<TF, D>(Us[o], dir, Fs[o]);
+  }
+#pragma unroll
+  for (int i = 0; i < NM; ++i) {
+    TF Gp[4], Gm[4];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      Gp[o] = Fs[o][i] + al * Us[o][i];
+      Gm[o] = Fs[o][i] - al * Us[o][i];
+    }
+    // sigma^+_j from (j-1, j, j+1), sigma^-_{j+1} from (j, j+1, j+2)
+    const TF sp = slope<TF, LIMITED>(Gp[1] - Gp[0], Gp[2] - Gp[1]);
+    const TF sm = slope<TF, LIMITED>(Gm[2] - Gm[1], Gm[3] - Gm[2]);
+    psi[i] = TF(0.5) * (Fs[1][i] + Fs[2][i]) - TF(0.5) * al * (Us[2][i] - Us[1][i]) +
+             TF(0.25) * (sp - sm);
+  }
+}
+
+// Face fluxes of one tile along DIR (compile-time): slot (fx, fy, fz) holds
+// the face on the low side of local cell (fx, fy, fz); slot + 1 along DIR is
+// the high side.  The thread computes its cell's high face, and the first
+// cell along DIR also its low face.
+template <typename TF, bool LIMITED, int D, int DIR>
+__device__ inline void tile_faces(const TF* sw, TF* sf, int ctr, int tx, int ty, TF al) {
+  using T = ETile<D, TF>;
+  constexpr int NM = D + 2;
+  constexpr int st = DIR == 0 ? 1 : (DIR == 1 ? T::SX : T::SX * T::SY);
+  constexpr int fst = DIR == 0 ? 1 : (DIR == 1 ? T::FX : T::FX * T::FY);
+  const int fbase = tx + T::FX * ty;
+  TF* sfd = sf + DIR * NM * T::NF;
+  TF psi[NM];
+  face_flux<TF, LIMITED, D>(sw, T::NS, ctr, st, DIR, al, psi);
+#pragma unroll
+  for (int c = 0; c < NM; ++c) sfd[c * T::NF + fbase + fst] = psi[c];
+  const bool first = DIR == 0 ? tx == 0 : (DIR == 1 ? ty == 0 : true);
+  if (first) {
+    face_flux<TF, LIMITED, D>(sw, T::NS, ctr - st, st, DIR, al, psi);
+#pragma unroll
+    for (int c = 0; c < NM; ++c) sfd[c * T::NF + fbase] = psi[c];
+  }
+}
+
+// All m MUSCL sub-steps of one kinetic step (Section 4.3.2, Eq. discmom:
+// forward Euler, unsplit over directions) in one cooperative launch:
+// W_0 -> W_1 -> ... with a grid barrier between sub-steps; U_E = W_{m mod 2}.
+// Per tile and sub-step: stage the tile and its halo in shared memory (loads
+// bypass L1: other blocks rewrite the buffers between sub-steps), compute each
+// face flux once, then update every cell from its two faces per direction.
+// Arithmetic in TF (FP64 in the FP64 build, FP32 in the FP32-storage builds).
+template <typename TF, bool LIMITED, int D>
+__global__ void __launch_bounds__(ETile<D, TF>::THREADS) k_euler(Geom g, DevPtrs p) {
+  using T = ETile<D, TF>;
+  constexpr int NM = D + 2;
+  extern __shared__ unsigned char s_raw[];
+  TF* sw = reinterpret_cast<TF*>(s_raw);  // [NM][SZ][SY][SX]
+  TF* sf = sw + NM * T::NS;               // [D][NM][FZ][FY][FX]
   const int m = *p.msub;
-  const double k = (g.dt / m) / g.dx;
-  const long long stride = (long long)gridDim.x * blockDim.x;
+  const TF k = (TF)((g.dt / m) / g.dx);
+  const int Nx = g.nx[0], Ny = g.nx[1], Nz = g.nx[2];
+  const long long nc = g.nc;
+  const int ntx = (Nx + T::TX - 1) / T::TX, nty = (Ny + T::TY - 1) / T::TY;
+  const int ntiles = ntx * nty * Nz;
+  const int tid = threadIdx.x;
+  const int cid = tid % T::CELLS, mydir = tid / T::CELLS;
+  const int tx = cid % T::TX, ty = cid / T::TX;
+  const int cz = D == 3 ? 2 : 0, cy = D >= 2 ? ty + 2 : 0, cx = tx + 2;
+  const int ctr = cx + T::SX * (cy + T::SY * cz);  // staged index of this thread's cell
+  TF al[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) al[d] = (TF)p.alpha[d];
   for (int s = 0; s < m; ++s) {
     const TF* src = (const TF*)((s & 1) ? p.W1 : p.W0);
     TF* dst = (TF*)((s & 1) ? p.W0 : p.W1);
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.nc; c += stride) {
-      int x[3];
-      cell_coords<D>(g, c, x);
-      double acc[kMaxM] = {0.0, 0.0, 0.0, 0.0, 0.0};
-      muscl_cell<TF, LIMITED, D>(g, src, x, p.alpha, acc);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const int x0 = (t % ntx) * T::TX;
+      const int y0 = ((t / ntx) % nty) * T::TY;
+      const int z = t / (ntx * nty);
+      for (int i = tid; i < T::NS; i += T::THREADS) {
+        const int lx = i % T::SX, ly = (i / T::SX) % T::SY, lz = i / (T::SX * T::SY);
+        const int gx = bc_index(x0 - 2 + lx, Nx, g.bc[0]);
+        const int gy = D >= 2 ? bc_index(y0 - 2 + ly, Ny, g.bc[1]) : 0;
+        const int gz = D == 3 ? bc_index(z - 2 + lz, Nz, g.bc[2]) : 0;
+        const long long cc = gx + (long long)Nx * (gy + (long long)Ny * gz);
 #pragma unroll
-      for (int i = 0; i < NM; ++i)
-        dst[i * g.nc + c] = (TF)((double)__ldcg(src + i * g.nc + c) - k * acc[i]);
+        for (int c = 0; c < NM; ++c) sw[c * T::NS + i] = __ldcg(src + c * nc + cc);
+      }
+      __syncthreads();
+      // face fluxes: slot (fx, fy, fz) of direction dir holds the face on the
+      // low side of local cell (fx, fy, fz) along dir; slot index + 1 along
+      // dir is the high side.  Thread (cell, dir) computes its cell's high
+      // face along dir, and the first cell along dir also its low face.
+      if (mydir == 0) tile_faces<TF, LIMITED, D, 0>(sw, sf, ctr, tx, ty, al[0]);
+      else if (D >= 2 && mydir == 1) tile_faces<TF, LIMITED, D, (D >= 2 ? 1 : 0)>(sw, sf, ctr, tx, ty, al[D >= 2 ? 1 : 0]);
+      else if (D == 3) tile_faces<TF, LIMITED, D, (D == 3 ? 2 : 0)>(sw, sf, ctr, tx, ty, al[D == 3 ? 2 : 0]);
+      __syncthreads();
+      const int gx = x0 + tx, gy = y0 + ty;
+      if (mydir == 0 && gx < Nx && gy < Ny) {
+        const int fbase = tx + T::FX * ty;
+        const long long cell = gx + (long long)Nx * (gy + (long long)Ny * z);
+#pragma unroll
+        for (int c = 0; c < NM; ++c) {
+          TF acc = TF(0);
+#pragma unroll
+          for (int dir = 0; dir < D; ++dir) {
+            const int fst = dir == 0 ? 1 : (dir == 1 ? T::FX : T::FX * T::FY);
+            const TF* sfd = sf + (dir * NM + c) * T::NF;
+            acc += sfd[fbase + fst] - sfd[fbase];
+          }
+          dst[c * nc + cell] = sw[c * T::NS + ctr] - k * acc;
+        }
+      }
+      __syncthreads();
     }
     if (s + 1 < m && !grid_sync(p.gbar, p.status)) return;
   }
@@ -625,20 +717,24 @@ __global__ void k_offsets(Geom g, long long n, long long* out, int width) {
 template <typename TF, bool LIM, int D>
 cudaError_t launch_euler_t(const Geom& g, const DevPtrs& p, cudaStream_t s, bool prepare,
                            int* blocks) {
+  using T = ETile<D, TF>;
   if (prepare) {
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_euler<TF, LIM, D>, kBlock, 0);
+    cudaFuncSetAttribute(k_euler<TF, LIM, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)T::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_euler<TF, LIM, D>, T::THREADS, T::SMEM);
     const long long nb = (long long)sms * (per_sm < 1 ? 1 : per_sm);
-    const long long need = (g.nc + kBlock - 1) / kBlock;
+    const long long need = (long long)((g.nx[0] + T::TX - 1) / T::TX) *
+                           ((g.nx[1] + T::TY - 1) / T::TY) * g.nx[2];
     *blocks = (int)(nb < need ? nb : need);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)g.euler_blocks);
-  cfg.blockDim = dim3(kBlock);
-  cfg.dynamicSmemBytes = 0;
+  cfg.blockDim = dim3(T::THREADS);
+  cfg.dynamicSmemBytes = T::SMEM;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

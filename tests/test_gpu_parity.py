@@ -104,8 +104,10 @@ def test_hofks_parts_match_oracle():
     for a, b in zip(g.parts(), orc.parts()):
         assert moment_err(a, b) <= 1e-12
     gi, oi = g.info(), orc.info()
+    # the integer decision (Euler sub-steps) must agree; alpha itself is computed
+    # from moments that differ at round-off between the two sides
     assert gi["m"] == oi["m"] and gi["n"] == oi["n"]
-    assert np.array_equal(gi["alpha"][:2], oi["alpha"][:2])
+    np.testing.assert_allclose(gi["alpha"][:2], oi["alpha"][:2], rtol=1e-13, atol=0)
 
 
 @pytest.mark.parametrize("p", [1, 3])
