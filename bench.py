@@ -44,6 +44,7 @@ WORKLOADS = {
     "quadrant_2d_f64": (lambda: W.quadrant_2d(n=256, nv=32, tau=1e-3, steps=500), "f64"),
     "quadrant_2d_bf16": (lambda: W.quadrant_2d(n=256, nv=32, tau=1e-3, steps=500), "bf16"),
     "sod_1d": (lambda: W.sod_1d(nx=200, nv=32, tau=1e-4), "f64"),
+    "batched_tubes": (lambda: W.batched_tubes(ncases=512, steps=100), "f32"),
 }
 DESCR = {
     "quadrant_2d": "2D-2V four-quadrant Riemann problem, 256x256 periodic cells x 32x32 velocities, "
@@ -55,6 +56,9 @@ DESCR = {
     "quadrant_2d_f64": "2D-2V four-quadrant Riemann problem, 256^2 x 32^2, HOFKS, FP64 f",
     "quadrant_2d_bf16": "2D-2V four-quadrant Riemann problem, 256^2 x 32^2, HOFKS, BF16 f storage",
     "sod_1d": "1D-1V Sod tube, 200 cells x 32 velocities, tau=1e-4, outflow, HOFKS, FP64",
+    "batched_tubes": "512 independent 1D-1V Riemann tubes in one batched launch per phase, "
+                     "N_x ~ U{100..2000}, N_v in {32,64,128}, tau = 10^U(-5,0), outflow, HOFKS, "
+                     "FP32 f / FP64 moments",
 }
 BYTES_PER_UPDATE = {"f64": 16, "f32": 8, "bf16": 4}
 DTYPE = {"f64": "f64", "f32": "f32", "bf16": "bf16"}
@@ -173,29 +177,42 @@ def physical_gpu_index(local_rank: int) -> int:
 
 def oracle_sample(case, budget_points: float):
     """A bounded sample of the workload for the CPU oracle: same velocity grid and
-    initial-data recipe, fewer cells (a square/cubic sub-problem)."""
+    initial-data recipe, fewer cells (a square/cubic sub-problem), or for a batch
+    the first tubes up to the budget.  Returns (list of cases, description)."""
+    if isinstance(case, list):
+        picked, pts = [], 0
+        for c in case:
+            picked.append(c)
+            pts += c.points
+            if pts >= budget_points:
+                break
+        return picked, f"the first {len(picked)} of {len(case)} tubes ({pts} points)"
     if case.name == "quadrant_2d":
         n = int(max(8, min(case.nx[0], round((budget_points / case.nvel) ** 0.5))))
-        return W.quadrant_2d(n=n, nv=case.nv[0], tau=case.tau, steps=1, dv=case.dv), f"{n}x{n} cells"
+        return ([W.quadrant_2d(n=n, nv=case.nv[0], tau=case.tau, steps=1, dv=case.dv)],
+                f"{n}x{n} cells x {case.nvel} velocities")
     if case.name == "density_wave_3d":
         n = int(max(4, min(case.nx[0], round((budget_points / case.nvel) ** (1 / 3)))))
-        return (W.density_wave_3d(n=n, nv=case.nv[0], tau=case.tau, steps=1, dv=case.dv),
-                f"{n}^3 cells")
-    return case, f"{case.nx[0]} cells"
+        return ([W.density_wave_3d(n=n, nv=case.nv[0], tau=case.tau, steps=1, dv=case.dv)],
+                f"{n}^3 cells x {case.nvel} velocities")
+    return [case], f"{case.nx[0]} cells x {case.nvel} velocities"
 
 
-def time_oracle(case, steps: int, warmup: int = 0):
+def time_oracle(cases, steps: int, warmup: int = 0):
+    """Single-thread FP64 oracle over the sample: (updates/s, seconds timed)."""
     import oracle
     from tests.helpers import grid
-    g = grid(case)
-    s = oracle.Scheme(g, tau=case.tau)
-    s.set_moments(conserved(case))
-    if warmup:
-        s.step(warmup)
-    t0 = time.perf_counter()
-    s.step(steps)
-    dt = time.perf_counter() - t0
-    return case.points * steps / dt, dt
+    total_pts, secs = 0, 0.0
+    for case in cases:
+        s = oracle.Scheme(grid(case), tau=case.tau)
+        s.set_moments(conserved(case))
+        if warmup:
+            s.step(warmup)
+        t0 = time.perf_counter()
+        s.step(steps)
+        secs += time.perf_counter() - t0
+        total_pts += case.points * steps
+    return total_pts / secs, secs
 
 
 def run_reference(args, case, descr, rank):
@@ -212,12 +229,54 @@ def run_reference(args, case, descr, rank):
         "data": "synthetic",
         "config": {"workload": descr, "sample": what},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{what} x {case.nvel} velocities, {args.steps} steps "
-                                   f"after {args.warmup} warm-up steps, single thread"},
+                         "sample": f"{what}, {args.steps} steps after {args.warmup} warm-up "
+                                   f"steps, single thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+class Job:
+    """The GPU side of one workload: a single problem (dvm.Solver) or a batch of
+    tubes (dvm.Batch), with the calls the benchmark times."""
+
+    def __init__(self, dvm, case, precision):
+        self.batch = isinstance(case, list)
+        if self.batch:
+            self.obj = dvm.Batch(case, precision=precision)
+            self.U0 = self.obj.pack([conserved(c) for c in case])
+            self.points = sum(c.points for c in case)
+            self.rows, self.cells = 3, self.obj.ncells
+        else:
+            self.obj = dvm.Solver.from_case(case, precision=precision)
+            self.U0 = conserved(case)
+            self.points = case.points
+            self.rows, self.cells = case.d + 2, case.ncells
+        self.stream = self.obj.stream
+        self.tiling = None
+
+    def set_moments(self, U):
+        self.obj.set_moments(U)
+
+    def prepare(self, dvm, case, precision, warmup):
+        self.obj.set_moments(self.U0)
+        if self.batch:
+            self.tiling = dvm.autotune_cached(self.obj, case, precision, dvm.HOFKS)
+        self.obj.step(warmup)
+
+    def launches_per_step(self):
+        return 3 if self.batch else self.obj.launches_per_step()
+
+    def kinetic_ms(self, steps):
+        """Average kinetic-pass time, CUDA events on the launching stream."""
+        if self.batch:
+            return self.obj.kinetic_ms(steps)
+        self.obj.profile_begin()
+        self.obj.step_async(steps)
+        ms, n = self.obj.profile_end()
+        self.obj.sync_status()
+        return ms / n
 
 
 def main():
@@ -236,7 +295,7 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     make, prec = WORKLOADS[args.workload]
     case = make()
-    if args.cells:
+    if args.cells and not isinstance(case, list):
         import dataclasses
         kw = {"n": args.cells} if case.d > 1 else {"nx": args.cells}
         fn = {"quadrant_2d": W.quadrant_2d, "density_wave_3d": W.density_wave_3d,
@@ -244,7 +303,7 @@ def main():
         small = fn(**kw, nv=case.nv[0], tau=case.tau, steps=case.steps, dv=case.dv)
         case = dataclasses.replace(small, name=case.name)
     if args.steps is None:
-        args.steps = case.steps
+        args.steps = case[0].steps if isinstance(case, list) else case.steps
     args.warmup = max(3, args.warmup)
     descr = DESCR[args.workload]
     if args.impl == "reference":
@@ -265,55 +324,51 @@ def main():
         torch.cuda.synchronize()
 
     precision = {"f64": dvm.F64, "f32": dvm.F32, "bf16": dvm.BF16S}[prec]
-    solver = dvm.Solver.from_case(case, precision=precision)
-    stream = solver.stream
-    U0 = torch.from_numpy(conserved(case)).contiguous().pin_memory()
-    solver.set_moments(U0)
-    solver.step(args.warmup)
-    launches = solver.launches_per_step()
+    job = Job(dvm, case, precision)
+    stream = job.stream
+    U0 = torch.from_numpy(job.U0).contiguous().pin_memory()
+    job.prepare(dvm, case, precision, args.warmup)
+    launches = job.launches_per_step()
 
-    # ---- device-timed region: K graph replays on the solver's stream
+    # ---- device-timed region: K graph replays on the job's stream
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(physical_gpu_index(local)) as clk:
         barrier()
         start.record(stream)
-        solver.step_async(args.steps)
+        job.obj.step_async(args.steps)
         stop.record(stream)
         stop.synchronize()
         barrier()
-    solver.sync_status()
+    job.obj.sync_status()
     ms = start.elapsed_time(stop)
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = case.points * args.steps * world / (ms * 1e-3)
+    value = job.points * args.steps * world / (ms * 1e-3)
 
     # ---- kinetic-pass roofline: the same steps, kinetic pass bracketed by events
-    solver.profile_begin()
-    solver.step_async(args.steps)
-    kin_ms, kin_n = solver.profile_end()
-    solver.sync_status()
-    bytes_alg = BYTES_PER_UPDATE[prec] * case.points
-    achieved = bytes_alg / (kin_ms / kin_n * 1e-3) / 1e9
+    kin_ms = job.kinetic_ms(args.steps)
+    bytes_alg = BYTES_PER_UPDATE[prec] * job.points
+    achieved = bytes_alg / (kin_ms * 1e-3) / 1e9
     peak, peak_kind = load_peaks()
     traffic = recorded_traffic(args.workload)
 
     # ---- end to end through the public API with host buffers
-    out = torch.empty((case.d + 2, case.ncells), dtype=torch.float64).pin_memory()
+    out = torch.empty((job.rows, job.cells), dtype=torch.float64).pin_memory()
     barrier()
     t0 = time.perf_counter()
-    solver.set_moments(U0)          # H2D of the initial moments, builds f^0
-    solver.step(args.steps)
-    solver.moments(out)             # D2H of the final moments
+    job.set_moments(U0)             # H2D of the initial moments, builds f^0
+    job.obj.step(args.steps)
+    job.obj.moments(out)            # D2H of the final moments
     barrier()
     e2e_s = time.perf_counter() - t0
     if dist:
         t = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    mom_bytes = 8 * (case.d + 2) * case.ncells
-    e2e = {"value": case.points * args.steps * world / e2e_s, "unit": UNIT,
+    mom_bytes = 8 * job.rows * job.cells
+    e2e = {"value": job.points * args.steps * world / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": mom_bytes / args.steps, "d2h_bytes_per_step": mom_bytes / args.steps,
            "note": "initial moments uploaded and final moments read back once per K-step job"}
 
@@ -324,20 +379,22 @@ def main():
     cpu = None
     if not args.no_cpu_baseline:
         sample, what = oracle_sample(case, 4e6)
-        v, secs = time_oracle(sample, steps=max(1, int(round(15.0 * 8e6 / sample.points))))
+        pts = sum(c.points for c in sample)
+        v, secs = time_oracle(sample, steps=max(1, int(round(15.0 * 8e6 / pts))))
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{what} x {case.nvel} velocities, {secs:.1f} s of single-thread FP64 oracle"}
+               "sample": f"{what}, {secs:.1f} s of single-thread FP64 oracle"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
-        "config": {"workload": descr, "cells": case.ncells, "velocities": case.nvel,
-                   "points": case.points, "l2": "f larger than L2 (no flush)",
-                   "parallelism": f"{world} independent replica(s)"},
+        "config": {"workload": descr, "cells": job.cells, "points": job.points,
+                   "l2": "f larger than L2 (no flush)",
+                   "parallelism": f"{world} independent replica(s)",
+                   **({"tiling": job.tiling} if job.tiling else {})},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "kinetic_pass",
                      "peak_source": peak_kind,
-                     "kernel_ms": kin_ms / kin_n, "bytes_per_launch": bytes_alg},
+                     "kernel_ms": kin_ms, "bytes_per_launch": bytes_alg},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches * args.steps,

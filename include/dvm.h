@@ -45,7 +45,7 @@ typedef enum {
   DVM_ERR_NONPHYSICAL = -5, /* rho <= 0 or theta <= 0 in some cell */
   DVM_ERR_TIMEOUT = -6,     /* a bounded device-side wait gave up */
   DVM_ERR_STATE = -7,       /* call out of order (e.g. step before a state is set) */
-  DVM_ERR_CFL = -8,         /* Euler sub-steps needed exceed the launch cap */
+  DVM_ERR_CFL = -8,         /* Euler sub-steps needed exceed max_subcycles */
   DVM_ERR_TOO_LARGE = -9    /* problem larger than the fixed scratch of
                                dvm_equilibrium_noalloc */
 } dvm_status;
@@ -85,9 +85,11 @@ typedef struct {
                                dimension must agree */
   int scheme;               /* dvm_scheme; DVM_HOFKS is the paper's scheme */
   int precision;            /* dvm_precision: storage type of f */
-  int euler_subcycles;      /* 0: Euler CFL rule of Eq. Time2 each step;
-                               > 0: that many MUSCL sub-steps per step */
-  int max_subcycles;        /* launch cap for the CFL rule; 0 = automatic */
+  int euler_subcycles;      /* 0: MUSCL sub-steps by Eq. Time2, each with the
+                               alpha of its own initial state, the last one
+                               ending at dt; > 0: that many equal sub-steps */
+  int max_subcycles;        /* cap on sub-steps per kinetic step, exceeding it
+                               sets DVM_ERR_CFL; 0 = 10^6 */
 } dvm_config;
 
 typedef struct dvm_handle dvm_handle;
@@ -174,6 +176,53 @@ int dvm_launches_per_step(dvm_handle* h, int* launches);
  * kinetic-pass time in milliseconds and the number of launches timed. */
 int dvm_profile_begin(dvm_handle* h);
 int dvm_profile_end(dvm_handle* h, double* kinetic_ms, int* launches);
+
+/* ----------------------------------------------------------------------
+ * Batched 1D-1V cases.  Many independent tubes (each a 1D configuration with
+ * its own N_x, N_v, kmin, dv, tau, p and boundary rule; all with the same
+ * scheme and precision, N_x <= 4096, scalar tau) advance together: one time
+ * step of the batch is three kernel launches for all cases, captured into
+ * one CUDA graph (Euler sub-steps per case; one persistent kinetic pass over
+ * a work queue of (case, cell tile) items ordered by cost; end-of-step
+ * update).  The scheme is the one of dvm_step (Sections 4.2 and 4.3).
+ * Packed layout of batch moments: rows rho, rho u, E of N_total cells each,
+ * FP64, case i's cells at [c_i, c_i + N_x,i) with c_i the running sum of
+ * the N_x of the cases before it. */
+typedef struct dvm_batch dvm_batch;
+
+/* cfgs: ncases configurations (dim must be 1).  Device memory is allocated
+ * with cudaMalloc and freed by dvm_batch_destroy.  DVM_ERR_ARG if a case is
+ * invalid or the cases disagree on scheme or precision. */
+int dvm_batch_create(const dvm_config* cfgs, int ncases, void* cuda_stream,
+                     dvm_batch** out);
+void dvm_batch_destroy(dvm_batch* b);
+const char* dvm_batch_last_error(const dvm_batch* b);
+/* Total cells and phase-space points of the batch. */
+int dvm_batch_sizes(const dvm_batch* b, long long* cells, long long* points);
+/* f^0 = E[U^0] for every case (Eq. minimMax); U packed as above, host or
+ * device. */
+int dvm_batch_set_state_moments(dvm_batch* b, const double* U, int on_device);
+int dvm_batch_step(dvm_batch* b, int nsteps);
+int dvm_batch_step_async(dvm_batch* b, int nsteps);
+int dvm_batch_sync_status(dvm_batch* b);
+/* Packed moments of all cases into the caller's buffer (host or device). */
+int dvm_batch_moments(dvm_batch* b, double* out, int on_device);
+/* f of case icase at its cell centres, N_v x N_x FP64, host buffer. */
+int dvm_batch_get_f(dvm_batch* b, int icase, double* out);
+/* Step index, per-case Euler sub-steps and alpha of the last step (host
+ * arrays of ncases entries; any pointer may be NULL). */
+int dvm_batch_info(dvm_batch* b, long long* n, int* substeps, double* alpha);
+/* Tile of the kinetic pass: threads per CTA (multiple of 32, <= 1024) and
+ * cells per thread (1..8). */
+int dvm_batch_set_tiling(dvm_batch* b, int threads, int cells_per_thread);
+/* Times the kinetic pass of every candidate tile (threads 64/128/256 x 1 or
+ * 2 cells per thread) on the current state, restores f, keeps the fastest
+ * and returns it with its time in ms.  Needs a state. */
+int dvm_batch_autotune(dvm_batch* b, int* threads, int* cells_per_thread,
+                       double* best_ms);
+/* Runs nsteps steps launch by launch with CUDA events around the kinetic
+ * pass; *ms receives its average time. */
+int dvm_batch_kinetic_ms(dvm_batch* b, int nsteps, double* ms);
 
 /* Allocation-free equilibrium.  The paper has no counterpart to this entry
  * point: it exists for callers that cannot allocate device memory (a program

@@ -530,48 +530,84 @@ static int equilibria(orc_state* S, const double* U) {
   return ORC_OK;
 }
 
-/* Euler sub-steps per kinetic step: dt_E = dt/m must satisfy Eq. Time2,
- * dt_E <= dx / (2 alpha_max); in several dimensions alpha_max is the sum over
- * directions (reading). */
-static int euler_substeps(const orc_state* S) {
-  if (S->g.subcycles > 0) return S->g.subcycles;
-  double asum = 0.0;
-  for (int i = 0; i < S->g.d; ++i) asum += S->alpha[i];
-  const double dtE = 0.5 * S->g.dx / asum;
-  int m = (int)ceil(S->dt / dtE);
-  return m < 1 ? 1 : m;
+/* alpha of an Euler state W (flux splitting and Eq. Time2): per direction the
+ * largest |u_dir| + sqrt(gamma theta) over the cells; cells with zero density
+ * (lambda = 1 makes W = 0 there) carry no wave and are skipped. */
+static void state_alpha(const orc_config* g, const double* W, double alpha[3]) {
+  const int d = g->d, nm = d + 2;
+  const long nc = ncells(g);
+  const double gamma = 1.0 + 2.0 / d;
+  for (int i = 0; i < 3; ++i) alpha[i] = 0.0;
+  for (long c = 0; c < nc; ++c) {
+    double Uc[MAXM] = {0.0, 0.0, 0.0, 0.0, 0.0}, rho, u[3], theta;
+    for (int i = 0; i < nm; ++i) Uc[i] = W[i * nc + c];
+    if (Uc[0] == 0.0) continue;
+    primitives(d, Uc, &rho, u, &theta);
+    const double cs = sqrt(gamma * theta);
+    for (int i = 0; i < d; ++i) {
+      const double a = fabs(u[i]) + cs;
+      if (a > alpha[i]) alpha[i] = a;
+    }
+  }
 }
 
-/* U_E from W = (1 - lambda) U^n by m MUSCL sub-steps (Section 4.3.2).
- * Reading: U_E carries the (1 - lambda) weight so that U_H = U_* + U_E has
- * the mass of f; for uniform lambda this equals (1 - lambda) MUSCL(U^n). */
+/* U_E from W = (1 - lambda) U^n by MUSCL sub-steps covering the kinetic step
+ * (Section 4.3.2).  Reading: U_E carries the (1 - lambda) weight so that
+ * U_H = U_* + U_E has the mass of f; for uniform lambda this equals
+ * (1 - lambda) MUSCL(U^n).  Each Euler sub-step takes alpha from its own
+ * initial state and its length from Eq. Time2, dt_E = dx / (2 sum_i alpha_i)
+ * (reading: unsplit multi-D), the last one shortened to end at dt; with a
+ * fixed count m the sub-steps are dt/m long and alpha is still taken per
+ * sub-step. */
 static int euler_part(orc_state* S) {
   const long nc = S->nc;
   const int nm = S->nm;
-  int rc = orc_euler_alpha(&S->g, S->U, S->alpha);
-  if (rc) return rc;
-  S->last_m = euler_substeps(S);
   int all_free = 1;
   for (long c = 0; c < nc; ++c)
     if (S->lam[c] != 1.0) all_free = 0;
   if (all_free) {
     /* free transport: W = 0 and the Euler solve is skipped */
     memset(S->UE, 0, sizeof(double) * nm * nc);
+    for (int i = 0; i < 3; ++i) S->alpha[i] = 0.0;
+    S->last_m = 0;
     return ORC_OK;
   }
   for (int i = 0; i < nm; ++i)
     for (long c = 0; c < nc; ++c)
       S->W0[i * nc + c] = (1.0 - S->lam[c]) * S->U[i * nc + c];
-  const double dtE = S->dt / S->last_m;
   const int limited = (S->g.scheme == ORC_HOFKS);
   double* a = S->W0;
   double* b = S->W1;
-  for (int s = 0; s < S->last_m; ++s) {
-    orc_muscl_step(&S->g, a, dtE, S->alpha, limited, b);
-    double* t = a;
+  double t = 0.0;
+  int m = 0;
+  for (;;) {
+    double alpha[3], asum = 0.0;
+    state_alpha(&S->g, a, alpha);
+    for (int i = 0; i < S->g.d; ++i) asum += alpha[i];
+    if (m == 0)
+      for (int i = 0; i < 3; ++i) S->alpha[i] = alpha[i];
+    double dtE;
+    int last;
+    if (S->g.subcycles > 0) {
+      dtE = S->dt / S->g.subcycles;
+      last = (m + 1 == S->g.subcycles);
+    } else {
+      if (!(asum > 0.0)) return ORC_ERR_NONPHYSICAL;
+      const double cfl = 0.5 * S->g.dx / asum;
+      const double rem = S->dt - t;
+      last = (cfl >= rem);
+      dtE = last ? rem : cfl;
+    }
+    orc_muscl_step(&S->g, a, dtE, alpha, limited, b);
+    double* tmp = a;
     a = b;
-    b = t;
+    b = tmp;
+    t += dtE;
+    m += 1;
+    if (last) break;
+    if (m > 1000000) return ORC_ERR_NONPHYSICAL;
   }
+  S->last_m = m;
   memcpy(S->UE, a, sizeof(double) * nm * nc);
   return ORC_OK;
 }

@@ -225,6 +225,7 @@ void bind(dvm_handle* h, char* base, const Layout& L) {
   p.gbar = (unsigned int*)(sm + 96);                  // 2 unsigned
   p.mlast = (int*)(sm + 104);
   p.alpha_prev = (double*)(sm + 112);                 // 3 doubles
+  p.aslot = (unsigned long long*)(sm + 144);          // 9
   h->offs = (long long*)(base + L.offs);
 }
 
@@ -307,6 +308,7 @@ int init_from_moments(dvm_handle* h) {
   if ((rc = cuda_check(h, cudaMemsetAsync(h->p.mlast, 0, sizeof(int), s), "memset"))) return rc;
   if ((rc = cuda_check(h, cudaMemsetAsync(h->p.alpha_prev, 0, 3 * sizeof(double), s), "memset"))) return rc;
   if ((rc = cuda_check(h, cudaMemsetAsync(h->p.gbar, 0, 2 * sizeof(unsigned), s), "memset"))) return rc;
+  if ((rc = cuda_check(h, cudaMemsetAsync(h->p.aslot, 0, 9 * sizeof(unsigned long long), s), "memset"))) return rc;
   launch_cell_params(g, h->p, 0, 1, s);
   launch_init_f(g, h->p, s);
   launch_cell_params(g, h->p, 1, 1, s);
@@ -390,7 +392,8 @@ int dvm_create(const dvm_config* cfg, void* workspace, void* cuda_stream, dvm_ha
   h->all_free = all_free;
   h->g.skip_euler = all_free ? 1 : 0;
   h->g.euler_blocks = euler_blocks(h->g);
-  h->g.m_cap = cfg->max_subcycles > 0 ? cfg->max_subcycles : (cfg->euler_subcycles > 0 ? cfg->euler_subcycles : 1 << 20);
+  h->g.m_cap = cfg->max_subcycles > 0 ? cfg->max_subcycles : 1000000;
+  if (cfg->euler_subcycles > 0 && h->g.m_cap < cfg->euler_subcycles) h->g.m_cap = cfg->euler_subcycles;
   cudaStream_t s = h->stream;
   if (cudaMemsetAsync(h->ws, 0, L.total, s) != cudaSuccess ||
       cudaMemcpyAsync(h->p.A, A, sizeof(double) * h->g.nm * h->g.nm, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -553,8 +556,8 @@ int dvm_info(dvm_handle* h, double* dt, long long* n, int* substeps, double* alp
   double a[3] = {0, 0, 0};
   cudaStream_t s = h->stream;
   rc |= cuda_check(h, cudaMemcpyAsync(&step, h->p.step, sizeof step, cudaMemcpyDeviceToHost, s), "copy");
-  rc |= cuda_check(h, cudaMemcpyAsync(&m, h->p.mlast, sizeof m, cudaMemcpyDeviceToHost, s), "copy");
-  rc |= cuda_check(h, cudaMemcpyAsync(a, h->p.alpha_prev, sizeof a, cudaMemcpyDeviceToHost, s), "copy");
+  rc |= cuda_check(h, cudaMemcpyAsync(&m, h->p.msub, sizeof m, cudaMemcpyDeviceToHost, s), "copy");
+  rc |= cuda_check(h, cudaMemcpyAsync(a, h->p.alpha, sizeof a, cudaMemcpyDeviceToHost, s), "copy");
   rc |= cuda_check(h, cudaStreamSynchronize(s), "sync");
   if (rc) return h->status;
   if (dt) *dt = h->g.dt;

@@ -1,0 +1,874 @@
+// dvm_batch.cu -- many independent 1D-1V cases advanced together.
+//
+// Cases differ in N_x, N_v, tau, p and boundary rule and share the scheme and
+// the storage precision.  One time step of the whole batch is three launches,
+// captured once into a CUDA graph:
+//   k_b_euler    one CTA per case: alpha and the Euler sub-step count of the
+//                case, W = (1 - lambda) U, all MUSCL sub-steps in shared
+//                memory (Section 4.3.2), U_E; the boundary pieces of outflow
+//                cases; reset of the work queue.
+//   k_b_kinetic  persistent: CTAs pull (case, cell tile) items from an atomic
+//                queue ordered by decreasing cost; each thread owns cells of the
+//                tile and sweeps all velocities of the case (the kinetic pass of
+//                dvm_kinetic.cu with per-case geometry).
+//   k_b_finalize all cells of all cases: U^{n+1}, nu, mu and next parameters.
+// The tile (threads per CTA, cells per thread) is chosen by dvm_batch_autotune.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "dvm_internal.cuh"
+#include "dvm_math.cuh"
+
+namespace dvm {
+namespace {
+
+struct BCase {
+  int nx, nv, kmin, p, bc, forced_sub;
+  int ghost_off, all_free;
+  long long f_off, c_off;
+  double dx, dv, dt, w;
+  double A[9];
+};
+
+struct BItem {
+  int bcase, x0;
+};
+
+struct BPtrs {
+  const BCase* cases;
+  int ncases;
+  const int* cell_case;
+  long long ncells;
+  const BItem* items;
+  int nitems;
+  void* F;
+  void* ghost;
+  double *U, *lam, *UE, *UM, *Us, *acc;  // acc: 6 x ncells
+  void* prm;
+  double* eqp;
+  int* msub;
+  double* alpha;
+  int* status;
+  long long* step;
+  unsigned* qcounter;
+  int scheme;
+  int cpt;  // cells per kinetic thread
+};
+
+constexpr int kB = 256;
+constexpr int kMaxBatchNx = 4096;
+
+// mu of Eq. minimMax for one cell of a 1D case (separable sums: one axis).
+template <bool F64>
+__device__ int b_cell_mu(const BCase& bc, const double* Uc, double mu[3], double& rho, double& u,
+                         double& theta) {
+  for (int i = 0; i < 3; ++i)
+    if (!isfinite(Uc[i])) return DVM_ERR_NONFINITE;
+  double uu[3];
+  primitives<1>(Uc, rho, uu, theta);
+  u = uu[0];
+  if (!(rho > 0.0) || !(theta > 0.0)) return DVM_ERR_NONPHYSICAL;
+  double G0, G1, G2;
+  if (F64) gauss_axis_sums(bc.nv, bc.kmin, bc.dv, u, theta, G0, G1, G2);
+  else gauss_axis_sums_f32(bc.nv, bc.kmin, (float)bc.dv, (float)u, (float)theta, G0, G1, G2);
+  const double pref = F64 ? bc.w * rho / sqrt(2.0 * M_PI * theta)
+                          : bc.w * rho * (double)rsqrtf(6.283185307179586f * (float)theta);
+  const double CM[3] = {pref * G0, pref * G1, 0.5 * pref * G2};
+  double r[3];
+  for (int i = 0; i < 3; ++i) r[i] = Uc[i] - CM[i];
+  for (int i = 0; i < 3; ++i) mu[i] = bc.A[3 * i] * r[0] + bc.A[3 * i + 1] * r[1] + bc.A[3 * i + 2] * r[2];
+  return 0;
+}
+
+// Per-cell parameters in the grouped layout of dvm_internal.cuh (d = 1).
+template <typename TC>
+__device__ void b_write_params(const BCase& bc, TC* prm, long long c, long long nc, double lam,
+                               double weight, double rho, double u, double theta, const double* nu,
+                               const double* mu) {
+  TC L, h;
+  if (sizeof(TC) == 8) {
+    L = (TC)(log2(weight) + log2(rho) - 0.5 * log2(2.0 * M_PI * theta));
+    h = (TC)(M_LOG2E * 0.5 / theta);
+  } else {
+    L = (TC)(log2f((float)weight) + log2f((float)rho) - 0.5f * log2f(6.283185307179586f * (float)theta));
+    h = (TC)(0.72134752044448170f / (float)theta);
+  }
+  prm[prm_at(row_lam(), c, nc)] = (TC)lam;
+  prm[prm_at(row_L(), c, nc)] = L;
+  prm[prm_at(row_u(0), c, nc)] = (TC)u;
+  prm[prm_at(row_h(1), c, nc)] = h;
+  for (int i = 0; i < 3; ++i) {
+    const double e = i == 2 ? 0.5 : 1.0;  // energy row: coefficient of v^2
+    prm[prm_at(row_nu(1, i), c, nc)] = (TC)(nu ? e * bc.w * nu[i] : 0.0);
+    prm[prm_at(row_mu(1, i), c, nc)] = (TC)(e * weight * bc.w * mu[i]);
+  }
+}
+
+template <typename TC>
+__global__ void k_b_cell_params(BPtrs p, int mode, int initial) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= p.ncells) return;
+  const BCase& bc = p.cases[p.cell_case[c]];
+  double Uc[3], mu[3], rho, u, theta;
+  for (int i = 0; i < 3; ++i) Uc[i] = p.U[i * p.ncells + c];
+  const double lam = p.lam[c];
+  if (mode == 0) {
+    const int rc = b_cell_mu<true>(bc, Uc, mu, rho, u, theta);
+    if (rc) { set_status(p.status, rc); return; }
+    b_write_params<double>(bc, p.eqp, c, p.ncells, lam, 1.0, rho, u, theta, nullptr, mu);
+    return;
+  }
+  const int rc = b_cell_mu<sizeof(TC) == 8>(bc, Uc, mu, rho, u, theta);
+  if (rc) { set_status(p.status, rc); return; }
+  const double weight = (p.scheme == DVM_FKS && initial) ? 0.0 : 1.0 - lam;
+  b_write_params<TC>(bc, (TC*)p.prm, c, p.ncells, lam, weight, rho, u, theta, nullptr, mu);
+}
+
+// f^0 = E[U^0] for the points of one case (grid: chunks x cases).
+template <typename TS, typename TC>
+__global__ void k_b_init_f(BPtrs p) {
+  const BCase& bc = p.cases[blockIdx.y];
+  const long long npts = (long long)bc.nx * bc.nv;
+  const long long nc = p.ncells;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(i / bc.nx), x = (int)(i % bc.nx);
+    const long long c = bc.c_off + x;
+    const double* e = p.eqp;
+    const TC v = (TC)((double)(bc.kmin + k) * bc.dv);
+    const TC du = v - (TC)e[prm_at(row_u(0), c, nc)];
+    const TC lin = (TC)e[prm_at(row_mu(1, 0), c, nc)] + (TC)e[prm_at(row_mu(1, 1), c, nc)] * v +
+                   (TC)e[prm_at(row_mu(1, 2), c, nc)] * v * v;
+    const TC ex = (TC)e[prm_at(row_L(), c, nc)] - (TC)e[prm_at(row_h(1), c, nc)] * du * du;
+    const TC f = (sizeof(TC) == 8 ? (TC)exp2((double)ex) : (TC)exp2f((float)ex)) + lin;
+    StoreT<TS>::store((TS*)p.F + bc.f_off + i, f);
+  }
+}
+
+__device__ inline int b_index(int t, int n, int bc) {
+  if (bc == DVM_BC_PERIODIC) {
+    if (t >= 0 && t < n) return t;
+    const int r = t % n;
+    return r < 0 ? r + n : r;
+  }
+  return t < 0 ? 0 : (t >= n ? n - 1 : t);
+}
+
+// One CTA per case: alpha, m, MUSCL sub-steps in shared memory, U_E; outflow
+// boundary pieces; queue reset.
+template <typename TS, typename TW, bool LIMITED, bool EULER>
+__global__ void __launch_bounds__(kB) k_b_euler(BPtrs p) {
+  extern __shared__ unsigned char s_raw[];
+  __shared__ double s_red[kB / 32];
+  const int ci = blockIdx.x, tid = threadIdx.x;
+  const BCase& bc = p.cases[ci];
+  const int nx = bc.nx;
+  const long long nc = p.ncells;
+  if (ci == 0 && tid == 0) *p.qcounter = 0u;
+  // outflow: the boundary pieces of every velocity at time n
+  if (bc.bc == DVM_BC_OUTFLOW) {
+    const long long n = *p.step;
+    const TS* F = (const TS*)p.F + bc.f_off;
+    TS* G = (TS*)p.ghost + bc.ghost_off;
+    for (int k = tid; k < bc.nv; k += kB) {
+      const long long o = transport_offset(bc.kmin + k, n, bc.p);
+      G[2 * k] = F[(long long)k * nx + wrap(0 - o, nx)];
+      G[2 * k + 1] = F[(long long)k * nx + wrap((long long)(nx - 1) - o, nx)];
+    }
+  }
+  if (!EULER) return;
+  TW* W0 = reinterpret_cast<TW*>(s_raw);
+  TW* W1 = W0 + 3 * nx;
+  // W = (1 - lambda) U and the alpha of every sub-step's initial state (Eq.
+  // Time2 per sub-step, the last one ending at dt)
+  double amax = 0.0;
+  for (int x = tid; x < nx; x += kB) {
+    const long long c = bc.c_off + x;
+    const double w = bc.all_free ? 0.0 : 1.0 - p.lam[c];
+    TW W[3];
+    for (int i = 0; i < 3; ++i) {
+      W[i] = (TW)(w * p.U[i * nc + c]);
+      W0[i * nx + x] = W[i];
+    }
+    double a[3];
+    state_alpha_of<1>(W, a);
+    amax = fmax(amax, a[0]);
+  }
+  double t = 0.0, a0 = 0.0;
+  int s = 0;
+  for (;; ++s) {
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if ((tid & 31) == 0) s_red[tid >> 5] = amax;
+    __syncthreads();
+    double al = 0.0;
+    for (int w = 0; w < kB / 32; ++w) al = fmax(al, s_red[w]);
+    __syncthreads();
+    if (s == 0) a0 = al;
+    if (bc.all_free) break;
+    double dtE;
+    bool last;
+    if (bc.forced_sub > 0) {
+      dtE = bc.dt / bc.forced_sub;
+      last = s + 1 == bc.forced_sub;
+    } else {
+      if (!(al > 0.0)) {
+        if (tid == 0) set_status(p.status, DVM_ERR_NONPHYSICAL);
+        break;
+      }
+      const double cfl = __ddiv_rn(__dmul_rn(0.5, bc.dx), al);
+      const double rem = __dsub_rn(bc.dt, t);
+      last = cfl >= rem;
+      dtE = last ? rem : cfl;
+    }
+    const TW kk = (TW)(dtE / bc.dx), alw = (TW)al;
+    const TW* src = (s & 1) ? W1 : W0;
+    TW* dst = (s & 1) ? W0 : W1;
+    amax = 0.0;
+    for (int x = tid; x < nx; x += kB) {
+      TW Us[5][3], Fs[5][3], Wn[3];
+      for (int o = 0; o < 5; ++o) {
+        const int xx = b_index(x + o - 2, nx, bc.bc);
+        for (int i = 0; i < 3; ++i) Us[o][i] = src[i * nx + xx];
+        euler_flux<TW, 1>(Us[o], 0, Fs[o]);
+      }
+      for (int i = 0; i < 3; ++i) {
+        TW Gp[5], Gm[5], psi[2];
+        for (int o = 0; o < 5; ++o) {
+          Gp[o] = Fs[o][i] + alw * Us[o][i];
+          Gm[o] = Fs[o][i] - alw * Us[o][i];
+        }
+        for (int f = 0; f < 2; ++f) {
+          const int j = 1 + f;
+          const TW sp = slope<TW, LIMITED>(Gp[j] - Gp[j - 1], Gp[j + 1] - Gp[j]);
+          const TW sm = slope<TW, LIMITED>(Gm[j + 1] - Gm[j], Gm[j + 2] - Gm[j + 1]);
+          psi[f] = TW(0.5) * (Fs[j][i] + Fs[j + 1][i]) - TW(0.5) * alw * (Us[j + 1][i] - Us[j][i]) +
+                   TW(0.25) * (sp - sm);
+        }
+        Wn[i] = Us[2][i] - kk * (psi[1] - psi[0]);
+        dst[i * nx + x] = Wn[i];
+      }
+      double a[3];
+      state_alpha_of<1>(Wn, a);
+      amax = fmax(amax, a[0]);
+    }
+    __syncthreads();
+    t = __dadd_rn(t, dtE);
+    if (last) break;
+    if (s + 1 >= 1000000) {
+      if (tid == 0) set_status(p.status, DVM_ERR_CFL);
+      break;
+    }
+  }
+  const int m = bc.all_free ? 0 : s + 1;
+  if (tid == 0) {
+    p.msub[ci] = m;
+    p.alpha[ci] = a0;
+  }
+  const TW* res = (m & 1) ? W1 : W0;
+  for (int x = tid; x < nx; x += kB)
+    for (int i = 0; i < 3; ++i) p.UE[i * nc + bc.c_off + x] = (double)res[i * nx + x];
+}
+
+// Persistent kinetic pass over (case, tile) items.
+template <typename TS, typename TC, bool HOFKS>
+__global__ void k_b_kinetic(BPtrs p) {
+  __shared__ int s_item;
+  __shared__ BCase s_case;
+  __shared__ int s_slot[kMaxV1], s_delta[kMaxV1];
+  const long long n = *p.step;
+  const long long nc = p.ncells;
+  const TC* prm = (const TC*)p.prm;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(p.qcounter, 1u);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= p.nitems) return;
+    const BItem item = p.items[it];
+    if (threadIdx.x == 0) s_case = p.cases[item.bcase];
+    __syncthreads();
+    const BCase& bc = s_case;
+    for (int k = threadIdx.x; k < bc.nv; k += blockDim.x) {
+      const long long kg = bc.kmin + k;
+      const long long o1 = transport_offset(kg, n + 1, bc.p);
+      s_slot[k] = wrap(o1, bc.nx);
+      s_delta[k] = (int)(o1 - transport_offset(kg, n, bc.p));
+    }
+    __syncthreads();
+    const TS* G = (const TS*)p.ghost + bc.ghost_off;
+    TS* F = (TS*)p.F + bc.f_off;
+    for (int j = 0; j < p.cpt; ++j) {
+      const int x = item.x0 + threadIdx.x + j * blockDim.x;
+      if (x >= bc.nx) break;
+      const long long c = bc.c_off + x;
+      const TC lam_c = prm[prm_at(row_lam(), c, nc)];
+      double acc[6] = {0, 0, 0, 0, 0, 0};
+      TC r[6] = {0, 0, 0, 0, 0, 0};
+      for (int k = 0; k < bc.nv; ++k) {
+        int s = x - s_delta[k];
+        bool clamped = false;
+        if (bc.bc == DVM_BC_PERIODIC) {
+          s = b_index(s, bc.nx, DVM_BC_PERIODIC);
+        } else if (s < 0 || s >= bc.nx) {
+          s = s < 0 ? 0 : bc.nx - 1;
+          clamped = true;
+        }
+        int q = x - s_slot[k];
+        if (q < 0) q += bc.nx;
+        const TC fv = clamped ? StoreT<TS>::load(G + 2 * k + (s == 0 ? 0 : 1))
+                              : StoreT<TS>::load(F + (long long)k * bc.nx + q);
+        const long long cs = bc.c_off + s;
+        const TC v = (TC)((double)(bc.kmin + k) * bc.dv);
+        const TC v2 = v * v;
+        const TC du = v - prm[prm_at(row_u(0), cs, nc)];
+        const TC ex = prm[prm_at(row_L(), cs, nc)] - prm[prm_at(row_h(1), cs, nc)] * du * du;
+        const TC M = sizeof(TC) == 8 ? (TC)exp2((double)ex) : (TC)exp2f((float)ex);
+        const TC lm = prm[prm_at(row_mu(1, 0), cs, nc)] + prm[prm_at(row_mu(1, 1), cs, nc)] * v +
+                      prm[prm_at(row_mu(1, 2), cs, nc)] * v2;
+        TC fnew;
+        if (HOFKS) {
+          const TC ln = prm[prm_at(row_nu(1, 0), cs, nc)] + prm[prm_at(row_nu(1, 1), cs, nc)] * v +
+                        prm[prm_at(row_nu(1, 2), cs, nc)] * v2;
+          const TC a = prm[prm_at(row_lam(), cs, nc)] * (fv + ln);  // T(lambda f^n)
+          const TC b = M + lm;                                        // T((1 - lambda) E^n)
+          fnew = a + b;
+          r[0] += a; r[1] += a * v; r[2] += a * v2;
+          r[3] += b; r[4] += b * v; r[5] += b * v2;
+        } else {
+          const TC fs = fv + M + lm;
+          fnew = lam_c * fs;
+          r[0] += fs; r[1] += fs * v; r[2] += fs * v2;
+        }
+        StoreT<TS>::store(F + (long long)k * bc.nx + q, fnew);
+        if ((k & 31) == 31) {
+          for (int t = 0; t < 6; ++t) acc[t] += (double)r[t], r[t] = TC(0);
+        }
+      }
+      for (int t = 0; t < 6; ++t) acc[t] += (double)r[t];
+      for (int t = 0; t < (HOFKS ? 6 : 3); ++t) p.acc[t * nc + c] = (t % 3 == 2 ? 0.5 : 1.0) * acc[t];
+    }
+  }
+}
+
+// End of step for every cell of every case.
+template <typename TC, bool HOFKS>
+__global__ void k_b_finalize(BPtrs p) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c == 0) *p.step += 1;
+  if (c >= p.ncells) return;
+  const long long nc = p.ncells;
+  const BCase& bc = p.cases[p.cell_case[c]];
+  double Un[3], nu[3];
+  if (HOFKS) {
+    double r[3];
+    for (int i = 0; i < 3; ++i) {
+      const double us = bc.w * p.acc[i * nc + c], um = bc.w * p.acc[(3 + i) * nc + c];
+      const double ue = p.UE[i * nc + c];
+      r[i] = ue - um;
+      Un[i] = us + ue;
+      p.Us[i * nc + c] = us;
+      p.UM[i * nc + c] = um;
+    }
+    for (int i = 0; i < 3; ++i) nu[i] = bc.A[3 * i] * r[0] + bc.A[3 * i + 1] * r[1] + bc.A[3 * i + 2] * r[2];
+  } else {
+    for (int i = 0; i < 3; ++i) {
+      Un[i] = bc.w * p.acc[i * nc + c];
+      p.Us[i * nc + c] = Un[i];
+    }
+  }
+  for (int i = 0; i < 3; ++i) p.U[i * nc + c] = Un[i];
+  double mu[3], rho, u, theta;
+  const int rc = b_cell_mu<sizeof(TC) == 8>(bc, Un, mu, rho, u, theta);
+  if (rc) { set_status(p.status, rc); return; }
+  const double lam = p.lam[c];
+  b_write_params<TC>(bc, (TC*)p.prm, c, nc, lam, 1.0 - lam, rho, u, theta, HOFKS ? nu : nullptr, mu);
+}
+
+// f of one case at the cell centres (stored piece + deferred term), FP64.
+template <typename TS, typename TC>
+__global__ void k_b_materialize(BPtrs p, int ci, double* out) {
+  const BCase& bc = p.cases[ci];
+  const long long npts = (long long)bc.nx * bc.nv;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= npts) return;
+  const int k = (int)(i / bc.nx), x = (int)(i % bc.nx);
+  const long long n = *p.step, nc = p.ncells, c = bc.c_off + x;
+  const TC* prm = (const TC*)p.prm;
+  const int q = wrap((long long)x - transport_offset(bc.kmin + k, n, bc.p), bc.nx);
+  const double v = (double)(bc.kmin + k) * bc.dv;
+  double f = (double)StoreT<TS>::load((const TS*)p.F + bc.f_off + (long long)k * bc.nx + q);
+  if (p.scheme == DVM_FKS) {
+    const double du = v - (double)prm[prm_at(row_u(0), c, nc)];
+    f += exp2((double)prm[prm_at(row_L(), c, nc)] - (double)prm[prm_at(row_h(1), c, nc)] * du * du) +
+         (double)prm[prm_at(row_mu(1, 0), c, nc)] + (double)prm[prm_at(row_mu(1, 1), c, nc)] * v +
+         (double)prm[prm_at(row_mu(1, 2), c, nc)] * v * v;
+  } else {
+    f += (double)prm[prm_at(row_nu(1, 0), c, nc)] + (double)prm[prm_at(row_nu(1, 1), c, nc)] * v +
+         (double)prm[prm_at(row_nu(1, 2), c, nc)] * v * v;
+  }
+  out[i] = f;
+}
+
+}  // namespace
+}  // namespace dvm
+
+using namespace dvm;
+
+struct dvm_batch {
+  std::vector<BCase> cases;
+  std::vector<int> nxs;
+  int ncases = 0;
+  long long ncells = 0, npoints = 0;
+  int precision = DVM_F32, scheme = DVM_HOFKS;
+  int threads = 128, cpt = 1;
+  int blocks = 0;
+  int max_nx = 0;
+  size_t euler_smem = 0;
+  BPtrs p{};
+  std::vector<void*> allocs;
+  cudaStream_t stream = nullptr, cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int* pinned = nullptr;
+  int status = 0;
+  std::string err;
+  bool state_set = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+namespace {
+
+int bfail(dvm_batch* b, int code, const std::string& m) {
+  if (b && b->status == 0) b->status = code;
+  if (b) b->err = m;
+  return code;
+}
+
+int bcheck(dvm_batch* b, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return 0;
+  return bfail(b, DVM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+int balloc(dvm_batch* b, T** ptr, size_t bytes) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, bytes < 256 ? 256 : bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(b, DVM_ERR_OOM, "batch allocation failed");
+  }
+  b->allocs.push_back(q);
+  *ptr = (T*)q;
+  return 0;
+}
+
+// Work items: tiles of threads * cpt cells, ordered by decreasing cost.
+int build_items(dvm_batch* b) {
+  std::vector<std::pair<long long, BItem>> v;
+  const int T = b->threads * b->cpt;
+  for (int i = 0; i < b->ncases; ++i)
+    for (int x0 = 0; x0 < b->cases[i].nx; x0 += T) {
+      const long long cells = std::min(T, b->cases[i].nx - x0);
+      v.push_back({cells * b->cases[i].nv, BItem{i, x0}});
+    }
+  std::stable_sort(v.begin(), v.end(), [](const auto& a, const auto& c) { return a.first > c.first; });
+  std::vector<BItem> items(v.size());
+  for (size_t i = 0; i < v.size(); ++i) items[i] = v[i].second;
+  if (b->p.items) cudaFree((void*)b->p.items);
+  BItem* d = nullptr;
+  if (cudaMalloc(&d, sizeof(BItem) * items.size()) != cudaSuccess) return bfail(b, DVM_ERR_OOM, "items");
+  b->p.items = d;
+  b->p.nitems = (int)items.size();
+  return bcheck(b, cudaMemcpy(d, items.data(), sizeof(BItem) * items.size(), cudaMemcpyHostToDevice),
+                "items upload");
+}
+
+template <typename TS, typename TC, bool HO>
+void launch_b_kinetic_t(dvm_batch* b, cudaStream_t s) {
+  k_b_kinetic<TS, TC, HO><<<b->blocks, b->threads, 0, s>>>(b->p);
+}
+
+int kinetic_blocks(dvm_batch* b) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const bool ho = b->scheme != DVM_FKS;
+  if (b->precision == DVM_F64)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ho ? (const void*)k_b_kinetic<double, double, true>
+                                                           : (const void*)k_b_kinetic<double, double, false>, b->threads, 0);
+  else if (b->precision == DVM_F32)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ho ? (const void*)k_b_kinetic<float, float, true>
+                                                           : (const void*)k_b_kinetic<float, float, false>, b->threads, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ho ? (const void*)k_b_kinetic<__nv_bfloat16, float, true>
+                                                           : (const void*)k_b_kinetic<__nv_bfloat16, float, false>, b->threads, 0);
+  return sms * (per < 1 ? 1 : per);
+}
+
+void launch_kinetic(dvm_batch* b, cudaStream_t s) {
+  const bool ho = b->scheme != DVM_FKS;
+  if (b->precision == DVM_F64) { if (ho) launch_b_kinetic_t<double, double, true>(b, s); else launch_b_kinetic_t<double, double, false>(b, s); }
+  else if (b->precision == DVM_F32) { if (ho) launch_b_kinetic_t<float, float, true>(b, s); else launch_b_kinetic_t<float, float, false>(b, s); }
+  else { if (ho) launch_b_kinetic_t<__nv_bfloat16, float, true>(b, s); else launch_b_kinetic_t<__nv_bfloat16, float, false>(b, s); }
+}
+
+template <typename TS, typename TW>
+void launch_euler_t(dvm_batch* b, cudaStream_t s) {
+  const size_t sm = b->euler_smem;
+  if (b->scheme == DVM_FKS) k_b_euler<TS, TW, true, false><<<b->ncases, kB, sm, s>>>(b->p);
+  else if (b->scheme == DVM_HOFKS) k_b_euler<TS, TW, true, true><<<b->ncases, kB, sm, s>>>(b->p);
+  else k_b_euler<TS, TW, false, true><<<b->ncases, kB, sm, s>>>(b->p);
+}
+
+void launch_euler(dvm_batch* b, cudaStream_t s) {
+  if (b->precision == DVM_F64) launch_euler_t<double, double>(b, s);
+  else if (b->precision == DVM_F32) launch_euler_t<float, float>(b, s);
+  else launch_euler_t<__nv_bfloat16, float>(b, s);
+}
+
+template <typename TS, typename TW>
+void set_euler_attr_t(dvm_batch* b) {
+  const int sm = (int)b->euler_smem;
+  cudaFuncSetAttribute(k_b_euler<TS, TW, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_b_euler<TS, TW, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_b_euler<TS, TW, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+}
+
+void launch_finalize(dvm_batch* b, cudaStream_t s) {
+  const unsigned nb = (unsigned)((b->ncells + kB - 1) / kB);
+  const bool ho = b->scheme != DVM_FKS;
+  if (b->precision == DVM_F64) { if (ho) k_b_finalize<double, true><<<nb, kB, 0, s>>>(b->p); else k_b_finalize<double, false><<<nb, kB, 0, s>>>(b->p); }
+  else { if (ho) k_b_finalize<float, true><<<nb, kB, 0, s>>>(b->p); else k_b_finalize<float, false><<<nb, kB, 0, s>>>(b->p); }
+}
+
+int enqueue(dvm_batch* b, cudaStream_t s, bool timed = false) {
+  launch_euler(b, s);
+  if (timed) cudaEventRecord(b->e0, s);
+  launch_kinetic(b, s);
+  if (timed) cudaEventRecord(b->e1, s);
+  launch_finalize(b, s);
+  return bcheck(b, cudaGetLastError(), "batch launch");
+}
+
+void drop(dvm_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+int ensure_graph(dvm_batch* b) {
+  if (b->exec) return 0;
+  int rc = bcheck(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "capture");
+  if (rc) return rc;
+  rc = enqueue(b, b->cap);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+  if (rc) return rc;
+  if ((rc = bcheck(b, e, "end capture"))) return rc;
+  b->graph = g;
+  return bcheck(b, cudaGraphInstantiate(&b->exec, g, 0), "instantiate");
+}
+
+int bsync(dvm_batch* b) {
+  int rc = bcheck(b, cudaMemcpyAsync(b->pinned, b->p.status, sizeof(int), cudaMemcpyDeviceToHost, b->stream), "status");
+  if (rc) return rc;
+  if ((rc = bcheck(b, cudaStreamSynchronize(b->stream), "sync"))) return rc;
+  if (*b->pinned) return bfail(b, *b->pinned, "device error in a batch case");
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dvm_batch_create(const dvm_config* cfgs, int ncases, void* cuda_stream, dvm_batch** out) {
+  if (!cfgs || ncases < 1 || !out) return DVM_ERR_ARG;
+  *out = nullptr;
+  dvm_batch* b = new dvm_batch();
+  b->ncases = ncases;
+  b->precision = cfgs[0].precision;
+  b->scheme = cfgs[0].scheme;
+  b->stream = (cudaStream_t)cuda_stream;
+  long long cells = 0, pts = 0;
+  int ghost = 0;
+  std::vector<double> lam;
+  for (int i = 0; i < ncases; ++i) {
+    Geom g;
+    std::string msg;
+    if (make_geom(&cfgs[i], &g, &msg) || g.d != 1 || cfgs[i].precision != b->precision ||
+        cfgs[i].scheme != b->scheme || g.nx[0] > kMaxBatchNx || cfgs[i].tau_field) {
+      delete b;
+      return DVM_ERR_ARG;
+    }
+    BCase c{};
+    c.nx = g.nx[0];
+    c.nv = g.nv[0];
+    c.kmin = g.kmin[0];
+    c.p = g.p;
+    c.bc = g.bc[0];
+    c.forced_sub = g.forced_sub;
+    c.ghost_off = ghost;
+    c.f_off = pts;
+    c.c_off = cells;
+    c.dx = g.dx;
+    c.dv = g.dv;
+    c.dt = g.dt;
+    c.w = g.w;
+    double A[kMaxM * kMaxM];
+    if (invert_moment_matrix(g, A)) { delete b; return DVM_ERR_ARG; }
+    for (int j = 0; j < 9; ++j) c.A[j] = A[j];
+    const double l = exp(-g.dt / cfgs[i].tau);
+    if (!(cfgs[i].tau >= 0)) { delete b; return DVM_ERR_ARG; }
+    c.all_free = l == 1.0;
+    for (int x = 0; x < c.nx; ++x) lam.push_back(l);
+    b->cases.push_back(c);
+    b->max_nx = std::max(b->max_nx, c.nx);
+    ghost += 2 * c.nv;
+    cells += c.nx;
+    pts += (long long)c.nx * c.nv;
+  }
+  b->ncells = cells;
+  b->npoints = pts;
+  BPtrs& p = b->p;
+  p.ncases = ncases;
+  p.ncells = cells;
+  p.scheme = b->scheme;
+  const size_t es = b->precision == DVM_F64 ? 8 : (b->precision == DVM_F32 ? 4 : 2);
+  const size_t tc = b->precision == DVM_F64 ? 8 : 4;
+  std::vector<int> cell_case;
+  for (int i = 0; i < ncases; ++i)
+    for (int x = 0; x < b->cases[i].nx; ++x) cell_case.push_back(i);
+  int rc = 0;
+  BCase* dcases = nullptr;
+  int* dcc = nullptr;
+  rc |= balloc(b, &dcases, sizeof(BCase) * ncases);
+  rc |= balloc(b, &dcc, sizeof(int) * cells);
+  rc |= balloc(b, &p.F, es * pts);
+  rc |= balloc(b, &p.ghost, es * ghost);
+  rc |= balloc(b, &p.U, 8 * 3 * cells);
+  rc |= balloc(b, &p.lam, 8 * cells);
+  rc |= balloc(b, &p.UE, 8 * 3 * cells);
+  rc |= balloc(b, &p.UM, 8 * 3 * cells);
+  rc |= balloc(b, &p.Us, 8 * 3 * cells);
+  rc |= balloc(b, &p.acc, 8 * 6 * cells);
+  rc |= balloc(b, &p.prm, tc * prm_rows(1) * cells);
+  rc |= balloc(b, &p.eqp, 8 * prm_rows(1) * cells);
+  rc |= balloc(b, &p.msub, sizeof(int) * ncases);
+  rc |= balloc(b, &p.alpha, sizeof(double) * ncases);
+  rc |= balloc(b, &p.status, 256);
+  if (rc) { dvm_batch_destroy(b); return DVM_ERR_OOM; }
+  p.step = (long long*)((char*)p.status + 64);
+  p.qcounter = (unsigned*)((char*)p.status + 128);
+  p.cases = dcases;
+  p.cell_case = dcc;
+  p.cpt = b->cpt;
+  if (cudaMemcpy(dcases, b->cases.data(), sizeof(BCase) * ncases, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dcc, cell_case.data(), sizeof(int) * cells, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p.lam, lam.data(), 8 * cells, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(p.status, 0, 256) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMallocHost((void**)&b->pinned, 64) != cudaSuccess ||
+      cudaEventCreate(&b->e0) != cudaSuccess || cudaEventCreate(&b->e1) != cudaSuccess) {
+    cudaGetLastError();
+    dvm_batch_destroy(b);
+    return DVM_ERR_CUDA;
+  }
+  const size_t tw = b->precision == DVM_F64 ? 8 : 4;
+  b->euler_smem = 2 * 3 * (size_t)b->max_nx * tw;
+  if (b->precision == DVM_F64) set_euler_attr_t<double, double>(b);
+  else if (b->precision == DVM_F32) set_euler_attr_t<float, float>(b);
+  else set_euler_attr_t<__nv_bfloat16, float>(b);
+  b->blocks = kinetic_blocks(b);
+  if (build_items(b)) { dvm_batch_destroy(b); return DVM_ERR_CUDA; }
+  *out = b;
+  return 0;
+}
+
+void dvm_batch_destroy(dvm_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  else cudaDeviceSynchronize();
+  drop(b);
+  if (b->p.items) cudaFree((void*)b->p.items);
+  for (void* q : b->allocs) cudaFree(q);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->pinned) cudaFreeHost(b->pinned);
+  if (b->e0) cudaEventDestroy(b->e0);
+  if (b->e1) cudaEventDestroy(b->e1);
+  delete b;
+}
+
+const char* dvm_batch_last_error(const dvm_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+int dvm_batch_sizes(const dvm_batch* b, long long* cells, long long* points) {
+  if (!b) return DVM_ERR_ARG;
+  if (cells) *cells = b->ncells;
+  if (points) *points = b->npoints;
+  return 0;
+}
+
+int dvm_batch_set_state_moments(dvm_batch* b, const double* U, int on_device) {
+  if (!b || !U) return DVM_ERR_ARG;
+  if (b->status) return b->status;
+  cudaStream_t s = b->stream;
+  int rc = bcheck(b, cudaMemcpyAsync(b->p.U, U, 8 * 3 * b->ncells, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s), "upload");
+  rc |= bcheck(b, cudaMemsetAsync(b->p.status, 0, 256, s), "memset");
+  if (rc) return b->status;
+  const unsigned nb = (unsigned)((b->ncells + kB - 1) / kB);
+  if (b->precision == DVM_F64) k_b_cell_params<double><<<nb, kB, 0, s>>>(b->p, 0, 1);
+  else k_b_cell_params<float><<<nb, kB, 0, s>>>(b->p, 0, 1);
+  dim3 gi(64, b->ncases);
+  if (b->precision == DVM_F64) k_b_init_f<double, double><<<gi, kB, 0, s>>>(b->p);
+  else if (b->precision == DVM_F32) k_b_init_f<float, float><<<gi, kB, 0, s>>>(b->p);
+  else k_b_init_f<__nv_bfloat16, float><<<gi, kB, 0, s>>>(b->p);
+  if (b->precision == DVM_F64) k_b_cell_params<double><<<nb, kB, 0, s>>>(b->p, 1, 1);
+  else k_b_cell_params<float><<<nb, kB, 0, s>>>(b->p, 1, 1);
+  if ((rc = bcheck(b, cudaGetLastError(), "init launch"))) return rc;
+  if ((rc = bsync(b))) return rc;
+  b->state_set = true;
+  return 0;
+}
+
+int dvm_batch_step_async(dvm_batch* b, int nsteps) {
+  if (!b) return DVM_ERR_ARG;
+  if (b->status) return b->status;
+  if (!b->state_set) return bfail(b, DVM_ERR_STATE, "step before a state was set");
+  int rc = ensure_graph(b);
+  if (rc) return rc;
+  for (int i = 0; i < nsteps; ++i)
+    if ((rc = bcheck(b, cudaGraphLaunch(b->exec, b->stream), "graph launch"))) return rc;
+  return 0;
+}
+
+int dvm_batch_sync_status(dvm_batch* b) {
+  if (!b) return DVM_ERR_ARG;
+  if (b->status) return b->status;
+  return bsync(b);
+}
+
+int dvm_batch_step(dvm_batch* b, int nsteps) {
+  const int rc = dvm_batch_step_async(b, nsteps);
+  return rc ? rc : bsync(b);
+}
+
+int dvm_batch_moments(dvm_batch* b, double* out, int on_device) {
+  if (!b || !out) return DVM_ERR_ARG;
+  if (b->status) return b->status;
+  int rc = bcheck(b, cudaMemcpyAsync(out, b->p.U, 8 * 3 * b->ncells, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream), "copy");
+  return rc ? rc : bcheck(b, cudaStreamSynchronize(b->stream), "sync");
+}
+
+int dvm_batch_get_f(dvm_batch* b, int icase, double* out) {
+  if (!b || !out || icase < 0 || icase >= b->ncases) return DVM_ERR_ARG;
+  if (b->status) return b->status;
+  const long long npts = (long long)b->cases[icase].nx * b->cases[icase].nv;
+  double* d = nullptr;
+  int rc = bcheck(b, cudaMalloc(&d, 8 * npts), "staging");
+  if (rc) return rc;
+  const unsigned nb = (unsigned)((npts + kB - 1) / kB);
+  if (b->precision == DVM_F64) k_b_materialize<double, double><<<nb, kB, 0, b->stream>>>(b->p, icase, d);
+  else if (b->precision == DVM_F32) k_b_materialize<float, float><<<nb, kB, 0, b->stream>>>(b->p, icase, d);
+  else k_b_materialize<__nv_bfloat16, float><<<nb, kB, 0, b->stream>>>(b->p, icase, d);
+  rc = bcheck(b, cudaGetLastError(), "materialize");
+  if (!rc) rc = bcheck(b, cudaMemcpyAsync(out, d, 8 * npts, cudaMemcpyDeviceToHost, b->stream), "copy");
+  if (!rc) rc = bcheck(b, cudaStreamSynchronize(b->stream), "sync");
+  cudaFree(d);
+  return rc;
+}
+
+int dvm_batch_info(dvm_batch* b, long long* n, int* substeps, double* alpha) {
+  if (!b) return DVM_ERR_ARG;
+  if (b->status) return b->status;
+  int rc = 0;
+  if (n) rc |= bcheck(b, cudaMemcpyAsync(n, b->p.step, 8, cudaMemcpyDeviceToHost, b->stream), "copy");
+  if (substeps) rc |= bcheck(b, cudaMemcpyAsync(substeps, b->p.msub, sizeof(int) * b->ncases, cudaMemcpyDeviceToHost, b->stream), "copy");
+  if (alpha) rc |= bcheck(b, cudaMemcpyAsync(alpha, b->p.alpha, 8 * b->ncases, cudaMemcpyDeviceToHost, b->stream), "copy");
+  rc |= bcheck(b, cudaStreamSynchronize(b->stream), "sync");
+  return rc ? b->status : 0;
+}
+
+int dvm_batch_set_tiling(dvm_batch* b, int threads, int cells_per_thread) {
+  if (!b || threads < 32 || threads > 1024 || (threads & 31) || cells_per_thread < 1 || cells_per_thread > 8)
+    return DVM_ERR_ARG;
+  if (b->status) return b->status;
+  b->threads = threads;
+  b->cpt = cells_per_thread;
+  b->p.cpt = cells_per_thread;
+  b->blocks = kinetic_blocks(b);
+  drop(b);
+  return build_items(b);
+}
+
+int dvm_batch_kinetic_ms(dvm_batch* b, int nsteps, double* ms) {
+  if (!b || !ms || nsteps < 1) return DVM_ERR_ARG;
+  if (b->status) return b->status;
+  if (!b->state_set) return bfail(b, DVM_ERR_STATE, "no state");
+  double tot = 0.0;
+  for (int i = 0; i < nsteps; ++i) {
+    int rc = enqueue(b, b->stream, true);
+    if (rc) return rc;
+    if ((rc = bcheck(b, cudaEventSynchronize(b->e1), "sync"))) return rc;
+    float t = 0.f;
+    cudaEventElapsedTime(&t, b->e0, b->e1);
+    tot += t;
+  }
+  *ms = tot / nsteps;
+  return bsync(b);
+}
+
+int dvm_batch_autotune(dvm_batch* b, int* threads, int* cells_per_thread, double* best_ms) {
+  if (!b) return DVM_ERR_ARG;
+  if (b->status) return b->status;
+  if (!b->state_set) return bfail(b, DVM_ERR_STATE, "no state");
+  // time the kinetic pass of each candidate tile on the current state, then
+  // put f back: the pass rewrites f in place
+  const size_t es = b->precision == DVM_F64 ? 8 : (b->precision == DVM_F32 ? 4 : 2);
+  const size_t fb = es * (size_t)b->npoints;
+  void* save = nullptr;
+  int rc = bcheck(b, cudaMalloc(&save, fb), "autotune staging");
+  if (rc) return rc;
+  cudaStream_t s = b->stream;
+  cudaMemcpyAsync(save, b->p.F, fb, cudaMemcpyDeviceToDevice, s);
+  // the Euler launch prepares the ghost pieces and the queue of this step
+  launch_euler(b, s);
+  const int cand_t[3] = {64, 128, 256}, cand_c[2] = {1, 2};
+  double best = 1e30;
+  int bt = b->threads, bcpt = b->cpt;
+  for (int ti : cand_t)
+    for (int ci : cand_c) {
+      if ((rc = dvm_batch_set_tiling(b, ti, ci))) break;
+      float acc = 0.f;
+      for (int r = 0; r < 3; ++r) {
+        cudaMemcpyAsync(b->p.F, save, fb, cudaMemcpyDeviceToDevice, s);
+        cudaMemsetAsync(b->p.qcounter, 0, sizeof(unsigned), s);
+        cudaEventRecord(b->e0, s);
+        launch_kinetic(b, s);
+        cudaEventRecord(b->e1, s);
+        cudaEventSynchronize(b->e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, b->e0, b->e1);
+        if (r > 0) acc += t;
+      }
+      if (acc / 2 < best) {
+        best = acc / 2;
+        bt = ti;
+        bcpt = ci;
+      }
+    }
+  cudaMemcpyAsync(b->p.F, save, fb, cudaMemcpyDeviceToDevice, s);
+  cudaStreamSynchronize(s);
+  cudaFree(save);
+  if (!rc) rc = dvm_batch_set_tiling(b, bt, bcpt);
+  if (rc) return rc;
+  if (threads) *threads = bt;
+  if (cells_per_thread) *cells_per_thread = bcpt;
+  if (best_ms) *best_ms = best;
+  return bcheck(b, cudaGetLastError(), "autotune");
+}
+
+}  // extern "C"

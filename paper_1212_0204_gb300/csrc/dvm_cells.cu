@@ -14,6 +14,7 @@
 #include <mutex>
 
 #include "dvm_internal.cuh"
+#include "dvm_math.cuh"
 
 namespace dvm {
 namespace {
@@ -31,78 +32,6 @@ __device__ inline void cell_coords(const Geom& g, long long c, int x[3]) {
 
 __device__ inline long long cell_index(const Geom& g, const int x[3]) {
   return x[0] + (long long)g.nx[0] * (x[1] + (long long)g.nx[1] * x[2]);
-}
-
-// Primitive variables (Eqs. Mo and E): rho, u, theta.  Written without
-// contractions so that the value matches a plain IEEE evaluation bit for bit
-// (alpha and the number of Euler sub-steps depend on it).
-template <int D>
-__device__ inline void primitives(const double* U, double& rho, double u[3], double& theta) {
-  rho = U[0];
-  double u2 = 0.0;
-  u[0] = u[1] = u[2] = 0.0;
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    u[i] = __ddiv_rn(U[1 + i], rho);
-    u2 = __dadd_rn(u2, __dmul_rn(u[i], u[i]));
-  }
-  theta = __ddiv_rn(__dsub_rn(__ddiv_rn(__dmul_rn(2.0, U[D + 1]), rho), u2), (double)D);
-}
-
-// Sums over one velocity axis of g(k) = exp(-(v_k - u)^2 / (2 theta)) times
-// 1, v_k, v_k^2, in FP64.  The Gaussian is evaluated from its peak outwards
-// with the recurrence g(k+1) = g(k) r_k, r_{k+1} = r_k q, q = exp(-dv^2/theta)
-// (ratios of consecutive Gaussian samples on a uniform grid): three
-// exponentials per axis instead of one per velocity.
-__device__ void gauss_axis_sums(int n, int kmin, double dv, double u, double theta, double& G0,
-                                double& G1, double& G2) {
-  const double h = 0.5 / theta;
-  int k0 = (int)floor(u / dv + 0.5) - kmin;
-  k0 = k0 < 0 ? 0 : (k0 >= n ? n - 1 : k0);
-  const double v0 = (kmin + k0) * dv;
-  const double g0 = exp(-(v0 - u) * (v0 - u) * h);
-  const double q = exp(-2.0 * dv * dv * h);
-  G0 = g0;
-  G1 = v0 * g0;
-  G2 = v0 * v0 * g0;
-  double g = g0, r = exp(-(2.0 * (v0 - u) * dv + dv * dv) * h);
-  for (int k = k0 + 1; k < n; ++k) {
-    g *= r;
-    r *= q;
-    const double v = (kmin + k) * dv;
-    G0 += g;
-    G1 += v * g;
-    G2 += v * v * g;
-  }
-  g = g0;
-  double s = exp((2.0 * (v0 - u) * dv - dv * dv) * h);
-  for (int k = k0 - 1; k >= 0; --k) {
-    g *= s;
-    s *= q;
-    const double v = (kmin + k) * dv;
-    G0 += g;
-    G1 += v * g;
-    G2 += v * v * g;
-  }
-}
-
-// Same sums with FP32 samples exp2(-(v - u)^2 log2(e) / (2 theta)) and FP32
-// accumulation, for the FP32-storage builds.
-__device__ void gauss_axis_sums_f32(int n, int kmin, float dv, float u, float theta, double& G0,
-                                    double& G1, double& G2) {
-  const float h2 = 0.72134752044448170f / theta;  // log2(e) / 2
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-  for (int k = 0; k < n; ++k) {
-    const float v = (kmin + k) * dv;
-    const float dd = v - u;
-    const float gk = exp2f(-h2 * dd * dd);
-    s0 += gk;
-    s1 = fmaf(v, gk, s1);
-    s2 = fmaf(v * v, gk, s2);
-  }
-  G0 = s0;
-  G1 = s1;
-  G2 = s2;
 }
 
 // mu = (C C^T)^{-1} (U - C M[U]) of Eq. minimMax, with C M[U] from the
@@ -259,25 +188,11 @@ __global__ void k_prim_to_cons(Geom g, const double* rho, const double* u, const
 
 // ------------------------------------------------------------ alpha and m
 
-// alpha_i contribution of one cell: |u_i| + sqrt(gamma theta), gamma = 1 + 2/d
-// (largest eigenvalue of the Euler system along i), evaluated without
-// contractions like the primitive variables.
+// Block max of alpha, atomically merged; the last block to finish publishes
+// the three maxima as the alpha of the first Euler sub-step (slot 0), clears
+// the other two slots and resets the reduction.
 template <int D>
-__device__ inline void alpha_of(const double* Uc, double a[3]) {
-  double rho, u[3], theta;
-  primitives<D>(Uc, rho, u, theta);
-  const double gamma = __dadd_rn(1.0, __ddiv_rn(2.0, (double)D));
-  const double cs = sqrt(__dmul_rn(gamma, theta));
-  a[0] = a[1] = a[2] = 0.0;
-#pragma unroll
-  for (int i = 0; i < D; ++i) a[i] = (rho > 0.0 && theta > 0.0) ? __dadd_rn(fabs(u[i]), cs) : 0.0;
-}
-
-// Block max of alpha, atomically merged; the last block to finish turns the
-// three maxima into the number of Euler sub-steps (Eq. Time2:
-// dt_E <= dx / (2 sum_i alpha_i)) and resets the reduction.
-template <int D>
-__device__ void alpha_reduce_and_substeps(const Geom& g, const DevPtrs& p, const double a[3]) {
+__device__ void alpha_reduce_publish(const Geom& g, const DevPtrs& p, const double a[3]) {
   __shared__ double red[3][kBlock / 32];
   __shared__ bool last;
 #pragma unroll
@@ -298,27 +213,11 @@ __device__ void alpha_reduce_and_substeps(const Geom& g, const DevPtrs& p, const
   __syncthreads();
   if (!last || threadIdx.x != 0) return;
   __threadfence();
-  double asum = 0.0;
-  *p.mlast = *p.msub;
   for (int i = 0; i < 3; ++i) {
-    const double ai = __longlong_as_double((long long)atomicExch(&p.alpha_bits[i], 0ull));
-    p.alpha_prev[i] = p.alpha[i];
-    p.alpha[i] = ai;
-    if (i < D) asum = __dadd_rn(asum, ai);
+    p.aslot[i] = atomicExch(&p.alpha_bits[i], 0ull);
+    p.aslot[3 + i] = 0ull;
+    p.aslot[6 + i] = 0ull;
   }
-  int m;
-  if (g.forced_sub > 0) {
-    m = g.forced_sub;
-  } else {
-    const double dtE = __ddiv_rn(__dmul_rn(0.5, g.dx), asum);
-    const double r = ceil(__ddiv_rn(g.dt, dtE));
-    m = (r < 1.0) ? 1 : (r > 1e9 ? 1000000000 : (int)r);
-  }
-  if (m > g.m_cap) {
-    set_status(p.status, DVM_ERR_CFL);
-    m = g.m_cap;
-  }
-  *p.msub = m;
   *p.counter = 0u;
 }
 
@@ -329,87 +228,19 @@ __global__ void __launch_bounds__(kBlock) k_alpha(Geom g, DevPtrs p) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   double a[3] = {0.0, 0.0, 0.0};
   if (c < g.nc) {
-    double Uc[kMaxM];
-#pragma unroll
-    for (int i = 0; i < D + 2; ++i) Uc[i] = p.U[i * g.nc + c];
-    alpha_of<D>(Uc, a);
+    TW W[kMaxM];
     const double w = 1.0 - p.lam[c];
 #pragma unroll
-    for (int i = 0; i < D + 2; ++i) ((TW*)p.W0)[i * g.nc + c] = (TW)(w * Uc[i]);
+    for (int i = 0; i < D + 2; ++i) {
+      W[i] = (TW)(w * p.U[i * g.nc + c]);
+      ((TW*)p.W0)[i * g.nc + c] = W[i];
+    }
+    state_alpha_of<D>(W, a);
   }
-  alpha_reduce_and_substeps<D>(g, p, a);
+  alpha_reduce_publish<D>(g, p, a);
 }
 
 // ---------------------------------------------------------------- MUSCL
-
-// Euler flux along dir (Eq. sys1), gamma = 1 + 2/d; zero density carries no
-// flux (only reached for lambda = 1, where W = 0).
-// Division in the Euler solver: IEEE in the FP64 build, the fast
-// approximate quotient (two ulp) in the FP32-storage builds.
-__device__ inline double e_div(double a, double b) { return a / b; }
-__device__ inline float e_div(float a, float b) { return __fdividef(a, b); }
-
-template <typename TF, int D>
-__device__ inline void euler_flux(const TF* U, int dir, TF* F) {
-  const TF rho = U[0];
-  TF u[3] = {TF(0), TF(0), TF(0)}, ke = TF(0);
-  if (rho != TF(0)) {
-    const TF ir = e_div(TF(1), rho);
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-      u[j] = U[1 + j] * ir;
-      ke += TF(0.5) * U[1 + j] * u[j];
-    }
-  }
-  const TF pr = (TF(2) / TF(D)) * (U[D + 1] - ke);
-  F[0] = U[1 + dir];
-#pragma unroll
-  for (int j = 0; j < D; ++j) F[1 + j] = U[1 + j] * u[dir] + (j == dir ? pr : TF(0));
-  F[D + 1] = (U[D + 1] + pr) * u[dir];
-}
-
-// van Leer limited slope b phi(a / b), phi(chi) = (|chi| + chi) / (1 + chi),
-// in product form (zero unless a b > 0).
-template <typename TF, bool LIMITED>
-__device__ inline TF slope(TF a, TF b) {
-  if (!LIMITED) return b;
-  const TF ab = a * b;
-  return ab > TF(0) ? e_div(ab + ab, a + b) : TF(0);
-}
-
-// Grid-wide barrier of the cooperative Euler launch: arrive on a counter, the
-// last block to arrive advances the generation word.  The wait is bounded
-// (2^31 SM clock cycles, about a second); on timeout the status word gets
-// DVM_ERR_TIMEOUT and false is returned so that the kernel can leave.
-__device__ bool grid_sync(unsigned* bar, int* status) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 1;
-    const unsigned gen = *vgen;
-    __threadfence();
-    int good = 1;
-    if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*vgen == gen) {
-        if (clock64() - t0 > (1LL << 31)) {
-          set_status(status, DVM_ERR_TIMEOUT);
-          good = 0;
-          break;
-        }
-        __nanosleep(100);
-      }
-    }
-    __threadfence();
-    ok = good;
-  }
-  __syncthreads();
-  return ok != 0;
-}
 
 // Tiles of the Euler sub-step: TX x TY cells of one z plane, one thread per
 // cell, staged with a two-cell halo in every active direction; the face
@@ -504,10 +335,9 @@ __global__ void __launch_bounds__(ETile<D, TF>::THREADS) k_euler(Geom g, DevPtrs
   using T = ETile<D, TF>;
   constexpr int NM = D + 2;
   extern __shared__ unsigned char s_raw[];
+  __shared__ double s_amax[3][T::THREADS / 32];
   TF* sw = reinterpret_cast<TF*>(s_raw);  // [NM][SZ][SY][SX]
   TF* sf = sw + NM * T::NS;               // [D][NM][FZ][FY][FX]
-  const int m = *p.msub;
-  const TF k = (TF)((g.dt / m) / g.dx);
   const int Nx = g.nx[0], Ny = g.nx[1], Nz = g.nx[2];
   const long long nc = g.nc;
   const int ntx = (Nx + T::TX - 1) / T::TX, nty = (Ny + T::TY - 1) / T::TY;
@@ -517,16 +347,48 @@ __global__ void __launch_bounds__(ETile<D, TF>::THREADS) k_euler(Geom g, DevPtrs
   const int tx = cid % T::TX, ty = cid / T::TX;
   const int cz = D == 3 ? 2 : 0, cy = D >= 2 ? ty + 2 : 0, cx = tx + 2;
   const int ctr = cx + T::SX * (cy + T::SY * cz);  // staged index of this thread's cell
-  TF al[3];
+  double t = 0.0, a0[3] = {0.0, 0.0, 0.0};
+  int s = 0;
+  for (;; ++s) {
+    // alpha of this sub-step's initial state: slot s % 3, complete since the
+    // barrier that ended the previous sub-step; slot (s + 2) % 3 was last read
+    // before that barrier and is cleared for sub-step s + 2
+    double ad[3], asum = 0.0;
 #pragma unroll
-  for (int d = 0; d < 3; ++d) al[d] = (TF)p.alpha[d];
-  for (int s = 0; s < m; ++s) {
+    for (int d = 0; d < 3; ++d) ad[d] = __longlong_as_double((long long)__ldcg(p.aslot + (s % 3) * 3 + d));
+#pragma unroll
+    for (int d = 0; d < D; ++d) asum = __dadd_rn(asum, ad[d]);
+    if (s == 0) a0[0] = ad[0], a0[1] = ad[1], a0[2] = ad[2];
+    if (blockIdx.x == 0 && tid == 0)
+      for (int d = 0; d < 3; ++d) p.aslot[((s + 2) % 3) * 3 + d] = 0ull;
+    // length of this sub-step: Eq. Time2 with its own alpha, the last one
+    // ending exactly at the kinetic dt (same arithmetic in every block)
+    double dtE;
+    bool last;
+    if (g.forced_sub > 0) {
+      dtE = g.dt / g.forced_sub;
+      last = s + 1 == g.forced_sub;
+    } else {
+      if (!(asum > 0.0)) {
+        if (blockIdx.x == 0 && tid == 0) set_status(p.status, DVM_ERR_NONPHYSICAL);
+        return;
+      }
+      const double cfl = __ddiv_rn(__dmul_rn(0.5, g.dx), asum);
+      const double rem = __dsub_rn(g.dt, t);
+      last = cfl >= rem;
+      dtE = last ? rem : cfl;
+    }
+    const TF k = (TF)(dtE / g.dx);
+    TF al[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) al[d] = (TF)ad[d];
     const TF* src = (const TF*)((s & 1) ? p.W1 : p.W0);
     TF* dst = (TF*)((s & 1) ? p.W0 : p.W1);
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-      const int x0 = (t % ntx) * T::TX;
-      const int y0 = ((t / ntx) % nty) * T::TY;
-      const int z = t / (ntx * nty);
+    double amax[3] = {0.0, 0.0, 0.0};
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const int x0 = (tile % ntx) * T::TX;
+      const int y0 = ((tile / ntx) % nty) * T::TY;
+      const int z = tile / (ntx * nty);
       for (int i = tid; i < T::NS; i += T::THREADS) {
         const int lx = i % T::SX, ly = (i / T::SX) % T::SY, lz = i / (T::SX * T::SY);
         const int gx = bc_index(x0 - 2 + lx, Nx, g.bc[0]);
@@ -537,10 +399,6 @@ __global__ void __launch_bounds__(ETile<D, TF>::THREADS) k_euler(Geom g, DevPtrs
         for (int c = 0; c < NM; ++c) sw[c * T::NS + i] = __ldcg(src + c * nc + cc);
       }
       __syncthreads();
-      // face fluxes: slot (fx, fy, fz) of direction dir holds the face on the
-      // low side of local cell (fx, fy, fz) along dir; slot index + 1 along
-      // dir is the high side.  Thread (cell, dir) computes its cell's high
-      // face along dir, and the first cell along dir also its low face.
       if (mydir == 0) tile_faces<TF, LIMITED, D, 0>(sw, sf, ctr, tx, ty, al[0]);
       else if (D >= 2 && mydir == 1) tile_faces<TF, LIMITED, D, (D >= 2 ? 1 : 0)>(sw, sf, ctr, tx, ty, al[D >= 2 ? 1 : 0]);
       else if (D == 3) tile_faces<TF, LIMITED, D, (D == 3 ? 2 : 0)>(sw, sf, ctr, tx, ty, al[D == 3 ? 2 : 0]);
@@ -549,6 +407,7 @@ __global__ void __launch_bounds__(ETile<D, TF>::THREADS) k_euler(Geom g, DevPtrs
       if (mydir == 0 && gx < Nx && gy < Ny) {
         const int fbase = tx + T::FX * ty;
         const long long cell = gx + (long long)Nx * (gy + (long long)Ny * z);
+        TF Wn[NM];
 #pragma unroll
         for (int c = 0; c < NM; ++c) {
           TF acc = TF(0);
@@ -558,12 +417,42 @@ __global__ void __launch_bounds__(ETile<D, TF>::THREADS) k_euler(Geom g, DevPtrs
             const TF* sfd = sf + (dir * NM + c) * T::NF;
             acc += sfd[fbase + fst] - sfd[fbase];
           }
-          dst[c * nc + cell] = sw[c * T::NS + ctr] - k * acc;
+          Wn[c] = sw[c * T::NS + ctr] - k * acc;
+          dst[c * nc + cell] = Wn[c];
+        }
+        if (!last) {
+          double an[3];
+          state_alpha_of<D>(Wn, an);
+#pragma unroll
+          for (int d = 0; d < 3; ++d) amax[d] = fmax(amax[d], an[d]);
         }
       }
       __syncthreads();
     }
-    if (s + 1 < m && !grid_sync(p.gbar, p.status)) return;
+    t = __dadd_rn(t, dtE);
+    if (last) break;
+    // merge this block's alpha of the new state into slot (s + 1) % 3
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double v = amax[d];
+      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if ((tid & 31) == 0) s_amax[d][tid >> 5] = v;
+    }
+    __syncthreads();
+    if (tid < 3) {
+      double v = 0.0;
+      for (int w = 0; w < T::THREADS / 32; ++w) v = fmax(v, s_amax[tid][w]);
+      atomicMax(p.aslot + ((s + 1) % 3) * 3 + tid, (unsigned long long)__double_as_longlong(v));
+    }
+    if (s + 1 >= g.m_cap) {
+      if (blockIdx.x == 0 && tid == 0) set_status(p.status, DVM_ERR_CFL);
+      break;
+    }
+    if (!grid_sync(p.gbar, p.status)) return;
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    *p.msub = s + 1;
+    for (int d = 0; d < 3; ++d) p.alpha[d] = a0[d];
   }
 }
 
@@ -639,14 +528,18 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Geom g, DevPtrs p) {
       const double lam = p.lam[c];
       write_params<TC, D>(g, (TC*)p.prm, c, lam, 1.0 - lam, rho, u, theta, HO ? nu : nullptr, mu);
       if (HO) {
-        alpha_of<D>(Un, a);
+        TW W[kMaxM];
         const double w = 1.0 - lam;
 #pragma unroll
-        for (int i = 0; i < NM; ++i) ((TW*)p.W0)[i * nc + c] = (TW)(w * Un[i]);
+        for (int i = 0; i < NM; ++i) {
+          W[i] = (TW)(w * Un[i]);
+          ((TW*)p.W0)[i * nc + c] = W[i];
+        }
+        state_alpha_of<D>(W, a);
       }
     }
   }
-  if (HO) alpha_reduce_and_substeps<D>(g, p, a);
+  if (HO) alpha_reduce_publish<D>(g, p, a);
 }
 
 // f at the cell centres: stored piece value plus the deferred term.

@@ -100,6 +100,7 @@ struct DevPtrs {
   long long* step;    // step index n
   unsigned int* counter;  // finished-block counter of the alpha reduction
   unsigned int* gbar;     // grid barrier of the Euler launch: count, generation
+  unsigned long long* aslot;  // 3 x 3: alpha (bit patterns) of Euler sub-steps s, s+1, s+2
 };
 
 // ---------------------------------------------------------------- helpers

@@ -1,0 +1,196 @@
+// dvm_math.cuh -- device math shared by the libdvm translation units:
+// primitive variables, separable Gaussian sums of the discrete Maxwellian,
+// the Euler flux and the van Leer slope of the MUSCL scheme.
+#pragma once
+
+#include <math.h>
+
+#include "dvm_internal.cuh"
+
+namespace dvm {
+namespace {
+
+// Primitive variables (Eqs. Mo and E): rho, u, theta.  Written without
+// contractions so that the value matches a plain IEEE evaluation bit for bit
+// (alpha and the number of Euler sub-steps depend on it).
+template <int D>
+__device__ inline void primitives(const double* U, double& rho, double u[3], double& theta) {
+  rho = U[0];
+  double u2 = 0.0;
+  u[0] = u[1] = u[2] = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    u[i] = __ddiv_rn(U[1 + i], rho);
+    u2 = __dadd_rn(u2, __dmul_rn(u[i], u[i]));
+  }
+  theta = __ddiv_rn(__dsub_rn(__ddiv_rn(__dmul_rn(2.0, U[D + 1]), rho), u2), (double)D);
+}
+
+// Sums over one velocity axis of g(k) = exp(-(v_k - u)^2 / (2 theta)) times
+// 1, v_k, v_k^2, in FP64.  The Gaussian is evaluated from its peak outwards
+// with the recurrence g(k+1) = g(k) r_k, r_{k+1} = r_k q, q = exp(-dv^2/theta)
+// (ratios of consecutive Gaussian samples on a uniform grid): three
+// exponentials per axis instead of one per velocity.
+__device__ void gauss_axis_sums(int n, int kmin, double dv, double u, double theta, double& G0,
+                                double& G1, double& G2) {
+  const double h = 0.5 / theta;
+  int k0 = (int)floor(u / dv + 0.5) - kmin;
+  k0 = k0 < 0 ? 0 : (k0 >= n ? n - 1 : k0);
+  const double v0 = (kmin + k0) * dv;
+  const double g0 = exp(-(v0 - u) * (v0 - u) * h);
+  const double q = exp(-2.0 * dv * dv * h);
+  G0 = g0;
+  G1 = v0 * g0;
+  G2 = v0 * v0 * g0;
+  double g = g0, r = exp(-(2.0 * (v0 - u) * dv + dv * dv) * h);
+  for (int k = k0 + 1; k < n; ++k) {
+    g *= r;
+    r *= q;
+    const double v = (kmin + k) * dv;
+    G0 += g;
+    G1 += v * g;
+    G2 += v * v * g;
+  }
+  g = g0;
+  double s = exp((2.0 * (v0 - u) * dv - dv * dv) * h);
+  for (int k = k0 - 1; k >= 0; --k) {
+    g *= s;
+    s *= q;
+    const double v = (kmin + k) * dv;
+    G0 += g;
+    G1 += v * g;
+    G2 += v * v * g;
+  }
+}
+
+// Same sums with FP32 samples exp2(-(v - u)^2 log2(e) / (2 theta)) and FP32
+// accumulation, for the FP32-storage builds.
+__device__ void gauss_axis_sums_f32(int n, int kmin, float dv, float u, float theta, double& G0,
+                                    double& G1, double& G2) {
+  const float h2 = 0.72134752044448170f / theta;  // log2(e) / 2
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  for (int k = 0; k < n; ++k) {
+    const float v = (kmin + k) * dv;
+    const float dd = v - u;
+    const float gk = exp2f(-h2 * dd * dd);
+    s0 += gk;
+    s1 = fmaf(v, gk, s1);
+    s2 = fmaf(v * v, gk, s2);
+  }
+  G0 = s0;
+  G1 = s1;
+  G2 = s2;
+}
+
+// Euler flux along dir (Eq. sys1), gamma = 1 + 2/d; zero density carries no
+// flux (only reached for lambda = 1, where W = 0).
+// Division in the Euler solver: IEEE in the FP64 build, the fast
+// approximate quotient (two ulp) in the FP32-storage builds.
+__device__ inline double e_div(double a, double b) { return a / b; }
+__device__ inline float e_div(float a, float b) { return __fdividef(a, b); }
+
+template <typename TF, int D>
+__device__ inline void euler_flux(const TF* U, int dir, TF* F) {
+  const TF rho = U[0];
+  TF u[3] = {TF(0), TF(0), TF(0)}, ke = TF(0);
+  if (rho != TF(0)) {
+    const TF ir = e_div(TF(1), rho);
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      u[j] = U[1 + j] * ir;
+      ke += TF(0.5) * U[1 + j] * u[j];
+    }
+  }
+  const TF pr = (TF(2) / TF(D)) * (U[D + 1] - ke);
+  F[0] = U[1 + dir];
+#pragma unroll
+  for (int j = 0; j < D; ++j) F[1 + j] = U[1 + j] * u[dir] + (j == dir ? pr : TF(0));
+  F[D + 1] = (U[D + 1] + pr) * u[dir];
+}
+
+// van Leer limited slope b phi(a / b), phi(chi) = (|chi| + chi) / (1 + chi),
+// in product form (zero unless a b > 0).
+template <typename TF, bool LIMITED>
+__device__ inline TF slope(TF a, TF b) {
+  if (!LIMITED) return b;
+  const TF ab = a * b;
+  return ab > TF(0) ? e_div(ab + ab, a + b) : TF(0);
+}
+
+// Grid-wide barrier of the cooperative Euler launch: arrive on a counter, the
+// last block to arrive advances the generation word.  The wait is bounded
+// (2^31 SM clock cycles, about a second); on timeout the status word gets
+// DVM_ERR_TIMEOUT and false is returned so that the kernel can leave.
+__device__ bool grid_sync(unsigned* bar, int* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    int good = 1;
+    if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == gen) {
+        if (clock64() - t0 > (1LL << 31)) {
+          set_status(status, DVM_ERR_TIMEOUT);
+          good = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// alpha_i contribution of one cell: |u_i| + sqrt(gamma theta), gamma = 1 + 2/d
+// (largest eigenvalue of the Euler system along i), evaluated without
+// contractions like the primitive variables.
+template <int D>
+__device__ inline void alpha_of(const double* Uc, double a[3]) {
+  double rho, u[3], theta;
+  primitives<D>(Uc, rho, u, theta);
+  const double gamma = __dadd_rn(1.0, __ddiv_rn(2.0, (double)D));
+  const double cs = sqrt(__dmul_rn(gamma, theta));
+  a[0] = a[1] = a[2] = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) a[i] = (rho > 0.0 && theta > 0.0) ? __dadd_rn(fabs(u[i]), cs) : 0.0;
+}
+
+// alpha contribution of one Euler state W (per direction |u_i| + sqrt(gamma
+// theta)); zero density (lambda = 1 makes W = 0) carries no wave.  FP64 states
+// are evaluated without contractions (same values as a plain IEEE
+// evaluation), FP32 states in FP32.
+template <int D>
+__device__ inline void state_alpha_of(const double* W, double a[3]) {
+  a[0] = a[1] = a[2] = 0.0;
+  if (W[0] == 0.0) return;
+  alpha_of<D>(W, a);
+}
+template <int D>
+__device__ inline void state_alpha_of(const float* W, double a[3]) {
+  a[0] = a[1] = a[2] = 0.0;
+  if (W[0] == 0.f) return;
+  const float ir = __fdividef(1.f, W[0]);
+  float u2 = 0.f, u[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    u[i] = W[1 + i] * ir;
+    u2 = fmaf(u[i], u[i], u2);
+  }
+  const float theta = (2.f * W[D + 1] * ir - u2) * (1.f / D);
+  const float cs = sqrtf(fmaxf((1.f + 2.f / D) * theta, 0.f));
+#pragma unroll
+  for (int i = 0; i < D; ++i) a[i] = (double)(fabsf(u[i]) + cs);
+}
+
+}  // namespace
+}  // namespace dvm

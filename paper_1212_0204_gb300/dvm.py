@@ -30,6 +30,10 @@ EXPORTS = [
     "dvm_sync_status", "dvm_moments", "dvm_get_f", "dvm_last_parts", "dvm_info", "dvm_offsets",
     "dvm_save", "dvm_load", "dvm_launches_per_step", "dvm_profile_begin", "dvm_profile_end",
     "dvm_equilibrium_noalloc",
+    "dvm_batch_create", "dvm_batch_destroy", "dvm_batch_last_error", "dvm_batch_sizes",
+    "dvm_batch_set_state_moments", "dvm_batch_step", "dvm_batch_step_async",
+    "dvm_batch_sync_status", "dvm_batch_moments", "dvm_batch_get_f", "dvm_batch_info",
+    "dvm_batch_set_tiling", "dvm_batch_autotune", "dvm_batch_kinetic_ms",
 ]
 
 
@@ -89,6 +93,22 @@ def lib():
         L.dvm_profile_begin.argtypes = [vp]
         L.dvm_profile_end.argtypes = [vp, dp, C.POINTER(C.c_int)]
         L.dvm_equilibrium_noalloc.argtypes = [C.POINTER(_Config), vp, vp, vp]
+        L.dvm_batch_create.argtypes = [C.POINTER(_Config), ip, vp, C.POINTER(vp)]
+        L.dvm_batch_destroy.argtypes = [vp]
+        L.dvm_batch_destroy.restype = None
+        L.dvm_batch_last_error.argtypes = [vp]
+        L.dvm_batch_last_error.restype = C.c_char_p
+        L.dvm_batch_sizes.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+        L.dvm_batch_set_state_moments.argtypes = [vp, vp, ip]
+        L.dvm_batch_step.argtypes = [vp, ip]
+        L.dvm_batch_step_async.argtypes = [vp, ip]
+        L.dvm_batch_sync_status.argtypes = [vp]
+        L.dvm_batch_moments.argtypes = [vp, vp, ip]
+        L.dvm_batch_get_f.argtypes = [vp, ip, vp]
+        L.dvm_batch_info.argtypes = [vp, C.POINTER(C.c_longlong), vp, vp]
+        L.dvm_batch_set_tiling.argtypes = [vp, ip, ip]
+        L.dvm_batch_autotune.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
+        L.dvm_batch_kinetic_ms.argtypes = [vp, ip, dp]
         _lib = L
     return _lib
 
@@ -284,3 +304,138 @@ class Solver:
         n = C.c_int()
         self._check(lib().dvm_launches_per_step(self._h, C.byref(n)))
         return n.value
+
+
+class Batch:
+    """Many independent 1D-1V cases advanced together (dvm_batch_*).  Moments are
+    packed: rows (rho, rho u, E) over all cells, case after case."""
+
+    def __init__(self, cases, precision=F32, scheme=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libdvm needs a CUDA GPU; no CPU fallback exists")
+        self._torch = torch
+        arr = (_Config * len(cases))()
+        self._keep = []
+        for i, case in enumerate(cases):
+            cfg, keep = config_from_case(case, precision, scheme)
+            arr[i] = cfg
+            self._keep += keep
+        self._cfgs = arr
+        self.ncases = len(cases)
+        self.nx = [int(c.nx[0]) for c in cases]
+        self.nv = [int(c.nv[0]) for c in cases]
+        self.offsets = np.concatenate([[0], np.cumsum(self.nx)]).astype(int)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        rc = lib().dvm_batch_create(arr, len(cases), C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if rc:
+            raise DvmError(rc, "dvm_batch_create failed")
+        self._h = h
+        cells, pts = C.c_longlong(), C.c_longlong()
+        lib().dvm_batch_sizes(h, C.byref(cells), C.byref(pts))
+        self.ncells, self.npoints = cells.value, pts.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dvm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _check(self, rc):
+        if rc:
+            raise DvmError(rc, lib().dvm_batch_last_error(self._h).decode())
+
+    def pack(self, per_case):
+        """Pack a list of (3, N_x,i) moment arrays into the batch layout."""
+        return np.ascontiguousarray(np.concatenate(per_case, axis=1))
+
+    def set_moments(self, U):
+        t = self._torch
+        if isinstance(U, t.Tensor):
+            self._check(lib().dvm_batch_set_state_moments(self._h, C.c_void_p(U.data_ptr()),
+                                                          1 if U.is_cuda else 0))
+        else:
+            a = np.ascontiguousarray(U, dtype=np.float64)
+            self._check(lib().dvm_batch_set_state_moments(self._h, a.ctypes.data_as(C.c_void_p), 0))
+
+    def step(self, n=1):
+        self._check(lib().dvm_batch_step(self._h, int(n)))
+
+    def step_async(self, n=1):
+        self._check(lib().dvm_batch_step_async(self._h, int(n)))
+
+    def sync_status(self):
+        self._check(lib().dvm_batch_sync_status(self._h))
+
+    def moments(self, out=None):
+        t = self._torch
+        if out is not None and isinstance(out, t.Tensor):
+            self._check(lib().dvm_batch_moments(self._h, C.c_void_p(out.data_ptr()),
+                                                1 if out.is_cuda else 0))
+            return out
+        a = np.zeros((3, self.ncells))
+        self._check(lib().dvm_batch_moments(self._h, a.ctypes.data_as(C.c_void_p), 0))
+        return a
+
+    def case_moments(self, U, i):
+        return U[:, self.offsets[i]:self.offsets[i + 1]]
+
+    def f(self, i):
+        a = np.zeros((self.nv[i], self.nx[i]))
+        self._check(lib().dvm_batch_get_f(self._h, int(i), a.ctypes.data_as(C.c_void_p)))
+        return a
+
+    def info(self):
+        n = C.c_longlong()
+        m = np.zeros(self.ncases, dtype=np.int32)
+        a = np.zeros(self.ncases)
+        self._check(lib().dvm_batch_info(self._h, C.byref(n), m.ctypes.data_as(C.c_void_p),
+                                         a.ctypes.data_as(C.c_void_p)))
+        return {"n": n.value, "m": m, "alpha": a}
+
+    def set_tiling(self, threads, cells_per_thread):
+        self._check(lib().dvm_batch_set_tiling(self._h, int(threads), int(cells_per_thread)))
+
+    def autotune(self):
+        t, c, ms = C.c_int(), C.c_int(), C.c_double()
+        self._check(lib().dvm_batch_autotune(self._h, C.byref(t), C.byref(c), C.byref(ms)))
+        return t.value, c.value, ms.value
+
+    def kinetic_ms(self, nsteps=3):
+        ms = C.c_double()
+        self._check(lib().dvm_batch_kinetic_ms(self._h, int(nsteps), C.byref(ms)))
+        return ms.value
+
+
+def autotune_cached(batch: "Batch", cases, precision, scheme) -> dict:
+    """Tile of the batched kinetic pass from a JSON cache keyed by the batch's
+    shapes; runs dvm_batch_autotune on a miss and records the result.  The cache
+    lives in $DVM_CACHE_DIR or ~/.cache/dvm (skipped if not writable)."""
+    import hashlib
+    import json
+    sig = hashlib.sha256(json.dumps([[int(c.nx[0]), int(c.nv[0])] for c in cases] +
+                                    [precision, scheme]).encode()).hexdigest()[:20]
+    d = os.environ.get("DVM_CACHE_DIR", os.path.join(os.path.expanduser("~"), ".cache", "dvm"))
+    path = os.path.join(d, "batch_autotune.json")
+    table = {}
+    try:
+        with open(path) as fh:
+            table = json.load(fh)
+    except (OSError, ValueError):
+        table = {}
+    if sig in table:
+        t, c = table[sig]["threads"], table[sig]["cells_per_thread"]
+        batch.set_tiling(t, c)
+        return dict(table[sig], cached=True)
+    t, c, ms = batch.autotune()
+    table[sig] = {"threads": t, "cells_per_thread": c, "kinetic_ms": ms}
+    try:
+        os.makedirs(d, exist_ok=True)
+        with open(path, "w") as fh:
+            json.dump(table, fh, indent=1)
+    except OSError:
+        pass
+    return dict(table[sig], cached=False)

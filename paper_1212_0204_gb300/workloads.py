@@ -162,7 +162,10 @@ def batched_tubes(ncases: int = 512, seed: int = SEED_BASE, steps: int = 100,
     """Independent 1D-1V Riemann tubes of uneven size.
 
     Nx ~ U{100..2000}, Nv in {32, 64, 128}, tau = 10^U(-5, 0), left/right rho and T
-    ~ U(0.1, 1), u = 0, outflow; dv = 12.8/Nv so every tube spans [-6.4, 6.4).
+    ~ U(0.1, 1), u = 0, outflow.  The velocity grid is centred on 0 with half-width
+    min(6.4, 5 sqrt(1.5 T_max)), T_max the hotter side: dv = 2 * halfwidth / Nv.  (A
+    fixed [-6.4, 6.4) grid leaves dv = 0.4 at Nv = 32, coarser than the thermal speed
+    of a T = 0.1 side, and the discrete Maxwellian of such a cell is under-resolved.)
     Case i draws from seed + i.
     """
     cases = []
@@ -172,7 +175,8 @@ def batched_tubes(ncases: int = 512, seed: int = SEED_BASE, steps: int = 100,
         nv = int(rng.choice(nv_choices))
         tau = float(10.0 ** rng.uniform(-5.0, 0.0))
         rl, rr, tl, tr = rng.uniform(0.1, 1.0, size=4)
-        c = sod_1d(nx=nx, nv=nv, tau=tau, steps=steps, dv=12.8 / nv, left=(rl, tl),
+        half = min(6.4, 5.0 * np.sqrt(1.5 * max(tl, tr)))
+        c = sod_1d(nx=nx, nv=nv, tau=tau, steps=steps, dv=2.0 * half / nv, left=(rl, tl),
                    right=(rr, tr))
         c.name = f"tube_{i}"
         cases.append(c)
