@@ -19,6 +19,9 @@ struct dvm_handle {
   DevPtrs p;
   cudaStream_t stream = nullptr;   // caller's stream
   cudaStream_t cap = nullptr;      // private stream used only for graph capture
+  cudaStream_t side = nullptr;     // high-priority stream of the Euler sub-steps
+  cudaEvent_t fork = nullptr, join = nullptr;
+  bool overlap = true;             // Euler sub-steps concurrent with the kinetic pass
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool use_graph = true;
@@ -232,11 +235,25 @@ void bind(dvm_handle* h, char* base, const Layout& L) {
 // Kernels of one time step, in order; e0/e1 (optional) bracket the kinetic pass.
 int enqueue_step(dvm_handle* h, cudaStream_t s, cudaEvent_t e0 = nullptr,
                  cudaEvent_t e1 = nullptr) {
+  // The Euler sub-steps read only W = (1 - lambda) U^n and write only their
+  // own buffers and U_E; the kinetic pass reads only F and the per-cell
+  // parameters (nu enters the stored pieces one step later), so the two are
+  // independent until the end-of-step kernel, which needs both.  With overlap
+  // the Euler kernel runs on a high-priority side stream forked from s.
   const Geom& g = h->g;
   int n = 0;
-  if (g.scheme != DVM_FKS && !g.skip_euler) {
-    const int rc = cuda_check(h, launch_euler(g, h->p, s), "Euler launch");
+  const bool euler = g.scheme != DVM_FKS && !g.skip_euler;
+  const bool fork = euler && h->overlap;
+  if (euler) {
+    cudaStream_t es = s;
+    if (fork) {
+      cudaEventRecord(h->fork, s);
+      cudaStreamWaitEvent(h->side, h->fork, 0);
+      es = h->side;
+    }
+    const int rc = cuda_check(h, launch_euler(g, h->p, es), "Euler launch");
     if (rc) return rc;
+    if (fork) cudaEventRecord(h->join, h->side);
     ++n;
   }
   if (g.ghost_mode) {
@@ -246,6 +263,7 @@ int enqueue_step(dvm_handle* h, cudaStream_t s, cudaEvent_t e0 = nullptr,
   if (e0) cudaEventRecord(e0, s);
   launch_kinetic_pass(g, h->p, s);
   if (e1) cudaEventRecord(e1, s);
+  if (fork) cudaStreamWaitEvent(s, h->join, 0);
   launch_finalize(g, h->p, s);
   n += 2;
   h->launches = n;
@@ -373,7 +391,14 @@ int dvm_create(const dvm_config* cfg, void* workspace, void* cuda_stream, dvm_ha
     h->own_ws = true;
   }
   bind(h, (char*)h->ws, L);
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  const char* ov = getenv("DVM_SERIAL_EULER");
+  h->overlap = !(ov && ov[0] == '1');
   if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming) != cudaSuccess ||
       cudaMallocHost((void**)&h->pinned_status, 64) != cudaSuccess) {
     dvm_destroy(h);
     return DVM_ERR_CUDA;
@@ -415,6 +440,9 @@ void dvm_destroy(dvm_handle* h) {
   for (cudaEvent_t e : h->ev0) cudaEventDestroy(e);
   for (cudaEvent_t e : h->ev1) cudaEventDestroy(e);
   if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->fork) cudaEventDestroy(h->fork);
+  if (h->join) cudaEventDestroy(h->join);
   if (h->pinned_status) cudaFreeHost(h->pinned_status);
   if (h->own_ws && h->ws) cudaFree(h->ws);
   delete h;

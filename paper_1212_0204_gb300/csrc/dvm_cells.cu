@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(ETile<D, TF>::THREADS) k_euler(Geom g, DevPtrs
   using T = ETile<D, TF>;
   constexpr int NM = D + 2;
   extern __shared__ unsigned char s_raw[];
-  __shared__ double s_amax[3][T::THREADS / 32];
+  __shared__ TF s_amax[3][T::THREADS / 32];
   TF* sw = reinterpret_cast<TF*>(s_raw);  // [NM][SZ][SY][SX]
   TF* sf = sw + NM * T::NS;               // [D][NM][FZ][FY][FX]
   const int Nx = g.nx[0], Ny = g.nx[1], Nz = g.nx[2];
@@ -347,44 +347,57 @@ __global__ void __launch_bounds__(ETile<D, TF>::THREADS) k_euler(Geom g, DevPtrs
   const int tx = cid % T::TX, ty = cid / T::TX;
   const int cz = D == 3 ? 2 : 0, cy = D >= 2 ? ty + 2 : 0, cx = tx + 2;
   const int ctr = cx + T::SX * (cy + T::SY * cz);  // staged index of this thread's cell
+  // per sub-step scalars, computed in FP64 by thread 0 only and broadcast
+  __shared__ double s_dtE;
+  __shared__ TF s_k, s_al[3];
+  __shared__ int s_last, s_bad;
   double t = 0.0, a0[3] = {0.0, 0.0, 0.0};
   int s = 0;
   for (;; ++s) {
-    // alpha of this sub-step's initial state: slot s % 3, complete since the
-    // barrier that ended the previous sub-step; slot (s + 2) % 3 was last read
-    // before that barrier and is cleared for sub-step s + 2
-    double ad[3], asum = 0.0;
+    if (tid == 0) {
+      // alpha of this sub-step's initial state: slot s % 3, complete since the
+      // barrier that ended the previous sub-step; slot (s + 2) % 3 was last
+      // read before that barrier and is cleared for sub-step s + 2
+      double ad[3], asum = 0.0;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) ad[d] = __longlong_as_double((long long)__ldcg(p.aslot + (s % 3) * 3 + d));
+      for (int d = 0; d < 3; ++d) ad[d] = __longlong_as_double((long long)__ldcg(p.aslot + (s % 3) * 3 + d));
 #pragma unroll
-    for (int d = 0; d < D; ++d) asum = __dadd_rn(asum, ad[d]);
-    if (s == 0) a0[0] = ad[0], a0[1] = ad[1], a0[2] = ad[2];
-    if (blockIdx.x == 0 && tid == 0)
-      for (int d = 0; d < 3; ++d) p.aslot[((s + 2) % 3) * 3 + d] = 0ull;
-    // length of this sub-step: Eq. Time2 with its own alpha, the last one
-    // ending exactly at the kinetic dt (same arithmetic in every block)
-    double dtE;
-    bool last;
-    if (g.forced_sub > 0) {
-      dtE = g.dt / g.forced_sub;
-      last = s + 1 == g.forced_sub;
-    } else {
-      if (!(asum > 0.0)) {
-        if (blockIdx.x == 0 && tid == 0) set_status(p.status, DVM_ERR_NONPHYSICAL);
-        return;
+      for (int d = 0; d < D; ++d) asum = __dadd_rn(asum, ad[d]);
+      if (s == 0) a0[0] = ad[0], a0[1] = ad[1], a0[2] = ad[2];
+      if (blockIdx.x == 0)
+        for (int d = 0; d < 3; ++d) p.aslot[((s + 2) % 3) * 3 + d] = 0ull;
+      // length of this sub-step: Eq. Time2 with its own alpha, the last one
+      // ending exactly at the kinetic dt (same arithmetic in every block)
+      double dtE = 0.0;
+      int last = 0, bad = 0;
+      if (g.forced_sub > 0) {
+        dtE = g.dt / g.forced_sub;
+        last = s + 1 == g.forced_sub;
+      } else if (!(asum > 0.0)) {
+        bad = 1;
+      } else {
+        const double cfl = __ddiv_rn(__dmul_rn(0.5, g.dx), asum);
+        const double rem = __dsub_rn(g.dt, t);
+        last = cfl >= rem;
+        dtE = last ? rem : cfl;
       }
-      const double cfl = __ddiv_rn(__dmul_rn(0.5, g.dx), asum);
-      const double rem = __dsub_rn(g.dt, t);
-      last = cfl >= rem;
-      dtE = last ? rem : cfl;
+      s_dtE = dtE;
+      s_k = (TF)(dtE / g.dx);
+      for (int d = 0; d < 3; ++d) s_al[d] = (TF)ad[d];
+      s_last = last;
+      s_bad = bad;
+      if (bad && blockIdx.x == 0) set_status(p.status, DVM_ERR_NONPHYSICAL);
     }
-    const TF k = (TF)(dtE / g.dx);
+    __syncthreads();
+    if (s_bad) return;
+    const bool last = s_last != 0;
+    const TF k = s_k;
     TF al[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) al[d] = (TF)ad[d];
+    for (int d = 0; d < 3; ++d) al[d] = s_al[d];
     const TF* src = (const TF*)((s & 1) ? p.W1 : p.W0);
     TF* dst = (TF*)((s & 1) ? p.W0 : p.W1);
-    double amax[3] = {0.0, 0.0, 0.0};
+    TF amax[3] = {TF(0), TF(0), TF(0)};
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
       const int x0 = (tile % ntx) * T::TX;
       const int y0 = ((tile / ntx) % nty) * T::TY;
@@ -421,28 +434,33 @@ __global__ void __launch_bounds__(ETile<D, TF>::THREADS) k_euler(Geom g, DevPtrs
           dst[c * nc + cell] = Wn[c];
         }
         if (!last) {
-          double an[3];
+          TF an[3];
           state_alpha_of<D>(Wn, an);
 #pragma unroll
-          for (int d = 0; d < 3; ++d) amax[d] = fmax(amax[d], an[d]);
+          for (int d = 0; d < 3; ++d) amax[d] = amax[d] > an[d] ? amax[d] : an[d];
         }
       }
       __syncthreads();
     }
-    t = __dadd_rn(t, dtE);
+    if (tid == 0) t = __dadd_rn(t, s_dtE);
     if (last) break;
-    // merge this block's alpha of the new state into slot (s + 1) % 3
+    // merge this block's alpha of the new state into slot (s + 1) % 3 (the
+    // bits of a non-negative double order like the value)
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      double v = amax[d];
-      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int d = 0; d < D; ++d) {
+      TF v = amax[d];
+      for (int o = 16; o > 0; o >>= 1) {
+        const TF w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = v > w ? v : w;
+      }
       if ((tid & 31) == 0) s_amax[d][tid >> 5] = v;
     }
     __syncthreads();
-    if (tid < 3) {
-      double v = 0.0;
-      for (int w = 0; w < T::THREADS / 32; ++w) v = fmax(v, s_amax[tid][w]);
-      atomicMax(p.aslot + ((s + 1) % 3) * 3 + tid, (unsigned long long)__double_as_longlong(v));
+    if (tid < D) {
+      TF v = TF(0);
+      for (int w = 0; w < T::THREADS / 32; ++w) v = v > s_amax[tid][w] ? v : s_amax[tid][w];
+      atomicMax(p.aslot + ((s + 1) % 3) * 3 + tid,
+                (unsigned long long)__double_as_longlong((double)v));
     }
     if (s + 1 >= g.m_cap) {
       if (blockIdx.x == 0 && tid == 0) set_status(p.status, DVM_ERR_CFL);

@@ -176,8 +176,8 @@ __device__ inline void state_alpha_of(const double* W, double a[3]) {
   alpha_of<D>(W, a);
 }
 template <int D>
-__device__ inline void state_alpha_of(const float* W, double a[3]) {
-  a[0] = a[1] = a[2] = 0.0;
+__device__ inline void state_alpha_of(const float* W, float a[3]) {
+  a[0] = a[1] = a[2] = 0.f;
   if (W[0] == 0.f) return;
   const float ir = __fdividef(1.f, W[0]);
   float u2 = 0.f, u[3] = {0.f, 0.f, 0.f};
@@ -189,7 +189,13 @@ __device__ inline void state_alpha_of(const float* W, double a[3]) {
   const float theta = (2.f * W[D + 1] * ir - u2) * (1.f / D);
   const float cs = sqrtf(fmaxf((1.f + 2.f / D) * theta, 0.f));
 #pragma unroll
-  for (int i = 0; i < D; ++i) a[i] = (double)(fabsf(u[i]) + cs);
+  for (int i = 0; i < D; ++i) a[i] = fabsf(u[i]) + cs;
+}
+template <int D>
+__device__ inline void state_alpha_of(const float* W, double a[3]) {
+  float af[3];
+  state_alpha_of<D>(W, af);
+  for (int i = 0; i < 3; ++i) a[i] = (double)af[i];
 }
 
 }  // namespace
