@@ -76,6 +76,13 @@ def lib():
         L.orc_muscl_step.argtypes = [C.POINTER(_Config), dp, C.c_double, dp,
                                      C.c_int, dp]
         L.orc_riemann_exact.argtypes = [C.c_double] * 7 + [dp, C.c_int, dp, dp, dp, dp, dp]
+        L.orc_step_flagged.argtypes = [C.c_void_p, C.POINTER(C.c_ubyte), C.c_int]
+        L.orc_set_lambda.argtypes = [C.c_void_p, dp]
+        L.orc_set_lambda.restype = None
+        L.orc_clone.restype = C.c_void_p
+        L.orc_clone.argtypes = [C.c_void_p]
+        L.orc_noneq.argtypes = [C.POINTER(_Config), dp, dp, dp]
+        L.orc_features.argtypes = [C.POINTER(_Config), dp, dp, dp]
         L.orc_mlp_forward.argtypes = [C.c_int, dp, dp, dp]
         L.orc_mlp_loss_grad.restype = C.c_double
         L.orc_mlp_loss_grad.argtypes = [C.c_int, dp, dp, dp, dp]
@@ -261,11 +268,53 @@ class Scheme:
         lib().orc_get_parts(self._h, _ptr(UE), _ptr(UM), _ptr(Us))
         return UE, UM, Us
 
+    def step_flagged(self, flags, keep_raw: bool = False):
+        """One HOFKS step with the flagged cells at equilibrium (lambda -> 0 form)."""
+        fl = np.ascontiguousarray(np.asarray(flags) != 0, dtype=np.uint8)
+        assert fl.size == self.grid.ncells
+        _check(lib().orc_step_flagged(self._h, fl.ctypes.data_as(C.POINTER(C.c_ubyte)),
+                                      int(keep_raw)), "step_flagged")
+
+    def set_lambda(self, lam):
+        """Replace the per-cell lambda (e.g. a flagged cell's lambda -> 0)."""
+        self._lam = _f64(lam)
+        assert self._lam.size == self.grid.ncells
+        lib().orc_set_lambda(self._h, _ptr(self._lam))
+
+    def clone(self) -> "Scheme":
+        other = Scheme.__new__(Scheme)
+        other.grid, other.tau = self.grid, self.tau
+        other._cfg = self.grid.cstruct()
+        other._h = lib().orc_clone(self._h)
+        if not other._h:
+            raise RuntimeError("oracle clone failed")
+        return other
+
     def info(self):
         dt, n, m = C.c_double(), C.c_longlong(), C.c_int()
         alpha = np.zeros(3)
         lib().orc_info(self._h, C.byref(dt), C.byref(n), C.byref(m), _ptr(alpha))
         return {"dt": dt.value, "n": n.value, "m": m.value, "alpha": alpha}
+
+
+def noneq(g: Grid, f, U) -> np.ndarray:
+    """log10 of the discrete-L1 distance of f from E[U], relative to ||E[U]||, per cell."""
+    f = _f64(f).reshape(g.nvel, g.ncells)
+    U = _f64(U).reshape(g.nmom, g.ncells)
+    out = np.zeros(g.ncells)
+    cfg = g.cstruct()
+    _check(lib().orc_noneq(C.byref(cfg), _ptr(f), _ptr(U), _ptr(out)), "noneq")
+    return out
+
+
+def features(g: Grid, U, tau) -> np.ndarray:
+    """The ten regime features per cell, shape (10, Nc)."""
+    U = _f64(U).reshape(g.nmom, g.ncells)
+    tau = _f64(np.broadcast_to(np.asarray(tau, dtype=np.float64), (g.ncells,)))
+    out = np.zeros((10, g.ncells))
+    cfg = g.cstruct()
+    _check(lib().orc_features(C.byref(cfg), _ptr(U), _ptr(tau), _ptr(out)), "features")
+    return out
 
 
 def mlp_forward(W, X) -> np.ndarray:

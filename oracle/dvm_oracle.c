@@ -707,3 +707,178 @@ int orc_step(orc_state* S, int nsteps) {
   }
   return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* learned regime path: flagged near-equilibrium cells                      */
+/* ------------------------------------------------------------------------ */
+
+/* One HOFKS step in which the cells with flags[c] != 0 are treated as being at
+ * equilibrium.  Theorem 1 (Section 4.3.1) shows that the HOFKS moments reduce
+ * to the MUSCL solution of the Euler system as lambda -> 0; a flagged cell
+ * takes that form:
+ *   (i)   its f^n is taken to be E[U^n_c] and its lambda to be 0;
+ *   (ii)  the HOFKS step runs with this lambda field (W = (1 - lambda) U^n
+ *         becomes U^n at flagged cells; their pieces enter the transport as
+ *         E_k[U^n_c] with weight 1);
+ *   (iii) afterwards the f^{n+1} of every flagged cell is E[U^{n+1}_c]
+ *         (keep_raw = 0), or the raw f^{n+1} of the kinetic update is kept
+ *         (keep_raw = 1: the one-step check of a flag).
+ * A flag on a cell with lambda = 1 (tau = inf) is ignored.  HOFKS only. */
+int orc_step_flagged(orc_state* S, const unsigned char* flags, int keep_raw) {
+  if (S->g.scheme == ORC_FKS) return ORC_ERR_ARG;
+  const long nc = S->nc, nv = S->nv;
+  const int nm = S->nm;
+  double* lam_eff = malloc(sizeof(double) * nc);
+  if (!lam_eff) return ORC_ERR_OOM;
+  double Uc[MAXM];
+  int rc = ORC_OK;
+  for (long c = 0; c < nc; ++c) {
+    const int fl = flags[c] != 0 && S->lam[c] != 1.0;
+    lam_eff[c] = fl ? 0.0 : S->lam[c];
+    if (!fl) continue;
+    for (int i = 0; i < nm; ++i) Uc[i] = S->U[i * nc + c];
+    rc = equilibrium_with(&S->g, S->C, S->A, Uc, S->tmpM, S->tmpF);
+    if (rc) break;
+    for (long k = 0; k < nv; ++k) S->f[k * nc + c] = S->tmpF[k];
+  }
+  double* lam = S->lam;
+  if (!rc) {
+    S->lam = lam_eff;
+    rc = step_hofks(S);
+    S->lam = lam;
+  }
+  for (long c = 0; !rc && !keep_raw && c < nc; ++c) {
+    if (!(flags[c] != 0 && lam[c] != 1.0)) continue;
+    for (int i = 0; i < nm; ++i) Uc[i] = S->U[i * nc + c];
+    rc = equilibrium_with(&S->g, S->C, S->A, Uc, S->tmpM, S->tmpF);
+    if (rc) break;
+    for (long k = 0; k < nv; ++k) S->f[k * nc + c] = S->tmpF[k];
+  }
+  free(lam_eff);
+  if (rc) return rc;
+  S->n += 1;
+  for (long c = 0; c < nc; ++c) {
+    double rho, u[3], theta;
+    for (int i = 0; i < nm; ++i) Uc[i] = S->U[i * nc + c];
+    rc = primitives(S->g.d, Uc, &rho, u, &theta);
+    if (rc) return rc;
+  }
+  return ORC_OK;
+}
+
+/* Size of the departure from equilibrium at every cell:
+ *   out[c] = log10(max(||f_c - E[U_c]||_1 / ||E[U_c]||_1, 1e-12)),
+ * discrete L1 norms over the velocities (the dv^d factor cancels).  f is
+ * nv x nc at cell positions, U is nm x nc. */
+int orc_noneq(const orc_config* g, const double* f, const double* U, double* out) {
+  int rc = check_config(g);
+  if (rc) return rc;
+  const int nm = g->d + 2;
+  const long nc = ncells(g), nv = nvel(g);
+  double* C = malloc(sizeof(double) * nm * nv);
+  double* M = malloc(sizeof(double) * nv);
+  double* E = malloc(sizeof(double) * nv);
+  double A[MAXM * MAXM];
+  if (!C || !M || !E) rc = ORC_ERR_OOM;
+  if (!rc) rc = orc_matrices(g, C, A);
+  for (long c = 0; !rc && c < nc; ++c) {
+    double Uc[MAXM];
+    for (int i = 0; i < nm; ++i) Uc[i] = U[i * nc + c];
+    rc = equilibrium_with(g, C, A, Uc, M, E);
+    if (rc) break;
+    double num = 0.0, den = 0.0;
+    for (long k = 0; k < nv; ++k) {
+      num += fabs(f[k * nc + c] - E[k]);
+      den += fabs(E[k]);
+    }
+    const double r = num / den;
+    out[c] = log10(r > 1e-12 ? r : 1e-12);
+  }
+  free(C);
+  free(M);
+  free(E);
+  return rc;
+}
+
+/* Ten regime features per cell (the inputs of the regime classifier):
+ *   0 rho, 1 u_x, 2 u_y, 3 theta, 4 log10 tau,
+ *   5 log10 K(tau sqrt(theta) |grad ln rho|),  6 log10 K(tau sqrt(theta) |grad ln theta|),
+ *   7 log10 K(tau |div u|),  8 log10 K(tau |d u_x / dy|),  9 log10 K(tau |d u_y / dx|),
+ * K(a) = max(a, 1e-12).  Derivatives are central differences over the two
+ * neighbours along each direction (the boundary rule of that direction
+ * supplies missing neighbours); u_y and the y-derivatives are 0 in 1D.
+ * tau is per cell (nc values).  out[i*nc + c]. */
+int orc_features(const orc_config* g, const double* U, const double* tau, double* out) {
+  int rc = check_config(g);
+  if (rc) return rc;
+  const int d = g->d, nm = d + 2;
+  const long nc = ncells(g);
+  double* prim = malloc(sizeof(double) * 5 * nc); /* rho, u_x, u_y, u_z, theta */
+  if (!prim) return ORC_ERR_OOM;
+  for (long c = 0; c < nc; ++c) {
+    double Uc[MAXM], rho, u[3], theta;
+    for (int i = 0; i < nm; ++i) Uc[i] = U[i * nc + c];
+    rc = primitives(d, Uc, &rho, u, &theta);
+    if (rc) {
+      free(prim);
+      return rc;
+    }
+    prim[0 * nc + c] = rho;
+    for (int i = 0; i < 3; ++i) prim[(1 + i) * nc + c] = u[i];
+    prim[4 * nc + c] = theta;
+  }
+  const double h2 = 2.0 * g->dx;
+  for (long c = 0; c < nc; ++c) {
+    /* D[q][i]: central difference of quantity q along direction i, q = ln rho,
+     * ln theta, u_x, u_y, u_z */
+    double Dq[5][3] = {{0}};
+    for (int i = 0; i < d; ++i) {
+      const long cp = neighbour(g, c, i, +1), cm = neighbour(g, c, i, -1);
+      Dq[0][i] = (log(prim[cp]) - log(prim[cm])) / h2;
+      Dq[1][i] = (log(prim[4 * nc + cp]) - log(prim[4 * nc + cm])) / h2;
+      for (int j = 0; j < 3; ++j)
+        Dq[2 + j][i] = (prim[(1 + j) * nc + cp] - prim[(1 + j) * nc + cm]) / h2;
+    }
+    const double rho = prim[c], theta = prim[4 * nc + c], t = tau[c];
+    double glr = 0.0, glt = 0.0, div = 0.0;
+    for (int i = 0; i < d; ++i) {
+      glr += Dq[0][i] * Dq[0][i];
+      glt += Dq[1][i] * Dq[1][i];
+      div += Dq[2 + i][i];
+    }
+    const double kn[5] = {t * sqrt(theta) * sqrt(glr), t * sqrt(theta) * sqrt(glt),
+                          t * fabs(div), t * fabs(Dq[2][1]), t * fabs(Dq[3][0])};
+    out[0 * nc + c] = rho;
+    out[1 * nc + c] = prim[1 * nc + c];
+    out[2 * nc + c] = prim[2 * nc + c];
+    out[3 * nc + c] = theta;
+    out[4 * nc + c] = log10(t);
+    for (int j = 0; j < 5; ++j) out[(5 + j) * nc + c] = log10(kn[j] > 1e-12 ? kn[j] : 1e-12);
+  }
+  free(prim);
+  return ORC_OK;
+}
+
+/* Deep copy of a scheme state (the one-step check runs on a copy). */
+orc_state* orc_clone(const orc_state* S) {
+  orc_state* T = orc_create(&S->g, S->lam, 0.0);
+  if (!T) return NULL;
+  /* orc_create took lambda as tau; overwrite with the exact lambdas */
+  const size_t phase = sizeof(double) * (size_t)S->nc * (size_t)S->nv;
+  const size_t mom = sizeof(double) * (size_t)S->nc * (size_t)S->nm;
+  memcpy(T->lam, S->lam, sizeof(double) * S->nc);
+  memcpy(T->f, S->f, phase);
+  memcpy(T->U, S->U, mom);
+  memcpy(T->UE, S->UE, mom);
+  memcpy(T->UM, S->UM, mom);
+  memcpy(T->Us, S->Us, mom);
+  T->n = S->n;
+  T->last_m = S->last_m;
+  for (int i = 0; i < 3; ++i) T->alpha[i] = S->alpha[i];
+  return T;
+}
+
+/* Replace the per-cell lambda = exp(-dt/tau) of a state (nc values). */
+void orc_set_lambda(orc_state* S, const double* lam) {
+  memcpy(S->lam, lam, sizeof(double) * S->nc);
+}

@@ -103,6 +103,26 @@ void orc_get_parts(const orc_state* S, double* UE, double* UM, double* Ustar);
 void orc_info(const orc_state* S, double* dt, long long* n, int* m,
               double* alpha);
 
+/* ---- learned regime path (test reference of the flagged step) ---- */
+
+/* One HOFKS step with the cells flags[c] != 0 treated as at equilibrium:
+ * their f^n is E[U^n], their lambda 0 (the lambda -> 0 form of Theorem 1);
+ * afterwards their f^{n+1} is E[U^{n+1}] unless keep_raw != 0.  Flags on
+ * cells with lambda = 1 are ignored. */
+int orc_step_flagged(orc_state* S, const unsigned char* flags, int keep_raw);
+
+/* Replace the per-cell lambda of a state (Nc values). */
+void orc_set_lambda(orc_state* S, const double* lam);
+
+/* Deep copy of a scheme state. */
+orc_state* orc_clone(const orc_state* S);
+
+/* log10(max(||f_c - E[U_c]||_1 / ||E[U_c]||_1, 1e-12)) per cell. */
+int orc_noneq(const orc_config* cfg, const double* f, const double* U, double* out);
+
+/* The ten regime features per cell, out[i*Nc + c] (see dvm_oracle.c). */
+int orc_features(const orc_config* cfg, const double* U, const double* tau, double* out);
+
 #ifdef __cplusplus
 }
 #endif
