@@ -224,6 +224,126 @@ int dvm_batch_autotune(dvm_batch* b, int* threads, int* cells_per_thread,
  * pass; *ms receives its average time. */
 int dvm_batch_kinetic_ms(dvm_batch* b, int nsteps, double* ms);
 
+/* ------------------------------------------------------------------------
+ * Learned regime path.
+ *
+ * Theorem 1 (Section 4.3.1) shows that as lambda -> 0 the HOFKS moments are
+ * the MUSCL solution of the Euler system: near equilibrium the kinetic
+ * update adds nothing.  A cell flagged as near equilibrium takes that form
+ * for one step (HOFKS only, periodic or outflow, any precision):
+ *   - its f^n is taken to be E[U^n] and its lambda to be 0: W = U^n feeds the
+ *     Euler part there, and its pieces enter the transport as E_k[U^n] with
+ *     weight 1 (no read of memory);
+ *   - the kinetic pass does not write its pieces; after the step its f is
+ *     E[U^{n+1}] by definition (dvm_get_f returns that);
+ *   - a cell that was flagged and no longer is gets E[U] written into its
+ *     pieces before its next kinetic update.
+ * Moments stay exactly conservative.  The flags come from the caller
+ * (DVM_LEARN_GIVEN) or from a 10-64-64-1 tanh network evaluated on ten local
+ * features of U^n at the start of every step (DVM_LEARN_MLP):
+ *   0 rho, 1 u_x, 2 u_y, 3 theta, 4 log10 tau,
+ *   5 log10 K(tau sqrt(theta) |grad ln rho|), 6 log10 K(tau sqrt(theta) |grad ln theta|),
+ *   7 log10 K(tau |div u|), 8 log10 K(tau |du_x/dy|), 9 log10 K(tau |du_y/dx|),
+ * K(a) = max(a, 1e-12), central differences over the two neighbours along each
+ * direction (boundary rule of the direction); u_y and y-derivatives are 0 in
+ * 1D.  The network predicts log10(||f - E[U]||_1 / ||E[U]||_1) (discrete L1
+ * over velocities); a cell is flagged when the prediction is below thr.
+ * Every check_every steps a seeded sample of cells is checked: for each
+ * sampled flagged cell the full kinetic update of the step is evaluated from
+ * its (partly equilibrium) neighbours and the true one-step non-equilibrium
+ * of the result is measured; if it is not below thr the cell and every cell
+ * within veto_radius (Chebyshev distance) stay unflagged for the rest of the
+ * run.  Flags on cells with lambda = 1 (tau = inf) are ignored.
+ * ------------------------------------------------------------------------ */
+#define DVM_NFEAT 10
+#define DVM_MLP_HIDDEN 64
+/* packed FP32 parameters, row-major: W1[64][10], b1[64], W2[64][64], b2[64],
+ * W3[64], b3 */
+#define DVM_MLP_NPARAM (64 * 10 + 64 + 64 * 64 + 64 + 64 + 1)
+
+typedef enum { DVM_LEARN_OFF = 0, DVM_LEARN_GIVEN = 1, DVM_LEARN_MLP = 2 } dvm_learn_mode;
+
+typedef struct {
+  int mode;                /* dvm_learn_mode */
+  int mlp_precision;       /* DVM_F32: FP32 on CUDA cores; DVM_BF16S: BF16
+                              operands, FP32 accumulate, on the tensor cores */
+  float thr;               /* flag when the predicted log10 non-equilibrium < thr */
+  int check_every;         /* steps between checks; 0 = no checks */
+  int check_samples;       /* cells drawn per check (1..65536) */
+  int veto_radius;         /* Chebyshev radius unflagged around a failed check */
+  unsigned long long seed; /* draws of the checked cells */
+  float feat_shift[DVM_NFEAT];  /* network input x' = (x - shift) * scale */
+  float feat_scale[DVM_NFEAT];
+} dvm_learn_config;
+
+typedef struct {
+  long long steps;         /* learned steps taken */
+  long long flagged;       /* cells flagged in the last step */
+  long long flagged_total; /* sum over steps */
+  long long materialised;  /* cells written back as E when unflagged */
+  long long checks;        /* checks run */
+  long long checked;       /* flagged cells checked */
+  long long failed;        /* checked cells whose true value was not below thr */
+  long long vetoed;        /* cells under a veto */
+  double sum_abs_err;      /* sum over checked cells of |prediction - true| (MLP mode) */
+  double max_abs_err;
+  double max_true;         /* largest true value seen by a check */
+} dvm_learn_stats;
+
+/* Switches the learned path on (or off with mode DVM_LEARN_OFF) for the
+ * following steps; allocates its buffers.  DVM_ERR_ARG for FKS, a bad mode or
+ * precision; in MLP mode the network parameters must be set before a step. */
+int dvm_learn_enable(dvm_handle* h, const dvm_learn_config* cfg);
+/* Network parameters, host FP32 DVM_MLP_NPARAM values (copied). */
+int dvm_learn_set_params(dvm_handle* h, const float* P);
+/* GIVEN mode: host, N_c bytes (nonzero = flag), used by every following step
+ * until replaced. */
+int dvm_learn_set_flags(dvm_handle* h, const unsigned char* flags);
+/* Flags used by the last step (host, N_c bytes). */
+int dvm_learn_flags(dvm_handle* h, unsigned char* out);
+/* Network predictions of the last step (host, N_c FP32; MLP mode). */
+int dvm_learn_predictions(dvm_handle* h, float* out);
+int dvm_learn_get_stats(dvm_handle* h, dvm_learn_stats* out);
+/* One learned step that also checks the n given cells (host int64 indices)
+ * as the periodic check does and writes their true one-step log10
+ * non-equilibrium to out (host FP32; flagged or not); the veto rule applies
+ * to those that were flagged. */
+int dvm_learn_step_checked(dvm_handle* h, int n, const long long* cells, float* out);
+
+/* The ten features of the current state, host FP32, sample-major
+ * (out[c * 10 + i]); tau from the handle's configuration. */
+int dvm_features(dvm_handle* h, float* out);
+/* Label of the current state: log10(max(||f - E[U]||_1 / ||E[U]||_1, 1e-12))
+ * per cell, host FP32, from the true f (stored pieces plus deferred term, or
+ * E for flagged cells). */
+int dvm_noneq(dvm_handle* h, float* out);
+
+/* ---- the network on its own: training and inference on device data ---- */
+typedef struct dvm_mlp dvm_mlp;
+typedef struct {
+  int epochs;
+  int batch;               /* samples per Adam step */
+  float lr, beta1, beta2, eps;
+  unsigned long long seed; /* per-epoch shuffles */
+} dvm_train_config;
+
+/* precision: DVM_F32 (CUDA cores) or DVM_BF16S (tensor cores, BF16 operands,
+ * FP32 accumulate, FP32 master weights). */
+int dvm_mlp_create(int precision, void* cuda_stream, dvm_mlp** out);
+void dvm_mlp_destroy(dvm_mlp* m);
+int dvm_mlp_set_params(dvm_mlp* m, const float* P);  /* host FP32, resets Adam */
+int dvm_mlp_get_params(dvm_mlp* m, float* P);        /* host FP32 */
+/* y = net(X): X device FP32 n x 10 (sample-major), y device FP32 n. */
+int dvm_mlp_forward(dvm_mlp* m, long long n, const float* X, float* y);
+/* Mean squared error over n samples and its gradient (device FP64,
+ * DVM_MLP_NPARAM values, overwritten); *loss on the host. */
+int dvm_mlp_loss_grad(dvm_mlp* m, long long n, const float* X, const float* t, double* grad,
+                      double* loss);
+/* Adam on the mean squared error over the n samples (device X, t), shuffled
+ * every epoch; *loss = mean loss of the last epoch. */
+int dvm_mlp_train(dvm_mlp* m, long long n, const float* X, const float* t,
+                  const dvm_train_config* cfg, double* loss);
+
 /* Allocation-free equilibrium.  The paper has no counterpart to this entry
  * point: it exists for callers that cannot allocate device memory (a program
  * that runs within a fixed device-memory budget set up in advance, or a host

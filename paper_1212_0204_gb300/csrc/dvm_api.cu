@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "dvm_internal.cuh"
+#include "dvm_learn.cuh"
 
 using namespace dvm;
 
@@ -38,6 +39,19 @@ struct dvm_handle {
   bool profiling = false;          // bracket each kinetic pass with events
   std::vector<cudaEvent_t> ev0, ev1;
   int nprof = 0;
+  // learned regime path
+  std::vector<double> lam_host;    // lambda per cell
+  std::vector<float> tau_host;     // tau per cell
+  dvm_learn_config lcfg{};
+  LearnDev L{};
+  void* lmem = nullptr;            // one allocation for every learned buffer
+  bool params_set = false;
+  long long learn_steps = 0;
+  long long checks_run = 0;
+  cudaGraph_t graph_chk = nullptr; // step with the periodic check
+  cudaGraphExec_t exec_chk = nullptr;
+  float* scratch = nullptr;        // read-back staging (features, labels)
+  size_t scratch_bytes = 0;
 };
 
 namespace {
@@ -233,8 +247,10 @@ void bind(dvm_handle* h, char* base, const Layout& L) {
 }
 
 // Kernels of one time step, in order; e0/e1 (optional) bracket the kinetic pass.
+// check: 0 none, 1 the periodic check of seeded cells, 2 the ncheck cells in
+// the learned buffer check_cells.
 int enqueue_step(dvm_handle* h, cudaStream_t s, cudaEvent_t e0 = nullptr,
-                 cudaEvent_t e1 = nullptr) {
+                 cudaEvent_t e1 = nullptr, int check = 0, int ncheck = 0) {
   // The Euler sub-steps read only W = (1 - lambda) U^n and write only their
   // own buffers and U_E; the kinetic pass reads only F and the per-cell
   // parameters (nu enters the stored pieces one step later), so the two are
@@ -242,8 +258,21 @@ int enqueue_step(dvm_handle* h, cudaStream_t s, cudaEvent_t e0 = nullptr,
   // the Euler kernel runs on a high-priority side stream forked from s.
   const Geom& g = h->g;
   int n = 0;
+  if (g.learn) {
+    // flags of this step, then the flag-dependent parameters, W and write-back
+    cudaMemsetAsync(h->L.mat_count, 0, sizeof(unsigned), s);
+    learn_launch_flags(g, h->p, h->L, h->lcfg.mode, h->lcfg.mlp_precision, h->lcfg.thr, s);
+    learn_launch_apply(g, h->p, h->L, s);
+    n += 2;
+    if (kinetic_is_windowed(g)) {
+      learn_launch_deep(g, h->L, s);
+      n += g.d;
+    }
+    learn_launch_materialise(g, h->p, h->L, s);
+    ++n;
+  }
   const bool euler = g.scheme != DVM_FKS && !g.skip_euler;
-  const bool fork = euler && h->overlap;
+  const bool fork = euler && h->overlap && !check;
   if (euler) {
     cudaStream_t es = s;
     if (fork) {
@@ -260,6 +289,12 @@ int enqueue_step(dvm_handle* h, cudaStream_t s, cudaEvent_t e0 = nullptr,
     launch_ghost(g, h->p, s);
     ++n;
   }
+  if (check) {
+    const int nchk = check == 2 ? ncheck : h->lcfg.check_samples;
+    learn_launch_check(g, h->p, h->L, nchk, check == 2, h->lcfg.thr, h->lcfg.veto_radius,
+                       h->lcfg.seed, h->lcfg.mode == DVM_LEARN_MLP, s);
+    ++n;
+  }
   if (e0) cudaEventRecord(e0, s);
   launch_kinetic_pass(g, h->p, s);
   if (e1) cudaEventRecord(e1, s);
@@ -273,22 +308,29 @@ int enqueue_step(dvm_handle* h, cudaStream_t s, cudaEvent_t e0 = nullptr,
 void drop_graph(dvm_handle* h) {
   if (h->exec) cudaGraphExecDestroy(h->exec);
   if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->exec_chk) cudaGraphExecDestroy(h->exec_chk);
+  if (h->graph_chk) cudaGraphDestroy(h->graph_chk);
   h->exec = nullptr;
   h->graph = nullptr;
+  h->exec_chk = nullptr;
+  h->graph_chk = nullptr;
 }
 
-int ensure_graph(dvm_handle* h) {
-  if (!h->use_graph || h->exec) return 0;
+// Captures one step (check = 0) or one step with the periodic check (1).
+int ensure_graph(dvm_handle* h, int check = 0) {
+  cudaGraphExec_t* ex = check ? &h->exec_chk : &h->exec;
+  cudaGraph_t* gr = check ? &h->graph_chk : &h->graph;
+  if (!h->use_graph || *ex) return 0;
   int rc = cuda_check(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal),
                       "begin capture");
   if (rc) return rc;
-  rc = enqueue_step(h, h->cap);
+  rc = enqueue_step(h, h->cap, nullptr, nullptr, check);
   cudaGraph_t graph = nullptr;
   const cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
   if (rc) return rc;
   if ((rc = cuda_check(h, e, "end capture"))) return rc;
-  h->graph = graph;
-  return cuda_check(h, cudaGraphInstantiate(&h->exec, graph, 0), "graph instantiate");
+  *gr = graph;
+  return cuda_check(h, cudaGraphInstantiate(ex, graph, 0), "graph instantiate");
 }
 
 int sync_status(dvm_handle* h) {
@@ -327,6 +369,13 @@ int init_from_moments(dvm_handle* h) {
   if ((rc = cuda_check(h, cudaMemsetAsync(h->p.alpha_prev, 0, 3 * sizeof(double), s), "memset"))) return rc;
   if ((rc = cuda_check(h, cudaMemsetAsync(h->p.gbar, 0, 2 * sizeof(unsigned), s), "memset"))) return rc;
   if ((rc = cuda_check(h, cudaMemsetAsync(h->p.aslot, 0, 9 * sizeof(unsigned long long), s), "memset"))) return rc;
+  if (h->lmem) {
+    // a new state: no cell is flagged (f = E[U] everywhere anyway)
+    const size_t nc = (size_t)g.nc;
+    if ((rc = cuda_check(h, cudaMemsetAsync(h->L.flag, 0, nc, s), "memset"))) return rc;
+    if ((rc = cuda_check(h, cudaMemsetAsync(h->L.flag_prev, 0, nc, s), "memset"))) return rc;
+    if ((rc = cuda_check(h, cudaMemsetAsync(h->L.veto, 0, nc, s), "memset"))) return rc;
+  }
   launch_cell_params(g, h->p, 0, 1, s);
   launch_init_f(g, h->p, s);
   launch_cell_params(g, h->p, 1, 1, s);
@@ -414,6 +463,10 @@ int dvm_create(const dvm_config* cfg, void* workspace, void* cuda_stream, dvm_ha
     lam[c] = exp(-h->g.dt / tau);
     all_free &= lam[c] == 1.0;
   }
+  h->lam_host = lam;
+  h->tau_host.resize((size_t)h->g.nc);
+  for (long long c = 0; c < h->g.nc; ++c)
+    h->tau_host[c] = (float)(cfg->tau_field ? cfg->tau_field[c] : cfg->tau);
   h->all_free = all_free;
   h->g.skip_euler = all_free ? 1 : 0;
   h->g.euler_blocks = euler_blocks(h->g);
@@ -445,6 +498,8 @@ void dvm_destroy(dvm_handle* h) {
   if (h->join) cudaEventDestroy(h->join);
   if (h->pinned_status) cudaFreeHost(h->pinned_status);
   if (h->own_ws && h->ws) cudaFree(h->ws);
+  if (h->lmem) cudaFree(h->lmem);
+  if (h->scratch) cudaFree(h->scratch);
   delete h;
 }
 
@@ -509,11 +564,22 @@ int dvm_step_async(dvm_handle* h, int nsteps) {
     }
     return 0;
   }
-  if ((rc = ensure_graph(h))) return rc;
+  if (h->g.learn && h->lcfg.mode == DVM_LEARN_MLP && !h->params_set)
+    return fail(h, DVM_ERR_STATE, "network parameters not set");
   for (int i = 0; i < nsteps; ++i) {
-    if (h->exec) {
-      if ((rc = cuda_check(h, cudaGraphLaunch(h->exec, h->stream), "graph launch"))) return rc;
-    } else if ((rc = enqueue_step(h, h->stream))) {
+    int check = 0;
+    if (h->g.learn) {
+      ++h->learn_steps;
+      if (h->lcfg.check_every > 0 && h->learn_steps % h->lcfg.check_every == 0) {
+        check = 1;
+        ++h->checks_run;
+      }
+    }
+    if ((rc = ensure_graph(h, check))) return rc;
+    cudaGraphExec_t ex = check ? h->exec_chk : h->exec;
+    if (ex) {
+      if ((rc = cuda_check(h, cudaGraphLaunch(ex, h->stream), "graph launch"))) return rc;
+    } else if ((rc = enqueue_step(h, h->stream, nullptr, nullptr, check))) {
       return rc;
     }
   }
@@ -613,6 +679,11 @@ int dvm_save(dvm_handle* h, void* buf, size_t* bytes) {
   if (rc) return rc;
   if (!bytes) return fail(h, DVM_ERR_ARG, "null size");
   if (!h->state_set) return fail(h, DVM_ERR_STATE, "no state to save");
+  if (buf && h->g.learn) {
+    // flagged cells hold f = E[U] by definition: write it into their pieces
+    learn_launch_flush(h->g, h->p, h->L, h->stream);
+    if ((rc = cuda_check(h, cudaGetLastError(), "learned flush"))) return rc;
+  }
   const Layout L = layout(h->g);
   BlobHeader hd;
   memset(&hd, 0, sizeof hd);
@@ -697,6 +768,264 @@ int dvm_launches_per_step(dvm_handle* h, int* launches) {
   n += 2;
   *launches = n;
   return 0;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ learned path
+
+namespace {
+
+int learn_alloc(dvm_handle* h) {
+  if (h->lmem) return 0;
+  const size_t nc = (size_t)h->g.nc;
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  size_t off = 0;
+  const size_t o_flag = off; off += up(nc);
+  const size_t o_prev = off; off += up(nc);
+  const size_t o_given = off; off += up(nc);
+  const size_t o_veto = off; off += up(nc);
+  const size_t o_deep = off; off += up(nc);
+  const size_t o_tmp = off; off += up(nc);
+  const size_t o_pred = off; off += up(4 * nc);
+  const size_t o_tau = off; off += up(4 * nc);
+  const size_t o_lw = off; off += up(8 * nc);
+  const size_t o_invw = off; off += up(8 * nc);
+  const size_t o_P = off; off += up(4 * DVM_MLP_NPARAM);
+  const size_t o_Pb = off; off += up(2 * DVM_MLP_NPARAM);
+  const size_t o_norm = off; off += up(4 * 2 * DVM_NFEAT);
+  const size_t o_list = off; off += up(4 * nc);
+  const size_t o_mc = off; off += up(4);
+  const size_t o_cnt = off; off += up(8 * kCntN);
+  const size_t o_err = off; off += up(8 * 4);
+  const size_t o_cc = off; off += up(8 * (size_t)kMaxCheck);
+  const size_t o_co = off; off += up(4 * (size_t)kMaxCheck);
+  char* b = nullptr;
+  if (cudaMalloc((void**)&b, off) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, DVM_ERR_OOM, "learned-path buffers");
+  }
+  h->lmem = b;
+  LearnDev& L = h->L;
+  L.flag = (unsigned char*)(b + o_flag);
+  L.flag_prev = (unsigned char*)(b + o_prev);
+  L.given = (unsigned char*)(b + o_given);
+  L.veto = (unsigned char*)(b + o_veto);
+  L.deep = (unsigned char*)(b + o_deep);
+  L.tmp = (unsigned char*)(b + o_tmp);
+  L.pred = (float*)(b + o_pred);
+  L.tauf = (float*)(b + o_tau);
+  L.lw = (double*)(b + o_lw);
+  L.invw = (double*)(b + o_invw);
+  L.P = (float*)(b + o_P);
+  L.Pb = (__nv_bfloat16*)(b + o_Pb);
+  L.norm = (float*)(b + o_norm);
+  L.mat_list = (int*)(b + o_list);
+  L.mat_count = (unsigned*)(b + o_mc);
+  L.cnt = (unsigned long long*)(b + o_cnt);
+  L.err = (double*)(b + o_err);
+  L.check_cells = (long long*)(b + o_cc);
+  L.check_out = (float*)(b + o_co);
+  std::vector<double> lw(nc), invw(nc);
+  for (size_t c = 0; c < nc; ++c) {
+    const double w = 1.0 - h->lam_host[c];
+    lw[c] = w > 0.0 ? -log2(w) : INFINITY;
+    invw[c] = w > 0.0 ? 1.0 / w : INFINITY;
+  }
+  cudaStream_t s = h->stream;
+  int rc = 0;
+  rc |= cuda_check(h, cudaMemsetAsync(b, 0, off, s), "memset");
+  rc |= cuda_check(h, cudaMemcpyAsync(L.tauf, h->tau_host.data(), 4 * nc, cudaMemcpyHostToDevice, s), "copy");
+  rc |= cuda_check(h, cudaMemcpyAsync(L.lw, lw.data(), 8 * nc, cudaMemcpyHostToDevice, s), "copy");
+  rc |= cuda_check(h, cudaMemcpyAsync(L.invw, invw.data(), 8 * nc, cudaMemcpyHostToDevice, s), "copy");
+  rc |= cuda_check(h, cudaStreamSynchronize(s), "sync");
+  return rc ? h->status : 0;
+}
+
+int ensure_scratch(dvm_handle* h, size_t bytes) {
+  if (h->scratch_bytes >= bytes) return 0;
+  if (h->scratch) cudaFree(h->scratch);
+  h->scratch = nullptr;
+  h->scratch_bytes = 0;
+  if (cudaMalloc((void**)&h->scratch, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, DVM_ERR_OOM, "read-back staging");
+  }
+  h->scratch_bytes = bytes;
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dvm_learn_enable(dvm_handle* h, const dvm_learn_config* cfg) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!cfg) return fail(h, DVM_ERR_ARG, "null learned config");
+  if (cfg->mode == DVM_LEARN_OFF) {
+    if (h->g.learn) {
+      if (h->state_set) learn_launch_flush(h->g, h->p, h->L, h->stream);
+      if ((rc = cuda_check(h, cudaStreamSynchronize(h->stream), "learned flush"))) return rc;
+      h->g.learn = 0;
+      h->p.lflag = nullptr;
+      h->p.ldeep = nullptr;
+      h->p.linvw = nullptr;
+      drop_graph(h);
+    }
+    return 0;
+  }
+  if (cfg->mode != DVM_LEARN_GIVEN && cfg->mode != DVM_LEARN_MLP)
+    return fail(h, DVM_ERR_ARG, "unknown learned mode");
+  if (h->g.scheme == DVM_FKS) return fail(h, DVM_ERR_ARG, "the learned path needs HOFKS");
+  if (cfg->mlp_precision != DVM_F32 && cfg->mlp_precision != DVM_BF16S)
+    return fail(h, DVM_ERR_ARG, "network precision must be DVM_F32 or DVM_BF16S");
+  if (cfg->check_every < 0 || cfg->veto_radius < 0 ||
+      (cfg->check_every > 0 && (cfg->check_samples < 1 || cfg->check_samples > kMaxCheck)))
+    return fail(h, DVM_ERR_ARG, "bad check settings");
+  if ((rc = learn_alloc(h))) return rc;
+  float norm[2 * DVM_NFEAT];
+  for (int i = 0; i < DVM_NFEAT; ++i) {
+    norm[i] = cfg->feat_shift[i];
+    norm[DVM_NFEAT + i] = cfg->feat_scale[i];
+  }
+  if ((rc = cuda_check(h, cudaMemcpyAsync(h->L.norm, norm, sizeof norm, cudaMemcpyHostToDevice,
+                                          h->stream), "copy"))) return rc;
+  if ((rc = cuda_check(h, cudaStreamSynchronize(h->stream), "sync"))) return rc;
+  h->lcfg = *cfg;
+  h->g.learn = 1;
+  h->p.lflag = h->L.flag;
+  h->p.ldeep = h->L.deep;
+  h->p.linvw = h->L.invw;
+  drop_graph(h);
+  return 0;
+}
+
+int dvm_learn_set_params(dvm_handle* h, const float* P) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!P) return fail(h, DVM_ERR_ARG, "null parameters");
+  if (!h->lmem) return fail(h, DVM_ERR_STATE, "learned path not enabled");
+  std::vector<__nv_bfloat16> pb(DVM_MLP_NPARAM);
+  for (int i = 0; i < DVM_MLP_NPARAM; ++i) pb[i] = __float2bfloat16_rn(P[i]);
+  rc |= cuda_check(h, cudaMemcpyAsync(h->L.P, P, 4 * DVM_MLP_NPARAM, cudaMemcpyHostToDevice, h->stream), "copy");
+  rc |= cuda_check(h, cudaMemcpyAsync(h->L.Pb, pb.data(), 2 * DVM_MLP_NPARAM, cudaMemcpyHostToDevice, h->stream), "copy");
+  rc |= cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
+  if (rc) return h->status;
+  h->params_set = true;
+  return 0;
+}
+
+int dvm_learn_set_flags(dvm_handle* h, const unsigned char* flags) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!flags) return fail(h, DVM_ERR_ARG, "null flags");
+  if (!h->lmem) return fail(h, DVM_ERR_STATE, "learned path not enabled");
+  rc |= cuda_check(h, cudaMemcpyAsync(h->L.given, flags, (size_t)h->g.nc, cudaMemcpyHostToDevice, h->stream), "copy");
+  rc |= cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
+  return rc ? h->status : 0;
+}
+
+int dvm_learn_flags(dvm_handle* h, unsigned char* out) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!out || !h->lmem) return fail(h, DVM_ERR_ARG, "no learned flags");
+  rc |= cuda_check(h, cudaMemcpyAsync(out, h->L.flag, (size_t)h->g.nc, cudaMemcpyDeviceToHost, h->stream), "copy");
+  rc |= cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
+  return rc ? h->status : 0;
+}
+
+int dvm_learn_predictions(dvm_handle* h, float* out) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!out || !h->lmem) return fail(h, DVM_ERR_ARG, "no learned predictions");
+  rc |= cuda_check(h, cudaMemcpyAsync(out, h->L.pred, 4 * (size_t)h->g.nc, cudaMemcpyDeviceToHost, h->stream), "copy");
+  rc |= cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
+  return rc ? h->status : 0;
+}
+
+int dvm_learn_get_stats(dvm_handle* h, dvm_learn_stats* out) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!out) return fail(h, DVM_ERR_ARG, "null stats");
+  memset(out, 0, sizeof *out);
+  if (!h->lmem) return 0;
+  unsigned long long cnt[kCntN];
+  double err[4];
+  const size_t nc = (size_t)h->g.nc;
+  std::vector<unsigned char> fl(nc), ve(nc);
+  cudaStream_t s = h->stream;
+  rc |= cuda_check(h, cudaMemcpyAsync(cnt, h->L.cnt, sizeof cnt, cudaMemcpyDeviceToHost, s), "copy");
+  rc |= cuda_check(h, cudaMemcpyAsync(err, h->L.err, sizeof err, cudaMemcpyDeviceToHost, s), "copy");
+  rc |= cuda_check(h, cudaMemcpyAsync(fl.data(), h->L.flag, nc, cudaMemcpyDeviceToHost, s), "copy");
+  rc |= cuda_check(h, cudaMemcpyAsync(ve.data(), h->L.veto, nc, cudaMemcpyDeviceToHost, s), "copy");
+  rc |= cuda_check(h, cudaStreamSynchronize(s), "sync");
+  if (rc) return h->status;
+  long long nf = 0, nv = 0;
+  for (size_t c = 0; c < nc; ++c) {
+    nf += fl[c] != 0;
+    nv += ve[c] != 0;
+  }
+  out->steps = h->learn_steps;
+  out->flagged = nf;
+  out->flagged_total = (long long)cnt[kCntFlagged];
+  out->materialised = (long long)cnt[kCntMaterialised];
+  out->checks = h->checks_run;
+  out->checked = (long long)cnt[kCntChecked];
+  out->failed = (long long)cnt[kCntFailed];
+  out->vetoed = nv;
+  out->sum_abs_err = err[0];
+  out->max_abs_err = err[1];
+  out->max_true = out->checked ? err[2] - 12.0 : 0.0;
+  return 0;
+}
+
+int dvm_learn_step_checked(dvm_handle* h, int n, const long long* cells, float* out) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!h->state_set) return fail(h, DVM_ERR_STATE, "step before a state was set");
+  if (!h->g.learn) return fail(h, DVM_ERR_STATE, "learned path not enabled");
+  if (n < 1 || n > kMaxCheck || !cells || !out) return fail(h, DVM_ERR_ARG, "bad check cells");
+  if (h->lcfg.mode == DVM_LEARN_MLP && !h->params_set)
+    return fail(h, DVM_ERR_STATE, "network parameters not set");
+  for (int i = 0; i < n; ++i)
+    if (cells[i] < 0 || cells[i] >= h->g.nc) return fail(h, DVM_ERR_ARG, "check cell out of range");
+  cudaStream_t s = h->stream;
+  if ((rc = cuda_check(h, cudaMemcpyAsync(h->L.check_cells, cells, 8 * (size_t)n, cudaMemcpyHostToDevice, s), "copy"))) return rc;
+  ++h->learn_steps;
+  ++h->checks_run;
+  if ((rc = enqueue_step(h, s, nullptr, nullptr, 2, n))) return rc;
+  if ((rc = cuda_check(h, cudaMemcpyAsync(out, h->L.check_out, 4 * (size_t)n, cudaMemcpyDeviceToHost, s), "copy"))) return rc;
+  return sync_status(h);
+}
+
+int dvm_features(dvm_handle* h, float* out) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!out) return fail(h, DVM_ERR_ARG, "null output");
+  if (!h->state_set) return fail(h, DVM_ERR_STATE, "no state");
+  if ((rc = learn_alloc(h))) return rc;
+  const size_t bytes = 4 * (size_t)DVM_NFEAT * (size_t)h->g.nc;
+  if ((rc = ensure_scratch(h, bytes))) return rc;
+  learn_launch_features(h->g, h->p, h->L, h->scratch, h->stream);
+  if ((rc = cuda_check(h, cudaGetLastError(), "features launch"))) return rc;
+  rc |= cuda_check(h, cudaMemcpyAsync(out, h->scratch, bytes, cudaMemcpyDeviceToHost, h->stream), "copy");
+  rc |= cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
+  return rc ? h->status : 0;
+}
+
+int dvm_noneq(dvm_handle* h, float* out) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!out) return fail(h, DVM_ERR_ARG, "null output");
+  if (!h->state_set) return fail(h, DVM_ERR_STATE, "no state");
+  const size_t bytes = 4 * (size_t)h->g.nc;
+  if ((rc = ensure_scratch(h, bytes))) return rc;
+  learn_launch_noneq(h->g, h->p, h->scratch, h->stream);
+  if ((rc = cuda_check(h, cudaGetLastError(), "label launch"))) return rc;
+  rc |= cuda_check(h, cudaMemcpyAsync(out, h->scratch, bytes, cudaMemcpyDeviceToHost, h->stream), "copy");
+  rc |= cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
+  return rc ? h->status : 0;
 }
 
 }  // extern "C"

@@ -23,65 +23,6 @@ constexpr int kBlock = 256;
 
 inline unsigned blocks_for(long long n, int b = kBlock) { return (unsigned)((n + b - 1) / b); }
 
-template <int D>
-__device__ inline void cell_coords(const Geom& g, long long c, int x[3]) {
-  x[0] = (int)(c % g.nx[0]);
-  x[1] = D > 1 ? (int)((c / g.nx[0]) % g.nx[1]) : 0;
-  x[2] = D > 2 ? (int)(c / ((long long)g.nx[0] * g.nx[1])) : 0;
-}
-
-__device__ inline long long cell_index(const Geom& g, const int x[3]) {
-  return x[0] + (long long)g.nx[0] * (x[1] + (long long)g.nx[1] * x[2]);
-}
-
-// mu = (C C^T)^{-1} (U - C M[U]) of Eq. minimMax, with C M[U] from the
-// separable factors of the Maxwellian.  Returns 0 or an error code.
-template <int D, bool F64>
-__device__ int cell_mu(const Geom& g, const double* A, const double* Uc, double mu[kMaxM],
-                       double& rho, double u[3], double& theta) {
-  constexpr int NM = D + 2;
-#pragma unroll
-  for (int i = 0; i < NM; ++i)
-    if (!isfinite(Uc[i])) return DVM_ERR_NONFINITE;
-  primitives<D>(Uc, rho, u, theta);
-  if (!(rho > 0.0) || !(theta > 0.0)) return DVM_ERR_NONPHYSICAL;
-  double G0[3], G1[3], G2[3];
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    if (F64) gauss_axis_sums(g.nv[i], g.kmin[i], g.dv, u[i], theta, G0[i], G1[i], G2[i]);
-    else gauss_axis_sums_f32(g.nv[i], g.kmin[i], (float)g.dv, (float)u[i], (float)theta, G0[i], G1[i], G2[i]);
-  }
-  const double pref = F64 ? g.w * rho * pow(2.0 * M_PI * theta, -0.5 * D)
-                          : g.w * rho * (double)powf(6.283185307179586f * (float)theta, -0.5f * D);
-  double CM[kMaxM];
-  double all = 1.0;
-#pragma unroll
-  for (int i = 0; i < D; ++i) all *= G0[i];
-  CM[0] = pref * all;
-  double e = 0.0;
-#pragma unroll
-  for (int j = 0; j < D; ++j) {
-    double other = 1.0;
-#pragma unroll
-    for (int i = 0; i < D; ++i)
-      if (i != j) other *= G0[i];
-    CM[1 + j] = pref * G1[j] * other;
-    e += G2[j] * other;
-  }
-  CM[D + 1] = 0.5 * pref * e;
-  double r[kMaxM];
-#pragma unroll
-  for (int i = 0; i < NM; ++i) r[i] = Uc[i] - CM[i];
-#pragma unroll
-  for (int i = 0; i < NM; ++i) {
-    double s = 0.0;
-#pragma unroll
-    for (int j = 0; j < NM; ++j) s += A[i * NM + j] * r[j];
-    mu[i] = s;
-  }
-  return 0;
-}
-
 // Kinetic-pass parameters of one cell (row layout in dvm_internal.cuh).
 template <typename TC, int D>
 __device__ void write_params(const Geom& g, TC* prm, long long c, double lam, double weight,
@@ -529,6 +470,10 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Geom g, DevPtrs p) {
         for (int j = 0; j < NM; ++j) s += p.A[i * NM + j] * r[j];
         nu[i] = s;
       }
+      // learned path: a flagged cell's f^{n+1} is E[U^{n+1}], no correction
+      if (g.learn && p.lflag[c])
+#pragma unroll
+        for (int i = 0; i < NM; ++i) nu[i] = 0.0;
     } else {
 #pragma unroll
       for (int i = 0; i < NM; ++i) {
@@ -582,6 +527,20 @@ __global__ void k_materialize(Geom g, DevPtrs p, double* out) {
     vv += v[i] * v[i];
   }
   const long long slot = cell_index(g, q);
+  if (g.learn && p.lflag[c]) {
+    // flagged in the last step: f = E[U] (weight-1 Maxwellian and mu)
+    double qq = 0.0, lin = (double)prm[prm_at(row_mu(D, 0), c, nc)];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const double du = v[i] - (double)prm[prm_at(row_u(i), c, nc)];
+      qq += du * du;
+      lin += (double)prm[prm_at(row_mu(D, 1 + i), c, nc)] * v[i];
+    }
+    lin += (double)prm[prm_at(row_mu(D, D + 1), c, nc)] * vv;
+    const double e = (double)prm[prm_at(row_L(), c, nc)] - (double)prm[prm_at(row_h(D), c, nc)] * qq;
+    out[k * nc + c] = (exp2(e) + lin) * p.linvw[c];
+    return;
+  }
   double f = (double)StoreT<TS>::load((const TS*)p.F + k * nc + slot);
   if (g.scheme == DVM_FKS) {
     double qq = 0.0, lin = (double)prm[prm_at(row_mu(D, 0), c, nc)];

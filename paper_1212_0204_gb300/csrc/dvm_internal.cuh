@@ -75,6 +75,7 @@ struct Geom {
   int ghost_mode;     // 0 none, 1 two boundary pieces per velocity (1D), 2 full copy
   int skip_euler;     // every lambda == 1: U_E = 0, no Euler launch
   int euler_blocks;   // grid of the cooperative Euler launch (all co-resident)
+  int learn;          // learned regime path on: flagged cells (see dvm_learn.cuh)
 };
 
 struct DevPtrs {
@@ -101,6 +102,11 @@ struct DevPtrs {
   unsigned int* counter;  // finished-block counter of the alpha reduction
   unsigned int* gbar;     // grid barrier of the Euler launch: count, generation
   unsigned long long* aslot;  // 3 x 3: alpha (bit patterns) of Euler sub-steps s, s+1, s+2
+  // learned path (null unless Geom::learn): flags of the step, cells whose
+  // every source is flagged too, 1 / (1 - lambda)
+  const unsigned char* lflag;
+  const unsigned char* ldeep;
+  const double* linvw;
 };
 
 // ---------------------------------------------------------------- helpers

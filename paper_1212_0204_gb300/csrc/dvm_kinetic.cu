@@ -57,6 +57,8 @@ __global__ void __launch_bounds__(kThreads) k_kpass_generic(Geom g, DevPtrs p) {
 
   const long long kb = blockIdx.y * g.nvel / g.nsplit;
   const long long ke = (blockIdx.y + 1) * g.nvel / g.nsplit;
+  // a flagged target's pieces are E by definition after the step: not stored
+  const bool store = !(g.learn && p.lflag[c]);
   int kx = (int)(kb % g.nv[0]);
   int ky = D > 1 ? (int)((kb / g.nv[0]) % g.nv[1]) : 0;
   int kz = D > 2 ? (int)(kb / ((long long)g.nv[0] * g.nv[1])) : 0;
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(kThreads) k_kpass_generic(Geom g, DevPtrs p) {
       for (int i = 0; i < D; ++i) racc[1 + i] += fs * v[i];
       racc[D + 1] += fs * vv;
     }
-    StoreT<TS>::store(F + k * nc + slot, fnew);
+    if (store) StoreT<TS>::store(F + k * nc + slot, fnew);
     // next velocity (x fastest); flush the short compute-type sums per row
     if (++kx == g.nv[0]) {
       kx = 0;
@@ -283,9 +285,24 @@ __global__ void __launch_bounds__(128, DVM_WIN_MINB) k_kpass_window(Geom g, DevP
   const float dv = (float)g.dv;
   const float4* __restrict__ pg = (const float4*)p.prm;
   TS* __restrict__ F = (TS*)p.F;
-  bool tact[Y];
+  bool tact[Y], sact[Y];
 #pragma unroll
-  for (int j = 0; j < Y; ++j) tact[j] = xact && (y0 + j < Ny);
+  for (int j = 0; j < Y; ++j) tact[j] = sact[j] = xact && (y0 + j < Ny);
+  // learned path: flagged targets are not stored; a CTA whose targets and
+  // all their sources are flagged has U_* = 0 and nothing to store, and only
+  // writes its zero partial sums
+  bool skip = false;
+  if (g.learn) {
+    int all_deep = 1;
+#pragma unroll
+    for (int j = 0; j < Y; ++j) {
+      if (!tact[j]) continue;
+      const long long cell = x + (long long)Nx * (y0 + j) + (long long)plane * z;
+      sact[j] = !p.lflag[cell];
+      all_deep &= p.ldeep[cell] != 0;
+    }
+    skip = __syncthreads_and(all_deep) != 0;
+  }
 
   float lam_c[Y];
   if (!HOFKS) {
@@ -305,7 +322,7 @@ __global__ void __launch_bounds__(128, DVM_WIN_MINB) k_kpass_window(Geom g, DevP
   if (sy_first < 0) sy_first += Ny;
   const long long kystep = (long long)nvx * nc;  // F offset between consecutive ky
 
-  for (int base = pb; base < pe; base += S) {
+  for (int base = skip ? pe : pb; base < pe; base += S) {
     const int pr = base + ws;
     const int kx = pr % nvx;
     const int kz = D == 3 ? pr / nvx : 0;
@@ -397,11 +414,11 @@ __global__ void __launch_bounds__(128, DVM_WIN_MINB) k_kpass_window(Geom g, DevP
           TS* Fr = Fk + r * Nx;
 #pragma unroll
           for (int j = 0; j < Y; ++j)
-            if (tact[j]) StoreT<TS>::store(Fr + j * Nx, fn[j]);
+            if (sact[j]) StoreT<TS>::store(Fr + j * Nx, fn[j]);
         } else {
 #pragma unroll
           for (int j = 0; j < Y; ++j) {
-            if (tact[j]) StoreT<TS>::store(Fk + r * Nx, fn[j]);
+            if (sact[j]) StoreT<TS>::store(Fk + r * Nx, fn[j]);
             if (++r == Ny) r = 0;
           }
         }
@@ -549,8 +566,10 @@ void kinetic_pass_prepare(const Geom& g) {
   else launch_window<__nv_bfloat16>(g, none, nullptr, true);
 }
 
+bool kinetic_is_windowed(const Geom& g) { return window_eligible(g) && !getenv_generic(); }
+
 void launch_kinetic_pass(const Geom& g, const DevPtrs& p, cudaStream_t s) {
-  if (window_eligible(g) && !getenv_generic()) {
+  if (kinetic_is_windowed(g)) {
     if (g.precision == DVM_F32) launch_window<float>(g, p, s);
     else launch_window<__nv_bfloat16>(g, p, s);
     return;

@@ -198,5 +198,64 @@ __device__ inline void state_alpha_of(const float* W, double a[3]) {
   for (int i = 0; i < 3; ++i) a[i] = (double)af[i];
 }
 
+template <int D>
+__device__ inline void cell_coords(const Geom& g, long long c, int x[3]) {
+  x[0] = (int)(c % g.nx[0]);
+  x[1] = D > 1 ? (int)((c / g.nx[0]) % g.nx[1]) : 0;
+  x[2] = D > 2 ? (int)(c / ((long long)g.nx[0] * g.nx[1])) : 0;
+}
+
+__device__ inline long long cell_index(const Geom& g, const int x[3]) {
+  return x[0] + (long long)g.nx[0] * (x[1] + (long long)g.nx[1] * x[2]);
+}
+
+// mu = (C C^T)^{-1} (U - C M[U]) of Eq. minimMax, with C M[U] from the
+// separable factors of the Maxwellian.  Returns 0 or an error code.
+template <int D, bool F64>
+__device__ int cell_mu(const Geom& g, const double* A, const double* Uc, double mu[kMaxM],
+                       double& rho, double u[3], double& theta) {
+  constexpr int NM = D + 2;
+#pragma unroll
+  for (int i = 0; i < NM; ++i)
+    if (!isfinite(Uc[i])) return DVM_ERR_NONFINITE;
+  primitives<D>(Uc, rho, u, theta);
+  if (!(rho > 0.0) || !(theta > 0.0)) return DVM_ERR_NONPHYSICAL;
+  double G0[3], G1[3], G2[3];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    if (F64) gauss_axis_sums(g.nv[i], g.kmin[i], g.dv, u[i], theta, G0[i], G1[i], G2[i]);
+    else gauss_axis_sums_f32(g.nv[i], g.kmin[i], (float)g.dv, (float)u[i], (float)theta, G0[i], G1[i], G2[i]);
+  }
+  const double pref = F64 ? g.w * rho * pow(2.0 * M_PI * theta, -0.5 * D)
+                          : g.w * rho * (double)powf(6.283185307179586f * (float)theta, -0.5f * D);
+  double CM[kMaxM];
+  double all = 1.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) all *= G0[i];
+  CM[0] = pref * all;
+  double e = 0.0;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    double other = 1.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+      if (i != j) other *= G0[i];
+    CM[1 + j] = pref * G1[j] * other;
+    e += G2[j] * other;
+  }
+  CM[D + 1] = 0.5 * pref * e;
+  double r[kMaxM];
+#pragma unroll
+  for (int i = 0; i < NM; ++i) r[i] = Uc[i] - CM[i];
+#pragma unroll
+  for (int i = 0; i < NM; ++i) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < NM; ++j) s += A[i * NM + j] * r[j];
+    mu[i] = s;
+  }
+  return 0;
+}
+
 }  // namespace
 }  // namespace dvm

@@ -34,7 +34,16 @@ EXPORTS = [
     "dvm_batch_set_state_moments", "dvm_batch_step", "dvm_batch_step_async",
     "dvm_batch_sync_status", "dvm_batch_moments", "dvm_batch_get_f", "dvm_batch_info",
     "dvm_batch_set_tiling", "dvm_batch_autotune", "dvm_batch_kinetic_ms",
+    "dvm_learn_enable", "dvm_learn_set_params", "dvm_learn_set_flags", "dvm_learn_flags",
+    "dvm_learn_predictions", "dvm_learn_get_stats", "dvm_learn_step_checked", "dvm_features",
+    "dvm_noneq",
+    "dvm_mlp_create", "dvm_mlp_destroy", "dvm_mlp_set_params", "dvm_mlp_get_params",
+    "dvm_mlp_forward", "dvm_mlp_loss_grad", "dvm_mlp_train",
 ]
+
+NFEAT, MLP_HIDDEN = 10, 64
+MLP_NPARAM = 64 * 10 + 64 + 64 * 64 + 64 + 64 + 1
+LEARN_OFF, LEARN_GIVEN, LEARN_MLP = 0, 1, 2
 
 
 class DvmError(RuntimeError):
@@ -57,6 +66,26 @@ class _Config(C.Structure):
                 ("tau_field", C.POINTER(C.c_double)), ("bc", (C.c_int * 2) * 3),
                 ("scheme", C.c_int), ("precision", C.c_int), ("euler_subcycles", C.c_int),
                 ("max_subcycles", C.c_int)]
+
+
+class _LearnConfig(C.Structure):
+    _fields_ = [("mode", C.c_int), ("mlp_precision", C.c_int), ("thr", C.c_float),
+                ("check_every", C.c_int), ("check_samples", C.c_int), ("veto_radius", C.c_int),
+                ("seed", C.c_ulonglong), ("feat_shift", C.c_float * NFEAT),
+                ("feat_scale", C.c_float * NFEAT)]
+
+
+class _LearnStats(C.Structure):
+    _fields_ = [("steps", C.c_longlong), ("flagged", C.c_longlong),
+                ("flagged_total", C.c_longlong), ("materialised", C.c_longlong),
+                ("checks", C.c_longlong), ("checked", C.c_longlong), ("failed", C.c_longlong),
+                ("vetoed", C.c_longlong), ("sum_abs_err", C.c_double),
+                ("max_abs_err", C.c_double), ("max_true", C.c_double)]
+
+
+class _TrainConfig(C.Structure):
+    _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("seed", C.c_ulonglong)]
 
 
 _lib = None
@@ -109,6 +138,23 @@ def lib():
         L.dvm_batch_set_tiling.argtypes = [vp, ip, ip]
         L.dvm_batch_autotune.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
         L.dvm_batch_kinetic_ms.argtypes = [vp, ip, dp]
+        L.dvm_learn_enable.argtypes = [vp, C.POINTER(_LearnConfig)]
+        L.dvm_learn_set_params.argtypes = [vp, vp]
+        L.dvm_learn_set_flags.argtypes = [vp, vp]
+        L.dvm_learn_flags.argtypes = [vp, vp]
+        L.dvm_learn_predictions.argtypes = [vp, vp]
+        L.dvm_learn_get_stats.argtypes = [vp, C.POINTER(_LearnStats)]
+        L.dvm_learn_step_checked.argtypes = [vp, ip, vp, vp]
+        L.dvm_features.argtypes = [vp, vp]
+        L.dvm_noneq.argtypes = [vp, vp]
+        L.dvm_mlp_create.argtypes = [ip, vp, C.POINTER(vp)]
+        L.dvm_mlp_destroy.argtypes = [vp]
+        L.dvm_mlp_destroy.restype = None
+        L.dvm_mlp_set_params.argtypes = [vp, vp]
+        L.dvm_mlp_get_params.argtypes = [vp, vp]
+        L.dvm_mlp_forward.argtypes = [vp, C.c_longlong, vp, vp]
+        L.dvm_mlp_loss_grad.argtypes = [vp, C.c_longlong, vp, vp, vp, dp]
+        L.dvm_mlp_train.argtypes = [vp, C.c_longlong, vp, vp, C.POINTER(_TrainConfig), dp]
         _lib = L
     return _lib
 
@@ -304,6 +350,141 @@ class Solver:
         n = C.c_int()
         self._check(lib().dvm_launches_per_step(self._h, C.byref(n)))
         return n.value
+
+    # --------------------------------------------------- learned regime path
+    def learn_enable(self, mode=LEARN_GIVEN, mlp_precision=F32, thr=-3.0, check_every=0,
+                     check_samples=256, veto_radius=2, seed=1212, shift=None, scale=None):
+        c = _LearnConfig()
+        c.mode, c.mlp_precision, c.thr = int(mode), int(mlp_precision), float(thr)
+        c.check_every, c.check_samples, c.veto_radius = int(check_every), int(check_samples), int(veto_radius)
+        c.seed = int(seed)
+        c.feat_shift[:] = [float(x) for x in (np.zeros(NFEAT) if shift is None else shift)]
+        c.feat_scale[:] = [float(x) for x in (np.ones(NFEAT) if scale is None else scale)]
+        self._check(lib().dvm_learn_enable(self._h, C.byref(c)))
+
+    def learn_disable(self):
+        c = _LearnConfig()
+        c.mode = LEARN_OFF
+        self._check(lib().dvm_learn_enable(self._h, C.byref(c)))
+
+    def learn_set_params(self, P):
+        a = np.ascontiguousarray(P, dtype=np.float32)
+        assert a.size == MLP_NPARAM
+        self._check(lib().dvm_learn_set_params(self._h, a.ctypes.data_as(C.c_void_p)))
+
+    def learn_set_flags(self, flags):
+        a = np.ascontiguousarray(np.asarray(flags) != 0, dtype=np.uint8)
+        assert a.size == self.nc
+        self._check(lib().dvm_learn_set_flags(self._h, a.ctypes.data_as(C.c_void_p)))
+
+    def learn_flags(self):
+        a = np.zeros(self.nc, dtype=np.uint8)
+        self._check(lib().dvm_learn_flags(self._h, a.ctypes.data_as(C.c_void_p)))
+        return a
+
+    def learn_predictions(self):
+        a = np.zeros(self.nc, dtype=np.float32)
+        self._check(lib().dvm_learn_predictions(self._h, a.ctypes.data_as(C.c_void_p)))
+        return a
+
+    def learn_stats(self) -> dict:
+        st = _LearnStats()
+        self._check(lib().dvm_learn_get_stats(self._h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in _LearnStats._fields_}
+
+    def learn_step_checked(self, cells):
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        out = np.zeros(cells.size, dtype=np.float32)
+        self._check(lib().dvm_learn_step_checked(self._h, int(cells.size),
+                                                 cells.ctypes.data_as(C.c_void_p),
+                                                 out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def features(self):
+        """The ten regime features of the current state, shape (Nc, 10)."""
+        a = np.zeros((self.nc, NFEAT), dtype=np.float32)
+        self._check(lib().dvm_features(self._h, a.ctypes.data_as(C.c_void_p)))
+        return a
+
+    def noneq(self):
+        """log10 of ||f - E[U]||_1 / ||E[U]||_1 per cell (true f)."""
+        a = np.zeros(self.nc, dtype=np.float32)
+        self._check(lib().dvm_noneq(self._h, a.ctypes.data_as(C.c_void_p)))
+        return a
+
+
+class Mlp:
+    """The regime network on device data (dvm_mlp_*): X is a CUDA FP32 tensor of
+    shape (n, 10), targets and outputs CUDA FP32 tensors of shape (n,)."""
+
+    def __init__(self, precision=F32, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libdvm needs a CUDA GPU; no CPU fallback exists")
+        self._torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        rc = lib().dvm_mlp_create(int(precision), C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if rc:
+            raise DvmError(rc, "dvm_mlp_create failed")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dvm_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _check(self, rc):
+        if rc:
+            raise DvmError(rc, "dvm_mlp call failed")
+
+    def set_params(self, P):
+        a = np.ascontiguousarray(P, dtype=np.float32)
+        assert a.size == MLP_NPARAM
+        self._check(lib().dvm_mlp_set_params(self._h, a.ctypes.data_as(C.c_void_p)))
+
+    def params(self):
+        a = np.zeros(MLP_NPARAM, dtype=np.float32)
+        self._check(lib().dvm_mlp_get_params(self._h, a.ctypes.data_as(C.c_void_p)))
+        return a
+
+    def _dev(self, X, dtype):
+        t = self._torch
+        X = t.as_tensor(X, dtype=dtype, device="cuda").contiguous()
+        return X
+
+    def forward(self, X):
+        t = self._torch
+        X = self._dev(X, t.float32)
+        y = t.empty(X.shape[0], dtype=t.float32, device="cuda")
+        self._check(lib().dvm_mlp_forward(self._h, X.shape[0], C.c_void_p(X.data_ptr()),
+                                          C.c_void_p(y.data_ptr())))
+        return y
+
+    def loss_grad(self, X, y):
+        t = self._torch
+        X, y = self._dev(X, t.float32), self._dev(y, t.float32)
+        g = t.empty(MLP_NPARAM, dtype=t.float64, device="cuda")
+        loss = C.c_double()
+        self._check(lib().dvm_mlp_loss_grad(self._h, X.shape[0], C.c_void_p(X.data_ptr()),
+                                            C.c_void_p(y.data_ptr()), C.c_void_p(g.data_ptr()),
+                                            C.byref(loss)))
+        return loss.value, g.cpu().numpy()
+
+    def train(self, X, y, epochs=10, batch=4096, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+              seed=1212):
+        t = self._torch
+        X, y = self._dev(X, t.float32), self._dev(y, t.float32)
+        c = _TrainConfig()
+        c.epochs, c.batch, c.lr, c.beta1, c.beta2, c.eps, c.seed = \
+            int(epochs), int(batch), float(lr), float(beta1), float(beta2), float(eps), int(seed)
+        loss = C.c_double()
+        self._check(lib().dvm_mlp_train(self._h, X.shape[0], C.c_void_p(X.data_ptr()),
+                                        C.c_void_p(y.data_ptr()), C.byref(c), C.byref(loss)))
+        return loss.value
 
 
 class Batch:
