@@ -272,7 +272,8 @@ int enqueue_step(dvm_handle* h, cudaStream_t s, cudaEvent_t e0 = nullptr,
     ++n;
   }
   const bool euler = g.scheme != DVM_FKS && !g.skip_euler;
-  const bool fork = euler && h->overlap && !check;
+  // profiled steps stay serial so that the events time the kinetic pass alone
+  const bool fork = euler && h->overlap && !check && !e0;
   if (euler) {
     cudaStream_t es = s;
     if (fork) {

@@ -233,6 +233,17 @@ __device__ __forceinline__ Slot load_slot(const float4* __restrict__ pg, long lo
   return s;
 }
 
+// 4-byte asynchronous global -> shared copy (zero fill when !pred: no bytes
+// are read, the address is still a valid one), commit and wait.
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem, bool pred) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int sz = pred ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 struct WinLaunch {
   int S;       // warps per CTA, each on every S-th velocity pair (kz, kx)
   int splits;  // velocity chunks across CTAs (partial-sum slices)
@@ -248,7 +259,7 @@ struct WinLaunch {
 // pairs pb + s, pb + s + 4, ...: at any time the four warps read source rows
 // shifted by one column from each other, so their parameter loads share L1
 // lines.
-template <typename TS, int D, int Y, bool HOFKS>
+template <typename TS, int D, int Y, bool HOFKS, bool ASYNC, bool LEARN>
 __global__ void __launch_bounds__(128, DVM_WIN_MINB) k_kpass_window(Geom g, DevPtrs p, WinLaunch wl) {
   constexpr int NM = D + 2;
   constexpr int NA = HOFKS ? 2 * NM : NM;
@@ -292,7 +303,7 @@ __global__ void __launch_bounds__(128, DVM_WIN_MINB) k_kpass_window(Geom g, DevP
   // all their sources are flagged has U_* = 0 and nothing to store, and only
   // writes its zero partial sums
   bool skip = false;
-  if (g.learn) {
+  if (LEARN) {
     int all_deep = 1;
 #pragma unroll
     for (int j = 0; j < Y; ++j) {
@@ -322,6 +333,42 @@ __global__ void __launch_bounds__(128, DVM_WIN_MINB) k_kpass_window(Geom g, DevP
   if (sy_first < 0) sy_first += Ny;
   const long long kystep = (long long)nvx * nc;  // F offset between consecutive ky
 
+  // FP32 storage: the F values of a block of Y velocities x Y targets go
+  // through shared memory by cp.async, one block ahead of the arithmetic
+  // (more loads in flight than registers allow; no register holds them)
+  static_assert(!ASYNC || sizeof(TS) == 4, "cp.async staging is for FP32 storage");
+  float* s_fb = reinterpret_cast<float*>(s_mid + NA * Y);  // [2][Y][Y][128]
+  int stage = 0;
+  auto issue = [&](int base_i, int kb_i, int st) {
+    const int pr_i = base_i + ws;
+    const int kx_i = pr_i % nvx;
+    const int kz_i = D == 3 ? pr_i / nvx : 0;
+    int qx_i = x - s_ox[kx_i];
+    if (qx_i < 0) qx_i += Nx;
+    int qz_i = 0;
+    if (D == 3) {
+      qz_i = z - s_oz[kz_i];
+      if (qz_i < 0) qz_i += Nz;
+    }
+    const float* Fb_i = reinterpret_cast<const float*>(F) +
+                        ((long long)kx_i + (long long)nvx * nvy * kz_i) * nc + qx_i + plane * qz_i;
+#pragma unroll
+    for (int jj = 0; jj < Y; ++jj) {
+      const int ky = kb_i - jj;
+      int r = y0 - s_oy[ky];
+      if (r < 0) r += Ny;
+      const float* Fk = Fb_i + (long long)ky * kystep;
+#pragma unroll
+      for (int j = 0; j < Y; ++j) {
+        cp_async4(s_fb + ((st * Y + jj) * Y + j) * 128 + tid, Fk + r * Nx, tact[j]);
+        if (++r == Ny) r = 0;
+      }
+    }
+  };
+  if (ASYNC && !skip && pb < pe) {
+    issue(pb, nvy - 1, 0);
+    cp_async_commit();
+  }
   for (int base = skip ? pe : pb; base < pe; base += S) {
     const int pr = base + ws;
     const int kx = pr % nvx;
@@ -357,25 +404,37 @@ __global__ void __launch_bounds__(128, DVM_WIN_MINB) k_kpass_window(Geom g, DevP
 #pragma unroll
       for (int j = 0; j < Y; ++j) in0[t][j] = in1[t][j] = in2[t][j] = 0.f;
     for (int kb = nvy - 1; kb >= 0; kb -= Y) {
-      // the F loads of Y steps first: Y*Y independent loads in flight
       float fv[Y][Y];
-      int row0[Y];
+      if constexpr (ASYNC) {
+        // this block's values landed in shared memory (prefetched one block
+        // ahead); queue the next block (or the next pair's first) meanwhile
+        if (kb - Y >= 0) issue(base, kb - Y, stage ^ 1);
+        else if (base + S < pe) issue(base + S, nvy - 1, stage ^ 1);
+        cp_async_commit();
+        cp_async_wait<1>();
 #pragma unroll
-      for (int jj = 0; jj < Y; ++jj) {
-        const int ky = kb - jj;
-        int r = y0 - s_oy[ky];
-        if (r < 0) r += Ny;
-        row0[jj] = r;
-        const TS* Fk = Fb + (long long)ky * kystep;
-        if (r + Y <= Ny) {  // no periodic wrap among the Y rows (warp-uniform)
-          const TS* Fr = Fk + r * Nx;
+        for (int jj = 0; jj < Y; ++jj)
 #pragma unroll
-          for (int j = 0; j < Y; ++j) fv[jj][j] = tact[j] ? StoreT<TS>::load(Fr + j * Nx) : 0.f;
-        } else {
+          for (int j = 0; j < Y; ++j) fv[jj][j] = s_fb[((stage * Y + jj) * Y + j) * 128 + tid];
+        stage ^= 1;
+      } else {
+        // the F loads of Y steps first: Y*Y independent loads in flight
 #pragma unroll
-          for (int j = 0; j < Y; ++j) {
-            fv[jj][j] = tact[j] ? StoreT<TS>::load(Fk + r * Nx) : 0.f;
-            if (++r == Ny) r = 0;
+        for (int jj = 0; jj < Y; ++jj) {
+          const int ky = kb - jj;
+          int r = y0 - s_oy[ky];
+          if (r < 0) r += Ny;
+          const TS* Fk = Fb + (long long)ky * kystep;
+          if (r + Y <= Ny) {  // no periodic wrap among the Y rows (warp-uniform)
+            const TS* Fr = Fk + r * Nx;
+#pragma unroll
+            for (int j = 0; j < Y; ++j) fv[jj][j] = tact[j] ? StoreT<TS>::load(Fr + j * Nx) : 0.f;
+          } else {
+#pragma unroll
+            for (int j = 0; j < Y; ++j) {
+              fv[jj][j] = tact[j] ? StoreT<TS>::load(Fk + r * Nx) : 0.f;
+              if (++r == Ny) r = 0;
+            }
           }
         }
       }
@@ -409,7 +468,8 @@ __global__ void __launch_bounds__(128, DVM_WIN_MINB) k_kpass_window(Geom g, DevP
           }
         }
         TS* Fk = Fb + ky * kystep;
-        int r = row0[jj];
+        int r = y0 - s_oy[ky];
+        if (r < 0) r += Ny;
         if (r + Y <= Ny) {
           TS* Fr = Fk + r * Nx;
 #pragma unroll
@@ -449,16 +509,19 @@ __global__ void __launch_bounds__(128, DVM_WIN_MINB) k_kpass_window(Geom g, DevP
       __syncthreads();
       for (int i = tid; i < NA * Y * 32; i += 128) {
         const int e = i / 32, l = i % 32;
-        double v = 0.0;
+        // the S warps' plane sums in FP32, then one FP64 add (GB300's FP64
+        // rate is 1/64 of FP32: one conversion and one add per element)
+        float v = 0.f;
 #pragma unroll
-        for (int w2 = 0; w2 < S; ++w2) v += (double)s_mid[e][l + 32 * w2];
-        s_acc[e][l] += v;
+        for (int w2 = 0; w2 < S; ++w2) v += s_mid[e][l + 32 * w2];
+        s_acc[e][l] += (double)v;
       }
       __syncthreads();
 #pragma unroll
       for (int a = 0; a < NA * Y; ++a) s_mid[a][tid] = 0.f;
     }
   }
+  if (ASYNC) cp_async_wait<0>();
   // this split's partial sums
   __syncthreads();
   for (int i = tid; i < NA * Y * 32; i += 128) {
@@ -500,21 +563,43 @@ WinLaunch window_shape(const Geom& g) {
   return wl;
 }
 
-constexpr size_t window_smem(int d, bool hofks) {
-  return (size_t)(hofks ? 2 : 1) * (d + 2) * kWinY * (32 * sizeof(double) + 128 * sizeof(float));
+constexpr size_t window_smem(int d, bool hofks, bool async) {
+  return (size_t)(hofks ? 2 : 1) * (d + 2) * kWinY * (32 * sizeof(double) + 128 * sizeof(float)) +
+         (async ? (size_t)2 * kWinY * kWinY * 128 * sizeof(float) : 0);
 }
 
-template <typename TS, int D, bool HO>
-void launch_window_t(const Geom& g, const DevPtrs& p, const WinLaunch& wl, cudaStream_t s, bool prepare) {
-  constexpr size_t sm = window_smem(D, HO);
+// FP32 staging of the F loads through shared memory: on by default in 2D,
+// where it measures faster; in 3D the extra shared memory costs the L1
+// capacity the parameter loads rely on (DVM_WIN_ASYNC=0/1 overrides).
+bool window_async(int d) {
+  const char* e = getenv("DVM_WIN_ASYNC");
+  if (e && (e[0] == '0' || e[0] == '1')) return e[0] == '1';
+  return d == 2;
+}
+
+template <typename TS, int D, bool HO, bool AS>
+void launch_window_a(const Geom& g, const DevPtrs& p, const WinLaunch& wl, cudaStream_t s, bool prepare) {
+  constexpr size_t sm = window_smem(D, HO, AS);
   if (prepare) {
-    cudaFuncSetAttribute(k_kpass_window<TS, D, kWinY, HO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sm);
+    cudaFuncSetAttribute(k_kpass_window<TS, D, kWinY, HO, AS, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_kpass_window<TS, D, kWinY, HO, AS, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     return;
   }
   dim3 grid((unsigned)((g.nx[0] + 31) / 32), (unsigned)((g.nx[1] + kWinY - 1) / kWinY),
             (unsigned)(g.nx[2] * wl.splits));
-  k_kpass_window<TS, D, kWinY, HO><<<grid, 128, sm, s>>>(g, p, wl);
+  if (g.learn) k_kpass_window<TS, D, kWinY, HO, AS, true><<<grid, 128, sm, s>>>(g, p, wl);
+  else k_kpass_window<TS, D, kWinY, HO, AS, false><<<grid, 128, sm, s>>>(g, p, wl);
+}
+
+template <typename TS, int D, bool HO>
+void launch_window_t(const Geom& g, const DevPtrs& p, const WinLaunch& wl, cudaStream_t s, bool prepare) {
+  if constexpr (sizeof(TS) == 4) {
+    if (prepare) launch_window_a<TS, D, HO, true>(g, p, wl, s, true);
+    else if (window_async(D)) return launch_window_a<TS, D, HO, true>(g, p, wl, s, false);
+  }
+  launch_window_a<TS, D, HO, false>(g, p, wl, s, prepare);
 }
 
 template <typename TS>
