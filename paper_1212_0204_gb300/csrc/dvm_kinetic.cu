@@ -244,6 +244,22 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// f streams through once per step: evict-first loads and stores keep the L1
+// lines of the per-cell parameters (reused by neighbouring targets) resident.
+template <typename TS> struct StreamT { };
+template <> struct StreamT<float> {
+  __device__ static float load(const float* p) { return __ldcs(p); }
+  __device__ static void store(float* p, float v) { __stcs(p, v); }
+};
+template <> struct StreamT<__nv_bfloat16> {
+  __device__ static float load(const __nv_bfloat16* p) {
+    return __bfloat162float(__ushort_as_bfloat16(__ldcs(reinterpret_cast<const unsigned short*>(p))));
+  }
+  __device__ static void store(__nv_bfloat16* p, float v) {
+    __stcs(reinterpret_cast<unsigned short*>(p), __bfloat16_as_ushort(__float2bfloat16_rn(v)));
+  }
+};
+
 struct WinLaunch {
   int S;       // warps per CTA, each on every S-th velocity pair (kz, kx)
   int splits;  // velocity chunks across CTAs (partial-sum slices)
@@ -428,11 +444,11 @@ __global__ void __launch_bounds__(128, DVM_WIN_MINB) k_kpass_window(Geom g, DevP
           if (r + Y <= Ny) {  // no periodic wrap among the Y rows (warp-uniform)
             const TS* Fr = Fk + r * Nx;
 #pragma unroll
-            for (int j = 0; j < Y; ++j) fv[jj][j] = tact[j] ? StoreT<TS>::load(Fr + j * Nx) : 0.f;
+            for (int j = 0; j < Y; ++j) fv[jj][j] = tact[j] ? StreamT<TS>::load(Fr + j * Nx) : 0.f;
           } else {
 #pragma unroll
             for (int j = 0; j < Y; ++j) {
-              fv[jj][j] = tact[j] ? StoreT<TS>::load(Fk + r * Nx) : 0.f;
+              fv[jj][j] = tact[j] ? StreamT<TS>::load(Fk + r * Nx) : 0.f;
               if (++r == Ny) r = 0;
             }
           }
@@ -474,11 +490,11 @@ __global__ void __launch_bounds__(128, DVM_WIN_MINB) k_kpass_window(Geom g, DevP
           TS* Fr = Fk + r * Nx;
 #pragma unroll
           for (int j = 0; j < Y; ++j)
-            if (sact[j]) StoreT<TS>::store(Fr + j * Nx, fn[j]);
+            if (sact[j]) StreamT<TS>::store(Fr + j * Nx, fn[j]);
         } else {
 #pragma unroll
           for (int j = 0; j < Y; ++j) {
-            if (sact[j]) StoreT<TS>::store(Fk + r * Nx, fn[j]);
+            if (sact[j]) StreamT<TS>::store(Fk + r * Nx, fn[j]);
             if (++r == Ny) r = 0;
           }
         }

@@ -20,6 +20,7 @@
 #include "dvm_learn.cuh"
 #include "dvm_math.cuh"
 #include "dvm_mlp.cuh"
+#include "dvm_tc.cuh"
 
 namespace dvm {
 namespace {
@@ -140,6 +141,50 @@ __global__ void __launch_bounds__(kFlagBlock) k_learn_flags(Geom g, DevPtrs p, L
   const unsigned b = __ballot_sync(0xffffffffu, fl);
   if ((tid & 31) == 0 && b) atomicAdd(&cnt, (unsigned)__popc(b));
   __syncthreads();
+  if (tid == 0 && cnt) atomicAdd(&L.cnt[kCntFlagged], (unsigned long long)cnt);
+}
+
+// MLP mode with the BF16 tensor-core network: 128 cells per tile, features in
+// FP32 per thread, the two hidden layers as tcgen05 MMAs (FP32 accumulate)
+template <int D>
+__global__ void __launch_bounds__(tc::kTcThreads) k_learn_flags_tc(Geom g, DevPtrs p, LearnDev L, float thr) {
+  __shared__ __align__(1024) tc::MlpSmem S;
+  __shared__ float sN[2 * kNIn];
+  __shared__ unsigned int cnt;
+  const int tid = threadIdx.x;
+  if (tid < 2 * kNIn) sN[tid] = L.norm[tid];
+  if (tid == 0) cnt = 0u;
+  tc::mlp_tc_setup(S, L.P);
+  unsigned phase = 0;
+  const long long ntiles = (g.nc + 127) / 128;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long c = tile * 128 + tid;
+    const bool real = c < g.nc;
+    float x[kNIn];
+    if (real) {
+      cell_features<D>(g, p.U, c, L.tauf[c], x);
+#pragma unroll
+      for (int i = 0; i < kNIn; ++i) x[i] = (x[i] - sN[i]) * sN[kNIn + i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < kNIn; ++i) x[i] = 0.f;
+    }
+    float pred = 0.f;
+    if (!tc::mlp_tc_tile(S, phase, x, pred)) {
+      if (tid == 0) set_status(p.status, DVM_ERR_TIMEOUT);
+      break;
+    }
+    unsigned char fl = 0;
+    if (real) {
+      fl = pred < thr && p.lam[c] != 1.0 && !L.veto[c];
+      L.pred[c] = pred;
+      L.flag_prev[c] = L.flag[c];
+      L.flag[c] = fl;
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, fl);
+    if ((tid & 31) == 0 && b) atomicAdd(&cnt, (unsigned)__popc(b));
+  }
+  tc::mlp_tc_teardown(S);
   if (tid == 0 && cnt) atomicAdd(&L.cnt[kCntFlagged], (unsigned long long)cnt);
 }
 
@@ -526,7 +571,12 @@ inline unsigned blocks_of(long long n, int b) { return (unsigned)((n + b - 1) / 
 
 void learn_launch_flags(const Geom& g, const DevPtrs& p, const LearnDev& L, int mode,
                         int mlp_precision, float thr, cudaStream_t s) {
-  (void)mlp_precision;
+  if (mode == DVM_LEARN_MLP && mlp_precision == DVM_BF16S) {
+    const long long tiles = (g.nc + 127) / 128;
+    const unsigned grid = (unsigned)(tiles < 152 * 4 ? tiles : 152 * 4);
+    DVM_LEARN_BY_DIM(g, (k_learn_flags_tc<DD><<<grid, tc::kTcThreads, 0, s>>>(g, p, L, thr)));
+    return;
+  }
   DVM_LEARN_BY_DIM(g, (k_learn_flags<DD><<<blocks_of(g.nc, kFlagBlock), kFlagBlock, 0, s>>>(g, p, L, mode, thr)));
 }
 

@@ -1,7 +1,7 @@
 // dvm_mlp.cu -- the regime network on its own: inference over device
 // samples, mean-squared-error gradient and Adam training (dvm_mlp_* in
-// dvm.h).  FP32 on the CUDA cores here; the BF16 tensor-core kernels are in
-// dvm_mlp_tc.cu.
+// dvm.h).  FP32 kernels on the CUDA cores; the BF16 forward pass runs on the
+// tensor cores (tcgen05, building blocks in dvm_tc.cuh).
 #include <math.h>
 #include <string.h>
 
@@ -10,6 +10,7 @@
 
 #include "dvm_internal.cuh"
 #include "dvm_mlp.cuh"
+#include "dvm_tc.cuh"
 
 using namespace dvm;
 
@@ -24,6 +25,7 @@ struct dvm_mlp {
   int* perm = nullptr;     // epoch order
   long long perm_cap = 0;
   long long t = 0;         // Adam steps taken
+  int* status = nullptr;   // device: tensor-core wait timed out
   bool set = false;
   std::string err;
 };
@@ -169,6 +171,30 @@ __global__ void __launch_bounds__(kGThreads) k_mlp_grad_f32(const float* __restr
   }
 }
 
+// BF16 tensor-core forward pass (tcgen05, FP32 accumulate in TMEM), one
+// 128-sample tile at a time per CTA.
+__global__ void __launch_bounds__(tc::kTcThreads) k_mlp_forward_tc(const float* __restrict__ P, long long n,
+                                                                   const float* __restrict__ X,
+                                                                   float* __restrict__ y, int* status) {
+  __shared__ __align__(1024) tc::MlpSmem S;
+  tc::mlp_tc_setup(S, P);
+  unsigned phase = 0;
+  const long long ntiles = (n + 127) / 128;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long s = tile * 128 + threadIdx.x;
+    float x[kNIn];
+#pragma unroll
+    for (int i = 0; i < kNIn; ++i) x[i] = s < n ? X[s * kNIn + i] : 0.f;
+    float out = 0.f;
+    if (!tc::mlp_tc_tile(S, phase, x, out)) {
+      if (threadIdx.x == 0) atomicCAS(status, 0, DVM_ERR_TIMEOUT);
+      break;
+    }
+    if (s < n) y[s] = out;
+  }
+  tc::mlp_tc_teardown(S);
+}
+
 __global__ void k_adam(float* __restrict__ P, float* __restrict__ m, float* __restrict__ v,
                        const double* __restrict__ grad, float lr, float b1, float b2, float eps,
                        float c1, float c2) {
@@ -225,7 +251,7 @@ int dvm_mlp_create(int precision, void* cuda_stream, dvm_mlp** out) {
   m->stream = (cudaStream_t)cuda_stream;
   char* b = nullptr;
   const size_t pb = 256 * ((sizeof(float) * kNP + 255) / 256);
-  const size_t gb = 256 * ((sizeof(double) * (kNP + 1) + 255) / 256);
+  const size_t gb = 256 * ((sizeof(double) * (kNP + 2) + 255) / 256);
   if (cudaMalloc((void**)&b, 3 * pb + gb) != cudaSuccess) {
     cudaGetLastError();
     delete m;
@@ -236,6 +262,7 @@ int dvm_mlp_create(int precision, void* cuda_stream, dvm_mlp** out) {
   m->v = (float*)(b + 2 * pb);
   m->grad = (double*)(b + 3 * pb);
   m->loss = m->grad + kNP;
+  m->status = (int*)(m->loss + 1);
   cudaFuncSetAttribute(k_mlp_grad_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(kGradSmemFloats * sizeof(float)));
   if (cudaMemsetAsync(b, 0, 3 * pb + gb, m->stream) != cudaSuccess ||
@@ -283,10 +310,23 @@ int dvm_mlp_forward(dvm_mlp* m, long long n, const float* X, float* y) {
   if (!m || n < 0 || (n > 0 && (!X || !y))) return DVM_ERR_ARG;
   if (!m->set) return mfail(m, DVM_ERR_STATE, "parameters not set");
   if (n == 0) return 0;
-  k_mlp_forward_f32<<<(unsigned)((n + kFwdBlock - 1) / kFwdBlock), kFwdBlock, 0, m->stream>>>(m->P, n, X, y);
+  if (m->precision == DVM_BF16S) {
+    const long long tiles = (n + 127) / 128;
+    const unsigned grid = (unsigned)(tiles < 152 * 4 ? tiles : 152 * 4);
+    k_mlp_forward_tc<<<grid, tc::kTcThreads, 0, m->stream>>>(m->P, n, X, y, m->status);
+  } else {
+    k_mlp_forward_f32<<<(unsigned)((n + kFwdBlock - 1) / kFwdBlock), kFwdBlock, 0, m->stream>>>(m->P, n, X, y);
+  }
   int rc = mcheck(m, cudaGetLastError(), "forward launch");
   if (!rc) rc = mcheck(m, cudaStreamSynchronize(m->stream), "sync");
-  return rc ? DVM_ERR_CUDA : 0;
+  if (rc) return DVM_ERR_CUDA;
+  int st = 0;
+  if (m->precision == DVM_BF16S) {
+    rc = mcheck(m, cudaMemcpy(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost), "status");
+    if (rc) return DVM_ERR_CUDA;
+    if (st) return mfail(m, st, "tensor-core forward did not complete");
+  }
+  return 0;
 }
 
 int dvm_mlp_loss_grad(dvm_mlp* m, long long n, const float* X, const float* t, double* grad,

@@ -224,3 +224,38 @@ def test_mlp_mode_flags_follow_the_network():
     assert np.array_equal(fl, pred < thr)
     st = s.learn_stats()
     assert st["steps"] == 1 and st["checks"] == 1 and st["flagged"] == fl.sum()
+
+
+def test_tensor_core_forward_matches_oracle():
+    """BF16 operands, FP32 accumulate (tcgen05): within BF16 rounding of the FP64
+    network (inputs, weights and the hidden layer carry 8-bit mantissas)."""
+    rng = np.random.default_rng(23)
+    P = (rng.standard_normal(dvm.MLP_NPARAM) * 0.3).astype(np.float32)
+    X = rng.standard_normal((1000, 10)).astype(np.float32)  # 7 full tiles + a ragged one
+    m = dvm.Mlp(dvm.BF16S)
+    m.set_params(P)
+    got = m.forward(X).cpu().numpy().astype(np.float64)
+    want = oracle.mlp_forward(P.astype(np.float64), X.astype(np.float64))
+    err = np.abs(got - want)
+    assert err.max() <= 0.03 * max(1.0, np.abs(want).max()), err.max()
+    assert np.corrcoef(got, want)[0, 1] > 0.9999
+
+
+def test_mlp_mode_with_tensor_core_network():
+    case = shear_case(n=40, nv=12, dv=0.9)
+    s = dvm.Solver.from_case(case, precision=dvm.F32)
+    s.set_moments(conserved(case))
+    s.step(1)
+    U = s.moments()
+    rng = np.random.default_rng(8)
+    P = (rng.standard_normal(dvm.MLP_NPARAM) * 0.2).astype(np.float32)
+    F = oracle.features(grid(case), U, case.tau)
+    shift, scale = F.mean(1), 1.0 / (F.std(1) + 1e-6)
+    s.learn_enable(dvm.LEARN_MLP, mlp_precision=dvm.BF16S, thr=0.0, shift=shift, scale=scale)
+    s.learn_set_params(P)
+    s.step(1)
+    pred = s.learn_predictions().astype(np.float64)
+    Xn = ((F.T - shift.astype(np.float32)) * scale.astype(np.float32)).astype(np.float64)
+    want = oracle.mlp_forward(P.astype(np.float64), Xn)
+    assert np.abs(pred - want).max() <= 0.03 * max(1.0, np.abs(want).max())
+    assert np.array_equal(s.learn_flags() != 0, pred < 0.0)
