@@ -45,6 +45,7 @@ WORKLOADS = {
     "quadrant_2d_bf16": (lambda: W.quadrant_2d(n=256, nv=32, tau=1e-3, steps=500), "bf16"),
     "sod_1d": (lambda: W.sod_1d(nx=200, nv=32, tau=1e-4), "f64"),
     "batched_tubes": (lambda: W.batched_tubes(ncases=512, steps=100), "f32"),
+    "shear_learned": (lambda: W.shear_layer_2d(n=512, nv=32, steps=50, dv=0.4), "f32"),
 }
 DESCR = {
     "quadrant_2d": "2D-2V four-quadrant Riemann problem, 256x256 periodic cells x 32x32 velocities, "
@@ -56,6 +57,9 @@ DESCR = {
     "quadrant_2d_f64": "2D-2V four-quadrant Riemann problem, 256^2 x 32^2, HOFKS, FP64 f",
     "quadrant_2d_bf16": "2D-2V four-quadrant Riemann problem, 256^2 x 32^2, HOFKS, BF16 f storage",
     "sod_1d": "1D-1V Sod tube, 200 cells x 32 velocities, tau=1e-4, outflow, HOFKS, FP64",
+    "shear_learned": "2D-2V shear layer, 512x512 periodic cells x 32x32 velocities, "
+                     "tau = 1e-5*10^(5r) (seeded smooth r), HOFKS FP32 + learned regime path vs plain "
+                     "FP32 and plain FP64, 50 steps",
     "batched_tubes": "512 independent 1D-1V Riemann tubes in one batched launch per phase, "
                      "N_x ~ U{100..2000}, N_v in {32,64,128}, tau = 10^U(-5,0), outflow, HOFKS, "
                      "FP32 f / FP64 moments",
@@ -279,6 +283,83 @@ class Job:
         return ms / n
 
 
+def run_learned(args, case, descr, rank, local):
+    """The learned regime path against the plain scheme on the 2D shear layer:
+    updates/s of FP32 + learned, plain FP32 and plain FP64 over the same steps, and
+    the L1 density error of each FP32 run against the FP64 run (the FP64 GPU form
+    agrees with the oracle to 1e-12).  value = learned / plain-FP64 speedup."""
+    import torch
+    from paper_1212_0204_gb300 import dvm, learned
+
+    torch.cuda.set_device(local)
+    net = learned.train_for_shear_layer(n=128, nv=case.nv[0], nsnap=200, warmup=10, dv=case.dv)
+    mlp_prec = dvm.BF16S if args.mlp == "bf16" else dvm.F32
+
+    def run(precision, with_net):
+        s = dvm.Solver.from_case(case, precision=precision)
+        s.set_primitive(case.rho, case.u, case.T)
+        if with_net:
+            learned.enable(s, net, args.thr, mlp_precision=mlp_prec)
+        s.step(args.warmup)
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        start.record(s.stream)
+        s.step_async(args.steps - args.warmup)
+        stop.record(s.stream)
+        stop.synchronize()
+        s.sync_status()
+        ms = start.elapsed_time(stop) / (args.steps - args.warmup)
+        U = s.moments()
+        st = s.learn_stats() if with_net else None
+        kin = None
+        if precision == dvm.F32:
+            s.profile_begin()
+            s.step(3)
+            kms, nk = s.profile_end()
+            kin = kms / nk
+        s.close()
+        return U, ms, st, kin
+
+    with ClockSampler(physical_gpu_index(local)) as clk:
+        U64, ms64, _, _ = run(dvm.F64, False)
+        U32, ms32, _, kin32 = run(dvm.F32, False)
+        UL, msl, st, kinl = run(dvm.F32, True)
+    l1 = lambda U: float(np.abs(U[0] - U64[0]).sum() / np.abs(U64[0]).sum())
+    pts = case.points
+    ups = lambda ms: pts / (ms * 1e-3)
+    peak, peak_kind = load_peaks()
+    achieved = BYTES_PER_UPDATE["f32"] * pts / (kinl * 1e-3) / 1e9
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "learned/plain speedup at same L1 err", "value": ups(msl) / ups(ms64), "unit": "x",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": msl,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": descr, "cells": case.ncells, "points": pts,
+                   "l2": "f larger than L2 (no flush)", "threshold": args.thr,
+                   "network": f"10-64-64-1 {args.mlp}, trained on 200 snapshots of the plain FP64 run at 128^2",
+                   "l1_horizon_steps": args.steps},
+        "learned": {"updates_per_s": ups(msl), "ms_per_step": msl, "l1_vs_fp64": l1(UL),
+                    "flagged_fraction_avg": st["flagged_total"] / max(st["steps"], 1) / case.ncells,
+                    "checks": st["checks"], "checked": st["checked"], "failed": st["failed"],
+                    "vetoed": st["vetoed"], "written_back": st["materialised"],
+                    "net_train_mse": net.train_mse, "net_val_mse": net.val_mse},
+        "plain_fp32": {"updates_per_s": ups(ms32), "ms_per_step": ms32, "l1_vs_fp64": l1(U32),
+                       "kinetic_ms": kin32},
+        "plain_fp64": {"updates_per_s": ups(ms64), "ms_per_step": ms64},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "kinetic_pass (learned run)",
+                     "peak_source": peak_kind, "kernel_ms": kinl},
+        "cpu_baseline": None,
+        "e2e": None,
+        "gpu_launches": None,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -287,6 +368,10 @@ def main():
     ap.add_argument("--workload", default="quadrant_2d", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--thr", type=float, default=-3.5,
+                    help="shear_learned: flag threshold on the predicted log10 non-equilibrium")
+    ap.add_argument("--mlp", default="bf16", choices=["bf16", "f32"],
+                    help="shear_learned: network precision (bf16 = tensor cores)")
     ap.add_argument("--cells", type=int, default=None,
                     help="override the cells per dimension (small profiling captures)")
     args = ap.parse_args()
@@ -308,6 +393,8 @@ def main():
     descr = DESCR[args.workload]
     if args.impl == "reference":
         return run_reference(args, case, descr, rank)
+    if args.workload == "shear_learned":
+        return run_learned(args, case, descr, rank, local)
 
     import torch
     from paper_1212_0204_gb300 import dvm
