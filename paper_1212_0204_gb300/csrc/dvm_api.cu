@@ -471,6 +471,12 @@ int dvm_create(const dvm_config* cfg, void* workspace, void* cuda_stream, dvm_ha
   h->all_free = all_free;
   h->g.skip_euler = all_free ? 1 : 0;
   h->g.euler_blocks = euler_blocks(h->g);
+  // optional cap of the Euler grid (fewer co-resident blocks leave room on
+  // every SM for the concurrent kinetic pass)
+  if (const char* eb = getenv("DVM_EULER_BLOCKS")) {
+    const int cap = atoi(eb);
+    if (cap > 0 && cap < h->g.euler_blocks) h->g.euler_blocks = cap;
+  }
   h->g.m_cap = cfg->max_subcycles > 0 ? cfg->max_subcycles : 1000000;
   if (cfg->euler_subcycles > 0 && h->g.m_cap < cfg->euler_subcycles) h->g.m_cap = cfg->euler_subcycles;
   cudaStream_t s = h->stream;

@@ -185,8 +185,14 @@ __global__ void __launch_bounds__(kB) k_b_euler(BPtrs p) {
   TW* W0 = reinterpret_cast<TW*>(s_raw);
   TW* W1 = W0 + 3 * nx;
   // W = (1 - lambda) U and the alpha of every sub-step's initial state (Eq.
-  // Time2 per sub-step, the last one ending at dt)
-  double amax = 0.0;
+  // Time2 per sub-step, the last one ending at dt).  alpha is reduced in the
+  // state's type; the sub-step scalars are computed once per CTA by thread 0
+  // (FP64 in the FP64 build, the quotient in FP32 otherwise) and broadcast.
+  __shared__ TW s_redw[kB / 32];
+  __shared__ double s_dtE;
+  __shared__ TW s_kk, s_alw;
+  __shared__ int s_flags;  // bit 0: last sub-step, bit 1: stop (error or all free)
+  TW amax = TW(0);
   for (int x = tid; x < nx; x += kB) {
     const long long c = bc.c_off + x;
     const double w = bc.all_free ? 0.0 : 1.0 - p.lam[c];
@@ -195,40 +201,55 @@ __global__ void __launch_bounds__(kB) k_b_euler(BPtrs p) {
       W[i] = (TW)(w * p.U[i * nc + c]);
       W0[i * nx + x] = W[i];
     }
-    double a[3];
+    TW a[3];
     state_alpha_of<1>(W, a);
-    amax = fmax(amax, a[0]);
+    amax = amax > a[0] ? amax : a[0];
   }
   double t = 0.0, a0 = 0.0;
   int s = 0;
   for (;; ++s) {
-    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    if ((tid & 31) == 0) s_red[tid >> 5] = amax;
-    __syncthreads();
-    double al = 0.0;
-    for (int w = 0; w < kB / 32; ++w) al = fmax(al, s_red[w]);
-    __syncthreads();
-    if (s == 0) a0 = al;
-    if (bc.all_free) break;
-    double dtE;
-    bool last;
-    if (bc.forced_sub > 0) {
-      dtE = bc.dt / bc.forced_sub;
-      last = s + 1 == bc.forced_sub;
-    } else {
-      if (!(al > 0.0)) {
-        if (tid == 0) set_status(p.status, DVM_ERR_NONPHYSICAL);
-        break;
-      }
-      const double cfl = __ddiv_rn(__dmul_rn(0.5, bc.dx), al);
-      const double rem = __dsub_rn(bc.dt, t);
-      last = cfl >= rem;
-      dtE = last ? rem : cfl;
+    for (int o = 16; o > 0; o >>= 1) {
+      const TW v = __shfl_xor_sync(0xffffffffu, amax, o);
+      amax = amax > v ? amax : v;
     }
-    const TW kk = (TW)(dtE / bc.dx), alw = (TW)al;
+    if ((tid & 31) == 0) s_redw[tid >> 5] = amax;
+    __syncthreads();
+    if (tid == 0) {
+      TW alt = TW(0);
+      for (int w = 0; w < kB / 32; ++w) alt = alt > s_redw[w] ? alt : s_redw[w];
+      const double al = (double)alt;
+      if (s == 0) a0 = al;
+      int flags = 0;
+      double dtE = 0.0;
+      if (bc.all_free) {
+        flags = 2;
+      } else if (bc.forced_sub > 0) {
+        dtE = bc.dt / bc.forced_sub;
+        flags = (s + 1 == bc.forced_sub) ? 1 : 0;
+      } else if (!(al > 0.0)) {
+        set_status(p.status, DVM_ERR_NONPHYSICAL);
+        flags = 2;
+      } else {
+        const double cfl = sizeof(TW) == 8 ? __ddiv_rn(__dmul_rn(0.5, bc.dx), al)
+                                           : (double)__fdiv_rn(0.5f * (float)bc.dx, (float)al);
+        const double rem = __dsub_rn(bc.dt, t);
+        flags = cfl >= rem ? 1 : 0;
+        dtE = flags ? rem : cfl;
+      }
+      s_dtE = dtE;
+      s_kk = sizeof(TW) == 8 ? (TW)(dtE / bc.dx) : (TW)((float)dtE / (float)bc.dx);
+      s_alw = alt;
+      s_flags = flags;
+      t = __dadd_rn(t, dtE);
+    }
+    __syncthreads();
+    const int flags = s_flags;
+    if (flags & 2) break;
+    const bool last = (flags & 1) != 0;
+    const TW kk = s_kk, alw = s_alw;
     const TW* src = (s & 1) ? W1 : W0;
     TW* dst = (s & 1) ? W0 : W1;
-    amax = 0.0;
+    amax = TW(0);
     for (int x = tid; x < nx; x += kB) {
       TW Us[5][3], Fs[5][3], Wn[3];
       for (int o = 0; o < 5; ++o) {
@@ -252,12 +273,13 @@ __global__ void __launch_bounds__(kB) k_b_euler(BPtrs p) {
         Wn[i] = Us[2][i] - kk * (psi[1] - psi[0]);
         dst[i * nx + x] = Wn[i];
       }
-      double a[3];
-      state_alpha_of<1>(Wn, a);
-      amax = fmax(amax, a[0]);
+      if (!last) {
+        TW a[3];
+        state_alpha_of<1>(Wn, a);
+        amax = amax > a[0] ? amax : a[0];
+      }
     }
     __syncthreads();
-    t = __dadd_rn(t, dtE);
     if (last) break;
     if (s + 1 >= 1000000) {
       if (tid == 0) set_status(p.status, DVM_ERR_CFL);

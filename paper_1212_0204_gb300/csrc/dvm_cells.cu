@@ -293,22 +293,50 @@ __global__ void __launch_bounds__(ETile<D, TF>::THREADS) k_euler(Geom g, DevPtrs
   __shared__ TF s_k, s_al[3];
   __shared__ int s_last, s_bad;
   double t = 0.0, a0[3] = {0.0, 0.0, 0.0};
+  // stage tile `tile` of the state src with its two-cell halo (loads bypass
+  // L1: other blocks rewrite the buffers between sub-steps)
+  auto stage = [&](const TF* src, int tile) {
+    const int x0 = (tile % ntx) * T::TX;
+    const int y0 = ((tile / ntx) % nty) * T::TY;
+    const int z = tile / (ntx * nty);
+    for (int i = tid; i < T::NS; i += T::THREADS) {
+      const int lx = i % T::SX, ly = (i / T::SX) % T::SY, lz = i / (T::SX * T::SY);
+      const int gx = bc_index(x0 - 2 + lx, Nx, g.bc[0]);
+      const int gy = D >= 2 ? bc_index(y0 - 2 + ly, Ny, g.bc[1]) : 0;
+      const int gz = D == 3 ? bc_index(z - 2 + lz, Nz, g.bc[2]) : 0;
+      const long long cc = gx + (long long)Nx * (gy + (long long)Ny * gz);
+#pragma unroll
+      for (int c = 0; c < NM; ++c) sw[c * T::NS + i] = __ldcg(src + c * nc + cc);
+    }
+  };
   int s = 0;
   for (;; ++s) {
+    const TF* src = (const TF*)((s & 1) ? p.W1 : p.W0);
+    TF* dst = (TF*)((s & 1) ? p.W0 : p.W1);
+    // thread 0 issues its reads of the barrier generation and of this
+    // sub-step's alpha first; their latency overlaps the first tile's staging
+    unsigned gen = 0;
+    double ad[3] = {0.0, 0.0, 0.0};
     if (tid == 0) {
+      gen = *reinterpret_cast<volatile unsigned*>(p.gbar + 1);
       // alpha of this sub-step's initial state: slot s % 3, complete since the
-      // barrier that ended the previous sub-step; slot (s + 2) % 3 was last
-      // read before that barrier and is cleared for sub-step s + 2
-      double ad[3], asum = 0.0;
+      // barrier that ended the previous sub-step
 #pragma unroll
       for (int d = 0; d < 3; ++d) ad[d] = __longlong_as_double((long long)__ldcg(p.aslot + (s % 3) * 3 + d));
+    }
+    if ((int)blockIdx.x < ntiles) stage(src, blockIdx.x);
+    if (tid == 0) {
+      double asum = 0.0;
 #pragma unroll
       for (int d = 0; d < D; ++d) asum = __dadd_rn(asum, ad[d]);
       if (s == 0) a0[0] = ad[0], a0[1] = ad[1], a0[2] = ad[2];
+      // slot (s + 2) % 3 was last read before the previous barrier: cleared
+      // for sub-step s + 2
       if (blockIdx.x == 0)
         for (int d = 0; d < 3; ++d) p.aslot[((s + 2) % 3) * 3 + d] = 0ull;
       // length of this sub-step: Eq. Time2 with its own alpha, the last one
-      // ending exactly at the kinetic dt (same arithmetic in every block)
+      // ending exactly at the kinetic dt (same arithmetic in every block; the
+      // quotient in the storage precision's arithmetic)
       double dtE = 0.0;
       int last = 0, bad = 0;
       if (g.forced_sub > 0) {
@@ -317,13 +345,14 @@ __global__ void __launch_bounds__(ETile<D, TF>::THREADS) k_euler(Geom g, DevPtrs
       } else if (!(asum > 0.0)) {
         bad = 1;
       } else {
-        const double cfl = __ddiv_rn(__dmul_rn(0.5, g.dx), asum);
+        const double cfl = sizeof(TF) == 8 ? __ddiv_rn(__dmul_rn(0.5, g.dx), asum)
+                                           : (double)__fdiv_rn(0.5f * (float)g.dx, (float)asum);
         const double rem = __dsub_rn(g.dt, t);
         last = cfl >= rem;
         dtE = last ? rem : cfl;
       }
       s_dtE = dtE;
-      s_k = (TF)(dtE / g.dx);
+      s_k = sizeof(TF) == 8 ? (TF)(dtE / g.dx) : (TF)((float)dtE / (float)g.dx);
       for (int d = 0; d < 3; ++d) s_al[d] = (TF)ad[d];
       s_last = last;
       s_bad = bad;
@@ -336,23 +365,15 @@ __global__ void __launch_bounds__(ETile<D, TF>::THREADS) k_euler(Geom g, DevPtrs
     TF al[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) al[d] = s_al[d];
-    const TF* src = (const TF*)((s & 1) ? p.W1 : p.W0);
-    TF* dst = (TF*)((s & 1) ? p.W0 : p.W1);
     TF amax[3] = {TF(0), TF(0), TF(0)};
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
       const int x0 = (tile % ntx) * T::TX;
       const int y0 = ((tile / ntx) % nty) * T::TY;
       const int z = tile / (ntx * nty);
-      for (int i = tid; i < T::NS; i += T::THREADS) {
-        const int lx = i % T::SX, ly = (i / T::SX) % T::SY, lz = i / (T::SX * T::SY);
-        const int gx = bc_index(x0 - 2 + lx, Nx, g.bc[0]);
-        const int gy = D >= 2 ? bc_index(y0 - 2 + ly, Ny, g.bc[1]) : 0;
-        const int gz = D == 3 ? bc_index(z - 2 + lz, Nz, g.bc[2]) : 0;
-        const long long cc = gx + (long long)Nx * (gy + (long long)Ny * gz);
-#pragma unroll
-        for (int c = 0; c < NM; ++c) sw[c * T::NS + i] = __ldcg(src + c * nc + cc);
+      if (tile != (int)blockIdx.x) {
+        stage(src, tile);
+        __syncthreads();
       }
-      __syncthreads();
       if (mydir == 0) tile_faces<TF, LIMITED, D, 0>(sw, sf, ctr, tx, ty, al[0]);
       else if (D >= 2 && mydir == 1) tile_faces<TF, LIMITED, D, (D >= 2 ? 1 : 0)>(sw, sf, ctr, tx, ty, al[D >= 2 ? 1 : 0]);
       else if (D == 3) tile_faces<TF, LIMITED, D, (D == 3 ? 2 : 0)>(sw, sf, ctr, tx, ty, al[D == 3 ? 2 : 0]);
@@ -407,7 +428,7 @@ __global__ void __launch_bounds__(ETile<D, TF>::THREADS) k_euler(Geom g, DevPtrs
       if (blockIdx.x == 0 && tid == 0) set_status(p.status, DVM_ERR_CFL);
       break;
     }
-    if (!grid_sync(p.gbar, p.status)) return;
+    if (!grid_sync(p.gbar, p.status, gen)) return;
   }
   if (blockIdx.x == 0 && tid == 0) {
     *p.msub = s + 1;

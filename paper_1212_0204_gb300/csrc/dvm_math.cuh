@@ -121,12 +121,13 @@ __device__ inline TF slope(TF a, TF b) {
 // last block to arrive advances the generation word.  The wait is bounded
 // (2^31 SM clock cycles, about a second); on timeout the status word gets
 // DVM_ERR_TIMEOUT and false is returned so that the kernel can leave.
-__device__ bool grid_sync(unsigned* bar, int* status) {
+// gen: the generation word as thread 0 read it before its block did the work
+// of this phase (it can only change once every block has arrived).
+__device__ bool grid_sync(unsigned* bar, int* status, unsigned gen) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* vgen = bar + 1;
-    const unsigned gen = *vgen;
     __threadfence();
     int good = 1;
     if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
