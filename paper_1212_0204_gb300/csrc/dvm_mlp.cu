@@ -195,6 +195,225 @@ __global__ void __launch_bounds__(tc::kTcThreads) k_mlp_forward_tc(const float* 
   tc::mlp_tc_teardown(S);
 }
 
+
+// Loss and gradient on the tensor cores (BF16 operands, FP32 accumulation):
+// CTAs walk 128-sample tiles; the weight gradient of all its tiles stays in
+// TMEM (D_G += AG BG^T per tile) and is added to the FP64 total once.
+__global__ void __launch_bounds__(tc::kTcThreads) k_mlp_grad_tc(const float* __restrict__ P,
+                                                                const float* __restrict__ X,
+                                                                const float* __restrict__ T,
+                                                                const int* __restrict__ idx,
+                                                                long long first, long long count,
+                                                                float scale, double* __restrict__ grad,
+                                                                double* __restrict__ loss, int* status) {
+  extern __shared__ __align__(1024) unsigned char s_raw[];
+  tc::TrainSmem& S = *reinterpret_cast<tc::TrainSmem*>(s_raw);
+  const int t = threadIdx.x, warp = t >> 5;
+  using tc::kmajor_offset;
+  using tc::st_bf16;
+  // ---- setup: weights in operand layout, biases, accumulators, mbarrier, TMEM
+  for (int i = t; i < 64 * 16; i += tc::kTcThreads) {
+    const int j = i / 16, k = i % 16;
+    st_bf16(S.B1, kmajor_offset(j, k, 16), k < 10 ? P[kOffW1 + j * 10 + k] : 0.f);
+  }
+  for (int i = t; i < 64 * 64; i += tc::kTcThreads) {
+    const int j = i / 64, k = i % 64;
+    const float w = P[kOffW2 + i];        // W2[j][k]
+    st_bf16(S.B2, kmajor_offset(j, k, 64), w);
+    st_bf16(S.B3, kmajor_offset(k, j, 64), w);  // W2^T: row k, column j
+  }
+  // BG rows 80..95: ones (row 80) and zeros, set once
+  for (int i = t; i < 16 * 128; i += tc::kTcThreads) {
+    const int r = 80 + i / 128, s = i % 128;
+    st_bf16(S.BG, kmajor_offset(r, s, 128), r == 80 ? 1.f : 0.f);
+  }
+  if (t < 64) {
+    S.b1[t] = P[kOffB1 + t];
+    S.b2[t] = P[kOffB2 + t];
+    S.w3[t] = P[kOffW3 + t];
+    S.gw3[t] = 0.f;
+  }
+  if (t == 0) {
+    S.b3 = P[kOffB3];
+    S.gb3 = 0.f;
+    tc::mbar_init(&S.mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (t < 32) {
+    tc::tmem_alloc(&S.tbase, tc::kTrainTmemCols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const unsigned lane_addr = S.tbase + ((unsigned)(warp * 32) << 16);
+  constexpr uint32_t id64 = tc::idesc_bf16(128, 64), id96 = tc::idesc_bf16(128, 96);
+  unsigned phase = 0;
+  int ntile = 0;
+  bool ok = true;
+  float lsum = 0.f;
+  const long long ntiles = (count + 127) / 128;
+  auto sync_mma = [&]() {  // operands written -> visible to the tensor cores
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  };
+  auto wait_mma = [&]() -> bool {
+    const bool w = tc::mbar_wait(&S.mbar, phase);
+    phase ^= 1u;
+    const bool all = __syncthreads_and(w) != 0;
+    tc::fence_after_sync();
+    return all;
+  };
+  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++ntile) {
+    const long long j = tile * 128 + t;
+    const bool real = j < count;
+    const long long r = real ? (idx ? idx[first + j] : first + j) : 0;
+    float x[kNIn];
+#pragma unroll
+    for (int i = 0; i < kNIn; ++i) x[i] = real ? X[r * kNIn + i] : 0.f;
+    const float target = real ? T[r] : 0.f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const float v = k < 10 ? x[k] : 0.f;
+      st_bf16(S.A1, kmajor_offset(t, k, 16), v);
+      st_bf16(S.BG, kmajor_offset(64 + k, t, 128), v);  // x^T
+    }
+    sync_mma();
+    if (t == 0) {
+      tc::mma_bf16(S.tbase, tc::smem_desc(S.A1, 128, 256), tc::smem_desc(S.B1, 128, 256), id64, 0);
+      tc::mma_commit(&S.mbar);
+    }
+    if (!(ok = wait_mma())) break;
+    float h1[64];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float v[16];
+      tc::tmem_ld16(lane_addr + 16 * c, v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int i = 16 * c + q;
+        h1[i] = tc::tanh_approx(v[q] + S.b1[i]);
+        st_bf16(S.A2, kmajor_offset(t, i, 64), h1[i]);
+        st_bf16(S.BG, kmajor_offset(i, t, 128), h1[i]);  // h1^T
+      }
+    }
+    sync_mma();
+    if (t == 0) {
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks)
+        tc::mma_bf16(S.tbase + 64, tc::smem_desc(reinterpret_cast<char*>(S.A2) + 256 * ks, 128, 1024),
+                     tc::smem_desc(reinterpret_cast<char*>(S.B2) + 256 * ks, 128, 1024), id64, ks > 0);
+      tc::mma_commit(&S.mbar);
+    }
+    if (!(ok = wait_mma())) break;
+    // output, error, dL/dy; d2 = dy W3 (1 - h2^2); dW3 and db3 sums
+    float h2[64];
+    float y = S.b3;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float v[16];
+      tc::tmem_ld16(lane_addr + 64 + 16 * c, v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int i = 16 * c + q;
+        h2[i] = tc::tanh_approx(v[q] + S.b2[i]);
+        y = fmaf(S.w3[i], h2[i], y);
+      }
+    }
+    const float e = real ? y - target : 0.f;
+    const float dy = 2.f * e * scale;
+    lsum = fmaf(e, e, lsum);
+    const int lane = t & 31;
+#pragma unroll
+    for (int i = 0; i < 64; ++i) {
+      const float d2 = dy * S.w3[i] * (1.f - h2[i] * h2[i]);
+      st_bf16(S.A3, kmajor_offset(t, i, 64), d2);
+      st_bf16(S.AG, kmajor_offset(i, t, 128), d2);  // d2^T
+      float g = dy * h2[i];  // dL/dW3_i of this sample, summed over the warp
+      for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+      if (lane == 0) atomicAdd(&S.gw3[i], g);
+    }
+    {
+      float g = dy;
+      for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+      if (lane == 0) atomicAdd(&S.gb3, g);
+    }
+    sync_mma();
+    if (t == 0) {
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks)
+        tc::mma_bf16(S.tbase, tc::smem_desc(reinterpret_cast<char*>(S.A3) + 256 * ks, 128, 1024),
+                     tc::smem_desc(reinterpret_cast<char*>(S.B3) + 256 * ks, 128, 1024), id64, ks > 0);
+      tc::mma_commit(&S.mbar);
+    }
+    if (!(ok = wait_mma())) break;
+    // d1 = dL/dh1 (1 - h1^2) into AG rows 64..127
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float v[16];
+      tc::tmem_ld16(lane_addr + 16 * c, v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int i = 16 * c + q;
+        st_bf16(S.AG, kmajor_offset(64 + i, t, 128), v[q] * (1.f - h1[i] * h1[i]));
+      }
+    }
+    sync_mma();
+    if (t == 0) {
+#pragma unroll
+      for (int ks = 0; ks < 8; ++ks)
+        tc::mma_bf16(S.tbase + 128, tc::smem_desc(reinterpret_cast<char*>(S.AG) + 256 * ks, 128, 2048),
+                     tc::smem_desc(reinterpret_cast<char*>(S.BG) + 256 * ks, 128, 2048), id96,
+                     (ntile > 0 || ks > 0) ? 1 : 0);
+      tc::mma_commit(&S.mbar);
+    }
+    // AG and BG are rewritten by the next tile: wait for this product
+    if (!(ok = wait_mma())) break;
+  }
+  if (!ok) {
+    if (t == 0) atomicCAS(status, 0, DVM_ERR_TIMEOUT);
+  } else if (ntile > 0) {
+    // D_G rows: lane r < 64 -> (dW2[r][0..63], db2[r] at column 80);
+    //           lane 64 + i -> (dW1[i][0..9] at columns 64..73, db1[i] at 80)
+    float v[16];
+    if (warp < 2) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        tc::tmem_ld16(lane_addr + 128 + 16 * c, v);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) atomicAdd(&grad[kOffW2 + t * 64 + 16 * c + q], (double)v[q]);
+      }
+      tc::tmem_ld16(lane_addr + 128 + 80, v);
+      tc::tmem_ld_wait();
+      atomicAdd(&grad[kOffB2 + t], (double)v[0]);
+    } else {
+      const int i = t - 64;
+      tc::tmem_ld16(lane_addr + 128 + 64, v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int k = 0; k < 10; ++k) atomicAdd(&grad[kOffW1 + i * 10 + k], (double)v[k]);
+      tc::tmem_ld16(lane_addr + 128 + 80, v);
+      tc::tmem_ld_wait();
+      atomicAdd(&grad[kOffB1 + i], (double)v[0]);
+    }
+    __syncthreads();
+    if (t < 64) atomicAdd(&grad[kOffW3 + t], (double)S.gw3[t]);
+    if (t == 0) atomicAdd(&grad[kOffB3], (double)S.gb3);
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if ((t & 31) == 0) atomicAdd(loss, (double)lsum);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (t < 32) tc::tmem_dealloc(S.tbase, tc::kTrainTmemCols);
+}
+
 __global__ void k_adam(float* __restrict__ P, float* __restrict__ m, float* __restrict__ v,
                        const double* __restrict__ grad, float lr, float b1, float b2, float eps,
                        float c1, float c2) {
@@ -225,16 +444,37 @@ int mcheck(dvm_mlp* m, cudaError_t e, const char* what) {
   return mfail(m, DVM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// gradient (and summed squared error) of samples first .. first + count of
+// the order idx (or of X itself) into m->grad / m->loss, which the caller zeroes
+void launch_grad(dvm_mlp* m, long long n, const float* X, const float* T, const int* idx,
+                 long long first, long long count, float scale) {
+  cudaStream_t s = m->stream;
+  if (m->precision == DVM_BF16S) {
+    const long long tiles = (count + 127) / 128;
+    const unsigned nb = (unsigned)(tiles < 152 ? tiles : 152);  // ~114 KB shared: one CTA per SM
+    k_mlp_grad_tc<<<nb, tc::kTcThreads, sizeof(tc::TrainSmem), s>>>(m->P, X, T, idx, first, count, scale,
+                                                                    m->grad, m->loss, m->status);
+  } else {
+    const unsigned nb = (unsigned)((count + kGS - 1) / kGS);
+    k_mlp_grad_f32<<<nb, kGThreads, kGradSmemFloats * sizeof(float), s>>>(m->P, n, X, T, idx, first,
+                                                                           count, scale, m->grad, m->loss);
+  }
+}
+
 int grad_batch(dvm_mlp* m, long long n, const float* X, const float* T, const int* idx,
                long long first, long long count, float scale) {
   cudaStream_t s = m->stream;
   int rc = mcheck(m, cudaMemsetAsync(m->grad, 0, sizeof(double) * (kNP + 1), s), "memset");
   if (rc) return rc;
-  (void)n;
-  const unsigned nb = (unsigned)((count + kGS - 1) / kGS);
-  k_mlp_grad_f32<<<nb, kGThreads, kGradSmemFloats * sizeof(float), s>>>(m->P, n, X, T, idx, first,
-                                                                         count, scale, m->grad, m->loss);
+  launch_grad(m, n, X, T, idx, first, count, scale);
   return mcheck(m, cudaGetLastError(), "gradient launch");
+}
+
+int check_status(dvm_mlp* m) {
+  if (m->precision != DVM_BF16S) return 0;
+  int st = 0;
+  if (mcheck(m, cudaMemcpy(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost), "status")) return DVM_ERR_CUDA;
+  return st ? mfail(m, st, "tensor-core kernel did not complete") : 0;
 }
 
 }  // namespace
@@ -265,6 +505,8 @@ int dvm_mlp_create(int precision, void* cuda_stream, dvm_mlp** out) {
   m->status = (int*)(m->loss + 1);
   cudaFuncSetAttribute(k_mlp_grad_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(kGradSmemFloats * sizeof(float)));
+  cudaFuncSetAttribute(k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(tc::TrainSmem));
   if (cudaMemsetAsync(b, 0, 3 * pb + gb, m->stream) != cudaSuccess ||
       cudaStreamSynchronize(m->stream) != cudaSuccess) {
     cudaGetLastError();
@@ -340,6 +582,7 @@ int dvm_mlp_loss_grad(dvm_mlp* m, long long n, const float* X, const float* t, d
   rc |= mcheck(m, cudaMemcpyAsync(&l, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->stream), "copy");
   rc |= mcheck(m, cudaStreamSynchronize(m->stream), "sync");
   if (rc) return DVM_ERR_CUDA;
+  if ((rc = check_status(m))) return rc;
   if (loss) *loss = l / (double)n;
   return 0;
 }
@@ -379,9 +622,7 @@ int dvm_mlp_train(dvm_mlp* m, long long n, const float* X, const float* t,
       const long long cnt = (n - b) < cfg->batch ? (n - b) : cfg->batch;
       // the loss accumulates over the epoch: keep it out of the reset
       if ((rc = mcheck(m, cudaMemsetAsync(m->grad, 0, sizeof(double) * kNP, s), "memset"))) return rc;
-      const unsigned nb = (unsigned)((cnt + kGS - 1) / kGS);
-      k_mlp_grad_f32<<<nb, kGThreads, kGradSmemFloats * sizeof(float), s>>>(
-          m->P, n, X, t, m->perm, b, cnt, 1.f / (float)cnt, m->grad, m->loss);
+      launch_grad(m, n, X, t, m->perm, b, cnt, 1.f / (float)cnt);
       ++m->t;
       const float c1 = 1.f / (1.f - powf(cfg->beta1, (float)m->t));
       const float c2 = 1.f / (1.f - powf(cfg->beta2, (float)m->t));
@@ -392,6 +633,7 @@ int dvm_mlp_train(dvm_mlp* m, long long n, const float* X, const float* t,
     double l = 0.0;
     if ((rc = mcheck(m, cudaMemcpyAsync(&l, m->loss, sizeof(double), cudaMemcpyDeviceToHost, s), "copy"))) return rc;
     if ((rc = mcheck(m, cudaStreamSynchronize(s), "sync"))) return rc;
+    if ((rc = check_status(m))) return rc;
     last = l / (double)n;
   }
   if (loss) *loss = last;

@@ -250,3 +250,39 @@ __device__ inline bool mlp_tc_tile(MlpSmem& S, unsigned& phase, const float x[10
 
 }  // namespace tc
 }  // namespace dvm
+
+namespace dvm {
+namespace tc {
+
+// Shared memory of the tensor-core training kernel (loss and gradient of the
+// 10-64-64-1 network, 128 samples per tile).  Operands (bf16, K-major):
+//   A1 [128 x 16]  inputs            B1 [64 x 16]  W1
+//   A2 [128 x 64]  h1                B2 [64 x 64]  W2
+//   A3 [128 x 64]  d2 = dL/dz2       B3 [64 x 64]  W2^T (rows i, K = j)
+//   AG [128 x 128] rows 0-63: d2^T, rows 64-127: d1^T (K = samples)
+//   BG [96 x 128]  rows 0-63: h1^T, 64-79: x^T (padded), 80: ones (K = samples)
+// TMEM columns: [0, 64) layer-1 pre-activations, then dL/dh1; [64, 128) layer 2;
+// [128, 224) the weight-gradient accumulator D_G = AG BG^T.
+struct TrainSmem {
+  __nv_bfloat16 A1[128 * 16];
+  __nv_bfloat16 B1[64 * 16];
+  __nv_bfloat16 A2[128 * 64];
+  __nv_bfloat16 B2[64 * 64];
+  __nv_bfloat16 A3[128 * 64];
+  __nv_bfloat16 B3[64 * 64];
+  __nv_bfloat16 AG[128 * 128];
+  __nv_bfloat16 BG[96 * 128];
+  float b1[64], b2[64], w3[64], b3;
+  float gw3[64], gb3;  // CTA sums of dL/dW3, dL/db3
+  uint64_t mbar;
+  unsigned tbase;
+};
+
+constexpr unsigned kTrainTmemCols = 256;
+
+__device__ __forceinline__ void st_bf16(void* base, int off, float v) {
+  *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(base) + off) = __float2bfloat16_rn(v);
+}
+
+}  // namespace tc
+}  // namespace dvm

@@ -42,10 +42,12 @@ def snapshots(case, nsnap: int = 200, warmup: int = 10, precision=dvm.F64):
     return X.reshape(-1, dvm.NFEAT), y.reshape(-1)
 
 
-def train(X, y, precision=dvm.F32, epochs: int = 20, batch: int = 1024, lr: float = 2e-3,
+def train(X, y, precision=dvm.BF16S, epochs: int = 20, batch: int = 1024, lr: float = 2e-3,
           val_frac: float = 0.2, seed: int = 1212) -> TrainedNet:
     """Adam on the mean squared error of the labels, 80/20 split by a seeded
-    shuffle; inputs standardised with the training split's mean and deviation."""
+    shuffle; inputs standardised with the training split's mean and deviation.
+    BF16S: forward and backward on the tensor cores (BF16 operands, FP32
+    accumulation, FP32 master weights); F32: FP32 on the CUDA cores."""
     import torch
     rng = np.random.default_rng(seed)
     order = rng.permutation(len(y))
@@ -77,7 +79,7 @@ def train(X, y, precision=dvm.F32, epochs: int = 20, batch: int = 1024, lr: floa
 
 
 def train_for_shear_layer(n: int = 128, nv: int = 32, nsnap: int = 200, warmup: int = 10,
-                          dv: float = 0.4, precision=dvm.F32, epochs: int = 20,
+                          dv: float = 0.4, precision=dvm.BF16S, epochs: int = 20,
                           seed: int = W.SEED_BASE) -> TrainedNet:
     """The regime network of the 2D shear-layer workload: snapshots of the plain
     FP64 run at n x n cells (one per step after the warm-up), then training."""

@@ -259,3 +259,36 @@ def test_mlp_mode_with_tensor_core_network():
     want = oracle.mlp_forward(P.astype(np.float64), Xn)
     assert np.abs(pred - want).max() <= 0.03 * max(1.0, np.abs(want).max())
     assert np.array_equal(s.learn_flags() != 0, pred < 0.0)
+
+
+def test_tensor_core_gradient_matches_oracle():
+    """BF16 tensor-core loss and gradient (forward, dL/dh1 = D2 W2 and the weight
+    gradients as tcgen05 MMAs, FP32 accumulation): norm-wise within 1e-2 of the
+    FP64 oracle gradient, loss within 1e-2."""
+    rng = np.random.default_rng(27)
+    P = (rng.standard_normal(dvm.MLP_NPARAM) * 0.3).astype(np.float32)
+    X = rng.standard_normal((1000, 10)).astype(np.float32)
+    y = rng.standard_normal(1000).astype(np.float32)
+    m = dvm.Mlp(dvm.BF16S)
+    m.set_params(P)
+    loss, g = m.loss_grad(X, y)
+    lo, go = oracle.mlp_loss_grad(P.astype(np.float64), X.astype(np.float64), y.astype(np.float64))
+    assert abs(loss - lo) <= 1e-2 * lo, (loss, lo)
+    rel = np.linalg.norm(g - go) / np.linalg.norm(go)
+    assert rel <= 1e-2, rel
+    # every parameter block is there (no block left at zero)
+    for a, b in ((0, 640), (640, 704), (704, 4800), (4800, 4864), (4864, 4928), (4928, 4929)):
+        assert np.linalg.norm(g[a:b] - go[a:b]) <= 5e-2 * np.linalg.norm(go[a:b]) + 1e-6, (a, b)
+
+
+def test_tensor_core_training_lowers_the_loss():
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((20000, 10)).astype(np.float32)
+    y = (np.tanh(X[:, 0] - 0.5 * X[:, 3]) + 0.1 * X[:, 7]).astype(np.float32)
+    P0 = (rng.standard_normal(dvm.MLP_NPARAM) * 0.1).astype(np.float32)
+    m = dvm.Mlp(dvm.BF16S)
+    m.set_params(P0)
+    l0, _ = m.loss_grad(X, y)
+    m.train(X, y, epochs=8, batch=512, lr=3e-3)
+    l2, _ = m.loss_grad(X, y)
+    assert l2 < 0.2 * l0, (l0, l2)
