@@ -41,6 +41,11 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     come from ``extra`` or the DVM_NVCC_EXTRA environment variable (space separated)."""
     extra = list(extra or []) + os.environ.get("DVM_NVCC_EXTRA", "").split()
     os.makedirs(OBJ, exist_ok=True)
+    # objects built with other flags are rebuilt
+    stamp = os.path.join(OBJ, "flags.txt")
+    flags = " ".join(ARCH + FLAGS + extra)
+    if not os.path.exists(stamp) or open(stamp).read() != flags:
+        force = True
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "dvm.h"))
     cc = nvcc()
@@ -62,6 +67,8 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         tmp = LIB + f".tmp{os.getpid()}"
         run([cc, *ARCH, "-shared", "-o", tmp, *objs])
         os.replace(tmp, LIB)
+    with open(stamp, "w") as fh:
+        fh.write(flags)
     return LIB
 
 

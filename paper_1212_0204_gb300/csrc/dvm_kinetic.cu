@@ -265,10 +265,16 @@ struct WinLaunch {
   int splits;  // velocity chunks across CTAs (partial-sum slices)
 };
 
-// Resident CTAs per SM the windowed pass is compiled for (register cap
-// 65536 / (128 * DVM_WIN_MINB)).
+// Warps per CTA of the windowed pass (each on every S-th velocity pair; their
+// parameter loads share L1 lines) and resident CTAs per SM it is compiled for
+// (register cap 65536 / (32 * DVM_WIN_S * DVM_WIN_MINB)).
+#ifndef DVM_WIN_S
+#define DVM_WIN_S 8
+#endif
+constexpr int kWinS = DVM_WIN_S;
+constexpr int kWinT = 32 * kWinS;
 #ifndef DVM_WIN_MINB
-#define DVM_WIN_MINB 4
+#define DVM_WIN_MINB 2
 #endif
 
 // CTA = S = 4 warps on the same 32 x Y targets; warp s takes the velocity
@@ -276,28 +282,28 @@ struct WinLaunch {
 // shifted by one column from each other, so their parameter loads share L1
 // lines.
 template <typename TS, int D, int Y, bool HOFKS, bool ASYNC, bool LEARN>
-__global__ void __launch_bounds__(128, DVM_WIN_MINB) k_kpass_window(Geom g, DevPtrs p, WinLaunch wl) {
+__global__ void __launch_bounds__(kWinT, DVM_WIN_MINB) k_kpass_window(Geom g, DevPtrs p, WinLaunch wl) {
   constexpr int NM = D + 2;
   constexpr int NA = HOFKS ? 2 * NM : NM;
   constexpr int NT = HOFKS ? 2 : 1;
-  constexpr int S = 4;
+  constexpr int S = kWinS;
   __shared__ int s_ox[kMaxV1], s_oy[kMaxV1], s_oz[kMaxV1];
   // dynamic: FP64 sums per (moment, target) and lane, shared by the S warps,
   // then each thread's FP32 sums of the current kz plane
   extern __shared__ double s_dyn[];
   double (*s_acc)[32] = reinterpret_cast<double (*)[32]>(s_dyn);
-  float (*s_mid)[128] = reinterpret_cast<float (*)[128]>(s_dyn + NA * Y * 32);
+  float (*s_mid)[kWinT] = reinterpret_cast<float (*)[kWinT]>(s_dyn + NA * Y * 32);
   const int tid = threadIdx.x;
   const long long n1 = *p.step + 1;
   const int Nx = g.nx[0], Ny = g.nx[1], Nz = g.nx[2];
   const int nvx = g.nv[0], nvy = g.nv[1], nvz = g.nv[2];
-  for (int t = tid; t < kMaxV1; t += 128) {
+  for (int t = tid; t < kMaxV1; t += kWinT) {
     if (t < nvx) s_ox[t] = wrap((long long)(g.kmin[0] + t) * n1, Nx);
     if (t < nvy) s_oy[t] = wrap((long long)(g.kmin[1] + t) * n1, Ny);
     if (D == 3 && t < nvz) s_oz[t] = wrap((long long)(g.kmin[2] + t) * n1, Nz);
   }
   for (int i = 0; i < NA * Y; ++i) s_mid[i][tid] = 0.f;
-  for (int i = tid; i < NA * Y * 32; i += 128) s_acc[i / 32][i % 32] = 0.0;
+  for (int i = tid; i < NA * Y * 32; i += kWinT) s_acc[i / 32][i % 32] = 0.0;
   __syncthreads();
 
   const int lane = tid & 31, ws = tid >> 5;
@@ -353,7 +359,7 @@ __global__ void __launch_bounds__(128, DVM_WIN_MINB) k_kpass_window(Geom g, DevP
   // through shared memory by cp.async, one block ahead of the arithmetic
   // (more loads in flight than registers allow; no register holds them)
   static_assert(!ASYNC || sizeof(TS) == 4, "cp.async staging is for FP32 storage");
-  float* s_fb = reinterpret_cast<float*>(s_mid + NA * Y);  // [2][Y][Y][128]
+  float* s_fb = reinterpret_cast<float*>(s_mid + NA * Y);  // [2][Y][Y][kWinT]
   int stage = 0;
   auto issue = [&](int base_i, int kb_i, int st) {
     const int pr_i = base_i + ws;
@@ -376,7 +382,7 @@ __global__ void __launch_bounds__(128, DVM_WIN_MINB) k_kpass_window(Geom g, DevP
       const float* Fk = Fb_i + (long long)ky * kystep;
 #pragma unroll
       for (int j = 0; j < Y; ++j) {
-        cp_async4(s_fb + ((st * Y + jj) * Y + j) * 128 + tid, Fk + r * Nx, tact[j]);
+        cp_async4(s_fb + ((st * Y + jj) * Y + j) * kWinT + tid, Fk + r * Nx, tact[j]);
         if (++r == Ny) r = 0;
       }
     }
@@ -423,7 +429,9 @@ __global__ void __launch_bounds__(128, DVM_WIN_MINB) k_kpass_window(Geom g, DevP
       float fv[Y][Y];
       if constexpr (ASYNC) {
         // this block's values landed in shared memory (prefetched one block
-        // ahead); queue the next block (or the next pair's first) meanwhile
+        // ahead); queue the next block (or the next pair's first) meanwhile;
+        // its stage was last read one block ago (an empty group past the end
+        // keeps the group count uniform)
         if (kb - Y >= 0) issue(base, kb - Y, stage ^ 1);
         else if (base + S < pe) issue(base + S, nvy - 1, stage ^ 1);
         cp_async_commit();
@@ -431,7 +439,7 @@ __global__ void __launch_bounds__(128, DVM_WIN_MINB) k_kpass_window(Geom g, DevP
 #pragma unroll
         for (int jj = 0; jj < Y; ++jj)
 #pragma unroll
-          for (int j = 0; j < Y; ++j) fv[jj][j] = s_fb[((stage * Y + jj) * Y + j) * 128 + tid];
+          for (int j = 0; j < Y; ++j) fv[jj][j] = s_fb[((stage * Y + jj) * Y + j) * kWinT + tid];
         stage ^= 1;
       } else {
         // the F loads of Y steps first: Y*Y independent loads in flight
@@ -523,7 +531,7 @@ __global__ void __launch_bounds__(128, DVM_WIN_MINB) k_kpass_window(Geom g, DevP
     // into the shared FP64 accumulators
     if ((base + S) % nvx == 0 || base + S >= pe) {
       __syncthreads();
-      for (int i = tid; i < NA * Y * 32; i += 128) {
+      for (int i = tid; i < NA * Y * 32; i += kWinT) {
         const int e = i / 32, l = i % 32;
         // the S warps' plane sums in FP32, then one FP64 add (GB300's FP64
         // rate is 1/64 of FP32: one conversion and one add per element)
@@ -540,7 +548,7 @@ __global__ void __launch_bounds__(128, DVM_WIN_MINB) k_kpass_window(Geom g, DevP
   if (ASYNC) cp_async_wait<0>();
   // this split's partial sums
   __syncthreads();
-  for (int i = tid; i < NA * Y * 32; i += 128) {
+  for (int i = tid; i < NA * Y * 32; i += kWinT) {
     const int e = i / 32, l = i % 32;
     const int a = e / Y, j = e % Y;
     const int xx = blockIdx.x * 32 + l;
@@ -558,7 +566,7 @@ bool window_eligible(const Geom& g) {
     if (g.bc[i] != DVM_BC_PERIODIC) return false;
   // 32-bit cell indices; rows wrap with one subtraction; the four warps of a
   // CTA end every kz plane in the same round
-  return g.nv[1] % kWinY == 0 && g.nv[0] % 4 == 0 && g.nx[1] >= kWinY && g.nc < (1LL << 31);
+  return g.nv[1] % kWinY == 0 && g.nv[0] % kWinS == 0 && g.nx[1] >= kWinY && g.nc < (1LL << 31);
 }
 
 // Velocity splits across CTAs: the smallest divisor (of the kz planes in 3D,
@@ -566,7 +574,7 @@ bool window_eligible(const Geom& g) {
 WinLaunch window_shape(const Geom& g) {
   const long long tiles = ((g.nx[0] + 31) / 32) * ((g.nx[1] + kWinY - 1) / kWinY) * g.nx[2];
   const long long target_ctas = 152LL * 3 * 2;
-  const int units = g.d == 3 ? g.nv[2] : g.nv[0] / 4;
+  const int units = g.d == 3 ? g.nv[2] : g.nv[0] / kWinS;
   int sp = 1;
   for (int c = 1; c <= 8 && c <= units; ++c) {
     if (units % c) continue;
@@ -574,23 +582,23 @@ WinLaunch window_shape(const Geom& g) {
     if (tiles * c >= target_ctas) break;
   }
   WinLaunch wl;
-  wl.S = 4;
+  wl.S = kWinS;
   wl.splits = sp;
   return wl;
 }
 
 constexpr size_t window_smem(int d, bool hofks, bool async) {
-  return (size_t)(hofks ? 2 : 1) * (d + 2) * kWinY * (32 * sizeof(double) + 128 * sizeof(float)) +
-         (async ? (size_t)2 * kWinY * kWinY * 128 * sizeof(float) : 0);
+  return (size_t)(hofks ? 2 : 1) * (d + 2) * kWinY * (32 * sizeof(double) + kWinT * sizeof(float)) +
+         (async ? (size_t)2 * kWinY * kWinY * kWinT * sizeof(float) : 0);
 }
 
-// FP32 staging of the F loads through shared memory: on by default in 2D,
-// where it measures faster; in 3D the extra shared memory costs the L1
-// capacity the parameter loads rely on (DVM_WIN_ASYNC=0/1 overrides).
+// FP32 staging of the F loads through shared memory: on by default (with 8
+// warps per CTA it measures faster in 2D and 3D; DVM_WIN_ASYNC=0/1 overrides).
 bool window_async(int d) {
   const char* e = getenv("DVM_WIN_ASYNC");
   if (e && (e[0] == '0' || e[0] == '1')) return e[0] == '1';
-  return d == 2;
+  (void)d;
+  return true;
 }
 
 template <typename TS, int D, bool HO, bool AS>
@@ -605,8 +613,8 @@ void launch_window_a(const Geom& g, const DevPtrs& p, const WinLaunch& wl, cudaS
   }
   dim3 grid((unsigned)((g.nx[0] + 31) / 32), (unsigned)((g.nx[1] + kWinY - 1) / kWinY),
             (unsigned)(g.nx[2] * wl.splits));
-  if (g.learn) k_kpass_window<TS, D, kWinY, HO, AS, true><<<grid, 128, sm, s>>>(g, p, wl);
-  else k_kpass_window<TS, D, kWinY, HO, AS, false><<<grid, 128, sm, s>>>(g, p, wl);
+  if (g.learn) k_kpass_window<TS, D, kWinY, HO, AS, true><<<grid, kWinT, sm, s>>>(g, p, wl);
+  else k_kpass_window<TS, D, kWinY, HO, AS, false><<<grid, kWinT, sm, s>>>(g, p, wl);
 }
 
 template <typename TS, int D, bool HO>

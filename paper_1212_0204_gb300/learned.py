@@ -88,7 +88,7 @@ def train_for_shear_layer(n: int = 128, nv: int = 32, nsnap: int = 200, warmup: 
     return train(X, y, precision=precision, epochs=epochs, seed=seed)
 
 
-def enable(solver, net: TrainedNet, thr: float, mlp_precision=dvm.F32, check_every: int = 10,
+def enable(solver, net: TrainedNet, thr: float, mlp_precision=dvm.BF16S, check_every: int = 10,
            check_samples: int = 1024, veto_radius: int = 2, seed: int = W.SEED_BASE):
     """Switch the learned path of ``solver`` on with the trained network."""
     solver.learn_enable(dvm.LEARN_MLP, mlp_precision=mlp_precision, thr=thr,

@@ -38,7 +38,7 @@ def small_cases():
     """Reduced-size versions of the workloads: several tiles and ragged tails."""
     sod = W.sod_1d(nx=203, nv=32, tau=1e-4)
     sod2 = W.sod_1d(nx=150, nv=32, tau=1e-2, p=3)
-    quad = W.quadrant_2d(n=37, nv=12, tau=1e-3, steps=4, dv=0.9)
+    quad = W.quadrant_2d(n=37, nv=16, tau=1e-3, steps=4, dv=0.7)
     wave = W.density_wave_3d(n=9, nv=8, tau=1e-4, steps=3, dv=1.2)
     shear = W.shear_layer_2d(n=33, nv=10, steps=3, dv=1.0)
     return {"sod_1d": (sod, 6), "sod_1d_p3": (sod2, 7), "quadrant_2d": (quad, 4),
