@@ -467,7 +467,7 @@ def main():
     if not args.no_cpu_baseline:
         sample, what = oracle_sample(case, 4e6)
         pts = sum(c.points for c in sample)
-        v, secs = time_oracle(sample, steps=max(1, int(round(15.0 * 8e6 / pts))))
+        v, secs = time_oracle(sample, steps=max(1, int(round(15.0 * 2e7 / pts))))
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{what}, {secs:.1f} s of single-thread FP64 oracle"}
     line = {

@@ -558,7 +558,10 @@ __global__ void __launch_bounds__(kWinT, DVM_WIN_MINB) k_kpass_window(Geom g, De
   }
 }
 
-constexpr int kWinY = 4;
+#ifndef DVM_WIN_Y
+#define DVM_WIN_Y 4
+#endif
+constexpr int kWinY = DVM_WIN_Y;  // targets (consecutive y cells) per thread
 
 bool window_eligible(const Geom& g) {
   if (g.d < 2 || g.precision == DVM_F64 || g.p != 1) return false;
