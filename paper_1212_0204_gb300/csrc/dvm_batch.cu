@@ -1,12 +1,12 @@
 // dvm_batch.cu -- many independent 1D-1V cases advanced together.
 //
 // Cases differ in N_x, N_v, tau, p and boundary rule and share the scheme and
-// the storage precision.  One time step of the whole batch is three launches,
+// the storage precision.  One time step of the whole batch is four launches,
 // captured once into a CUDA graph:
-//   k_b_euler    one CTA per case: alpha and the Euler sub-step count of the
-//                case, W = (1 - lambda) U, all MUSCL sub-steps in shared
-//                memory (Section 4.3.2), U_E; the boundary pieces of outflow
-//                cases; reset of the work queue.
+//   k_b_prepare  the boundary pieces of outflow cases; reset of the work queue.
+//   k_b_euler    one CTA per case (largest first), on a forked stream beside
+//                the kinetic pass: alpha, W = (1 - lambda) U, all MUSCL
+//                sub-steps in shared memory (Section 4.3.2), U_E.
 //   k_b_kinetic  persistent: CTAs pull (case, cell tile) items from an atomic
 //                queue ordered by decreasing cost; each thread owns cells of the
 //                tile and sweeps all velocities of the case (the kinetic pass of
@@ -56,6 +56,7 @@ struct BPtrs {
   int* status;
   long long* step;
   unsigned* qcounter;
+  const int* order;   // cases by decreasing Euler cost (largest first)
   int scheme;
   int cpt;  // cells per kinetic thread
 };
@@ -161,26 +162,35 @@ __device__ inline int b_index(int t, int n, int bc) {
 
 // One CTA per case: alpha, m, MUSCL sub-steps in shared memory, U_E; outflow
 // boundary pieces; queue reset.
-template <typename TS, typename TW, bool LIMITED, bool EULER>
-__global__ void __launch_bounds__(kB) k_b_euler(BPtrs p) {
-  extern __shared__ unsigned char s_raw[];
-  __shared__ double s_red[kB / 32];
+// Start of a step, one CTA per case: the outflow cases' boundary pieces of
+// every velocity at time n (read by the kinetic pass for sources outside the
+// tube) and the reset of the kinetic work queue.
+template <typename TS>
+__global__ void k_b_prepare(BPtrs p) {
   const int ci = blockIdx.x, tid = threadIdx.x;
   const BCase& bc = p.cases[ci];
   const int nx = bc.nx;
-  const long long nc = p.ncells;
   if (ci == 0 && tid == 0) *p.qcounter = 0u;
-  // outflow: the boundary pieces of every velocity at time n
-  if (bc.bc == DVM_BC_OUTFLOW) {
-    const long long n = *p.step;
-    const TS* F = (const TS*)p.F + bc.f_off;
-    TS* G = (TS*)p.ghost + bc.ghost_off;
-    for (int k = tid; k < bc.nv; k += kB) {
-      const long long o = transport_offset(bc.kmin + k, n, bc.p);
-      G[2 * k] = F[(long long)k * nx + wrap(0 - o, nx)];
-      G[2 * k + 1] = F[(long long)k * nx + wrap((long long)(nx - 1) - o, nx)];
-    }
+  if (bc.bc != DVM_BC_OUTFLOW) return;
+  const long long n = *p.step;
+  const TS* F = (const TS*)p.F + bc.f_off;
+  TS* G = (TS*)p.ghost + bc.ghost_off;
+  for (int k = tid; k < bc.nv; k += blockDim.x) {
+    const long long o = transport_offset(bc.kmin + k, n, bc.p);
+    G[2 * k] = F[(long long)k * nx + wrap(0 - o, nx)];
+    G[2 * k + 1] = F[(long long)k * nx + wrap((long long)(nx - 1) - o, nx)];
   }
+}
+
+// All MUSCL sub-steps of one case (CTA blockIdx.x takes case order[blockIdx.x]).
+template <typename TS, typename TW, bool LIMITED, bool EULER, bool SPLIT>
+__global__ void __launch_bounds__(kB) k_b_euler(BPtrs p) {
+  extern __shared__ unsigned char s_raw[];
+  __shared__ double s_red[kB / 32];
+  const int ci = p.order[blockIdx.x], tid = threadIdx.x;
+  const BCase& bc = p.cases[ci];
+  const int nx = bc.nx;
+  const long long nc = p.ncells;
   if (!EULER) return;
   TW* W0 = reinterpret_cast<TW*>(s_raw);
   TW* W1 = W0 + 3 * nx;
@@ -250,6 +260,45 @@ __global__ void __launch_bounds__(kB) k_b_euler(BPtrs p) {
     const TW* src = (s & 1) ? W1 : W0;
     TW* dst = (s & 1) ? W0 : W1;
     amax = TW(0);
+    if (SPLIT) {
+      // split fluxes G+- = F +- alpha W once per cell, then the two faces of
+      // every cell from them (boundary cells by the case's rule)
+      TW* Gp = W1 + 3 * nx;
+      TW* Gm = Gp + 3 * nx;
+      for (int x = tid; x < nx; x += kB) {
+        TW U[3], F[3];
+        for (int i = 0; i < 3; ++i) U[i] = src[i * nx + x];
+        euler_flux<TW, 1>(U, 0, F);
+        for (int i = 0; i < 3; ++i) {
+          Gp[i * nx + x] = F[i] + alw * U[i];
+          Gm[i * nx + x] = F[i] - alw * U[i];
+        }
+      }
+      __syncthreads();
+      for (int x = tid; x < nx; x += kB) {
+        int xx[5];
+        for (int o = 0; o < 5; ++o) xx[o] = b_index(x + o - 2, nx, bc.bc);
+        TW Wn[3];
+        for (int i = 0; i < 3; ++i) {
+          const TW* gp = Gp + i * nx;
+          const TW* gm = Gm + i * nx;
+          TW psi[2];
+          for (int f = 0; f < 2; ++f) {
+            const int j = 1 + f;  // face between cells j and j + 1 of the stencil
+            const TW sp = slope<TW, LIMITED>(gp[xx[j]] - gp[xx[j - 1]], gp[xx[j + 1]] - gp[xx[j]]);
+            const TW sm = slope<TW, LIMITED>(gm[xx[j + 1]] - gm[xx[j]], gm[xx[j + 2]] - gm[xx[j + 1]]);
+            psi[f] = TW(0.5) * (gp[xx[j]] + gm[xx[j + 1]]) + TW(0.25) * (sp - sm);
+          }
+          Wn[i] = src[i * nx + x] - kk * (psi[1] - psi[0]);
+          dst[i * nx + x] = Wn[i];
+        }
+        if (!last) {
+          TW a[3];
+          state_alpha_of<1>(Wn, a);
+          amax = amax > a[0] ? amax : a[0];
+        }
+      }
+    } else {
     for (int x = tid; x < nx; x += kB) {
       TW Us[5][3], Fs[5][3], Wn[3];
       for (int o = 0; o < 5; ++o) {
@@ -278,6 +327,7 @@ __global__ void __launch_bounds__(kB) k_b_euler(BPtrs p) {
         state_alpha_of<1>(Wn, a);
         amax = amax > a[0] ? amax : a[0];
       }
+    }
     }
     __syncthreads();
     if (last) break;
@@ -451,6 +501,7 @@ struct dvm_batch {
   int blocks = 0;
   int max_nx = 0;
   size_t euler_smem = 0;
+  bool split_euler = false;
   BPtrs p{};
   std::vector<void*> allocs;
   cudaStream_t stream = nullptr, cap = nullptr;
@@ -461,6 +512,8 @@ struct dvm_batch {
   std::string err;
   bool state_set = false;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaStream_t side = nullptr;       // high-priority stream of the Euler kernel
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 namespace {
@@ -541,9 +594,14 @@ void launch_kinetic(dvm_batch* b, cudaStream_t s) {
 template <typename TS, typename TW>
 void launch_euler_t(dvm_batch* b, cudaStream_t s) {
   const size_t sm = b->euler_smem;
-  if (b->scheme == DVM_FKS) k_b_euler<TS, TW, true, false><<<b->ncases, kB, sm, s>>>(b->p);
-  else if (b->scheme == DVM_HOFKS) k_b_euler<TS, TW, true, true><<<b->ncases, kB, sm, s>>>(b->p);
-  else k_b_euler<TS, TW, false, true><<<b->ncases, kB, sm, s>>>(b->p);
+  if (b->scheme == DVM_FKS) k_b_euler<TS, TW, true, false, false><<<b->ncases, kB, sm, s>>>(b->p);
+  else if (b->split_euler) {
+    if (b->scheme == DVM_HOFKS) k_b_euler<TS, TW, true, true, true><<<b->ncases, kB, sm, s>>>(b->p);
+    else k_b_euler<TS, TW, false, true, true><<<b->ncases, kB, sm, s>>>(b->p);
+  } else {
+    if (b->scheme == DVM_HOFKS) k_b_euler<TS, TW, true, true, false><<<b->ncases, kB, sm, s>>>(b->p);
+    else k_b_euler<TS, TW, false, true, false><<<b->ncases, kB, sm, s>>>(b->p);
+  }
 }
 
 void launch_euler(dvm_batch* b, cudaStream_t s) {
@@ -555,9 +613,11 @@ void launch_euler(dvm_batch* b, cudaStream_t s) {
 template <typename TS, typename TW>
 void set_euler_attr_t(dvm_batch* b) {
   const int sm = (int)b->euler_smem;
-  cudaFuncSetAttribute(k_b_euler<TS, TW, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  cudaFuncSetAttribute(k_b_euler<TS, TW, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  cudaFuncSetAttribute(k_b_euler<TS, TW, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_b_euler<TS, TW, true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_b_euler<TS, TW, true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_b_euler<TS, TW, false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_b_euler<TS, TW, true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_b_euler<TS, TW, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
 void launch_finalize(dvm_batch* b, cudaStream_t s) {
@@ -567,11 +627,33 @@ void launch_finalize(dvm_batch* b, cudaStream_t s) {
   else { if (ho) k_b_finalize<float, true><<<nb, kB, 0, s>>>(b->p); else k_b_finalize<float, false><<<nb, kB, 0, s>>>(b->p); }
 }
 
+void launch_prepare(dvm_batch* b, cudaStream_t s) {
+  if (b->precision == DVM_F64) k_b_prepare<double><<<b->ncases, 128, 0, s>>>(b->p);
+  else if (b->precision == DVM_F32) k_b_prepare<float><<<b->ncases, 128, 0, s>>>(b->p);
+  else k_b_prepare<__nv_bfloat16><<<b->ncases, 128, 0, s>>>(b->p);
+}
+
+// One batched step.  The Euler sub-steps read only W = (1 - lambda) U^n and
+// the kinetic pass only f and the parameters, so (except in timed steps) the
+// Euler kernel runs on a forked high-priority stream beside the kinetic pass.
 int enqueue(dvm_batch* b, cudaStream_t s, bool timed = false) {
-  launch_euler(b, s);
+  launch_prepare(b, s);
+  const bool euler = b->scheme != DVM_FKS;
+  const bool fork = euler && !timed;
+  if (euler) {
+    cudaStream_t es = s;
+    if (fork) {
+      cudaEventRecord(b->fork, s);
+      cudaStreamWaitEvent(b->side, b->fork, 0);
+      es = b->side;
+    }
+    launch_euler(b, es);
+    if (fork) cudaEventRecord(b->join, b->side);
+  }
   if (timed) cudaEventRecord(b->e0, s);
   launch_kinetic(b, s);
   if (timed) cudaEventRecord(b->e1, s);
+  if (fork) cudaStreamWaitEvent(s, b->join, 0);
   launch_finalize(b, s);
   return bcheck(b, cudaGetLastError(), "batch launch");
 }
@@ -683,7 +765,17 @@ int dvm_batch_create(const dvm_config* cfgs, int ncases, void* cuda_stream, dvm_
   rc |= balloc(b, &p.msub, sizeof(int) * ncases);
   rc |= balloc(b, &p.alpha, sizeof(double) * ncases);
   rc |= balloc(b, &p.status, 256);
+  int* dorder = nullptr;
+  rc |= balloc(b, &dorder, sizeof(int) * ncases);
   if (rc) { dvm_batch_destroy(b); return DVM_ERR_OOM; }
+  p.order = dorder;
+  // Euler work of a case ~ cells x sub-steps ~ N_x N_v (the sub-step count
+  // grows as the velocity spacing shrinks): largest first
+  std::vector<int> order(ncases);
+  for (int i = 0; i < ncases; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+    return (long long)b->cases[a].nx * b->cases[a].nv > (long long)b->cases[c].nx * b->cases[c].nv;
+  });
   p.step = (long long*)((char*)p.status + 64);
   p.qcounter = (unsigned*)((char*)p.status + 128);
   p.cases = dcases;
@@ -692,16 +784,31 @@ int dvm_batch_create(const dvm_config* cfgs, int ncases, void* cuda_stream, dvm_
   if (cudaMemcpy(dcases, b->cases.data(), sizeof(BCase) * ncases, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(dcc, cell_case.data(), sizeof(int) * cells, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(p.lam, lam.data(), 8 * cells, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dorder, order.data(), sizeof(int) * ncases, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(p.status, 0, 256) != cudaSuccess ||
       cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMallocHost((void**)&b->pinned, 64) != cudaSuccess ||
-      cudaEventCreate(&b->e0) != cudaSuccess || cudaEventCreate(&b->e1) != cudaSuccess) {
+      cudaEventCreate(&b->e0) != cudaSuccess || cudaEventCreate(&b->e1) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     dvm_batch_destroy(b);
     return DVM_ERR_CUDA;
   }
+  {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&b->side, cudaStreamNonBlocking, hi) != cudaSuccess) {
+      cudaGetLastError();
+      dvm_batch_destroy(b);
+      return DVM_ERR_CUDA;
+    }
+  }
   const size_t tw = b->precision == DVM_F64 ? 8 : 4;
-  b->euler_smem = 2 * 3 * (size_t)b->max_nx * tw;
+  // W0, W1 and, for the split-flux form, G+ and G- (3 rows each) per case;
+  // the split form only while that fits next to a second CTA per SM
+  b->split_euler = 4 * 3 * (size_t)b->max_nx * tw <= 110 * 1024;
+  b->euler_smem = (b->split_euler ? 4 : 2) * 3 * (size_t)b->max_nx * tw;
   if (b->precision == DVM_F64) set_euler_attr_t<double, double>(b);
   else if (b->precision == DVM_F32) set_euler_attr_t<float, float>(b);
   else set_euler_attr_t<__nv_bfloat16, float>(b);
@@ -722,6 +829,9 @@ void dvm_batch_destroy(dvm_batch* b) {
   if (b->pinned) cudaFreeHost(b->pinned);
   if (b->e0) cudaEventDestroy(b->e0);
   if (b->e1) cudaEventDestroy(b->e1);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
+  if (b->side) cudaStreamDestroy(b->side);
   delete b;
 }
 
@@ -856,8 +966,8 @@ int dvm_batch_autotune(dvm_batch* b, int* threads, int* cells_per_thread, double
   if (rc) return rc;
   cudaStream_t s = b->stream;
   cudaMemcpyAsync(save, b->p.F, fb, cudaMemcpyDeviceToDevice, s);
-  // the Euler launch prepares the ghost pieces and the queue of this step
-  launch_euler(b, s);
+  // the ghost pieces of this step (the queue is reset before every timing)
+  launch_prepare(b, s);
   const int cand_t[3] = {64, 128, 256}, cand_c[2] = {1, 2};
   double best = 1e30;
   int bt = b->threads, bcpt = b->cpt;
