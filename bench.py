@@ -283,6 +283,23 @@ class Job:
         return ms / n
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest value of x over all ranks (a replica's time: the job ends with
+    the slowest replica); x itself without a process group."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(points: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job phase-space updates per second: every replica advances its own
+    problem of `points` updates per step (weak scaling)."""
+    return points * steps * world / seconds
+
+
 def run_learned(args, case, descr, rank, local):
     """The learned regime path against the plain scheme on the 2D shear layer:
     updates/s of FP32 + learned, plain FP32 and plain FP64 over the same steps, and
@@ -427,12 +444,8 @@ def main():
         stop.synchronize()
         barrier()
     job.obj.sync_status()
-    ms = start.elapsed_time(stop)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = job.points * args.steps * world / (ms * 1e-3)
+    ms = max_over_ranks(start.elapsed_time(stop), dist, "cuda")
+    value = job_rate(job.points, args.steps, world, ms * 1e-3)
 
     # ---- kinetic-pass roofline: the same steps, kinetic pass bracketed by events
     kin_ms = job.kinetic_ms(args.steps)
@@ -449,13 +462,9 @@ def main():
     job.obj.step(args.steps)
     job.obj.moments(out)            # D2H of the final moments
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     mom_bytes = 8 * job.rows * job.cells
-    e2e = {"value": job.points * args.steps * world / e2e_s, "unit": UNIT,
+    e2e = {"value": job_rate(job.points, args.steps, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": mom_bytes / args.steps, "d2h_bytes_per_step": mom_bytes / args.steps,
            "note": "initial moments uploaded and final moments read back once per K-step job"}
 
