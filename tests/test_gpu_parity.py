@@ -201,3 +201,30 @@ def test_primitive_and_moment_initialisation_agree():
     b.set_moments(conserved(case))
     assert moment_err(a.moments(), b.moments()) <= 1e-15
     assert np.abs(a.f() - b.f()).max() <= 1e-14 * np.abs(b.f()).max()
+
+
+@pytest.mark.parametrize("case", [
+    W.sod_1d(nx=64, nv=32, tau=0.0),
+    W.quadrant_2d(n=20, nv=16, tau=0.0, steps=3, dv=0.7),
+], ids=["sod_tau0", "quadrant_tau0"])
+def test_tau_zero_matches_oracle(case):
+    """lambda = 0 exactly (the fluid limit: HOFKS reduces to the Euler scheme)."""
+    orc = oracle.Scheme(grid(case), tau=case.tau)
+    orc.set_moments(conserved(case))
+    orc.step(3)
+    g = gpu_run(case, 3, dvm.F64)
+    assert moment_err(g.moments(), orc.moments()) <= 1e-12
+
+
+@pytest.mark.parametrize("case,precision,tol", [
+    (W.sod_1d(nx=3, nv=8, tau=1e-3, dv=1.0), dvm.F64, 1e-12),          # three cells
+    (W.quadrant_2d(n=5, nv=8, tau=1e-3, steps=2, dv=1.0), dvm.F64, 1e-12),  # 5 x 5, one tile
+    (W.sod_1d(nx=40, nv=256, tau=1e-3, dv=0.05), dvm.F64, 1e-12),     # 256 velocities (maximum)
+    (W.quadrant_2d(n=33, nv=16, tau=1e-3, steps=2, dv=0.7), dvm.F32, 1e-5),  # ragged x and y tails
+], ids=["three_cells", "five_by_five", "max_velocities", "ragged_window"])
+def test_edge_sizes_match_oracle(case, precision, tol):
+    orc = oracle.Scheme(grid(case), tau=case.tau)
+    orc.set_moments(conserved(case))
+    orc.step(2)
+    g = gpu_run(case, 2, precision)
+    assert moment_err(g.moments(), orc.moments()) <= tol
