@@ -62,6 +62,12 @@ struct BPtrs {
 };
 
 constexpr int kB = 256;
+// threads of a batched Euler CTA (one tube): the tube's cells per thread, and
+// so the sub-step latency of the largest tubes, fall as it grows
+#ifndef DVM_BATCH_EULER_THREADS
+#define DVM_BATCH_EULER_THREADS 512
+#endif
+constexpr int kBE = DVM_BATCH_EULER_THREADS;
 constexpr int kMaxBatchNx = 4096;
 
 // mu of Eq. minimMax for one cell of a 1D case (separable sums: one axis).
@@ -184,9 +190,9 @@ __global__ void k_b_prepare(BPtrs p) {
 
 // All MUSCL sub-steps of one case (CTA blockIdx.x takes case order[blockIdx.x]).
 template <typename TS, typename TW, bool LIMITED, bool EULER, bool SPLIT>
-__global__ void __launch_bounds__(kB) k_b_euler(BPtrs p) {
+__global__ void __launch_bounds__(kBE) k_b_euler(BPtrs p) {
   extern __shared__ unsigned char s_raw[];
-  __shared__ double s_red[kB / 32];
+  __shared__ double s_red[kBE / 32];
   const int ci = p.order[blockIdx.x], tid = threadIdx.x;
   const BCase& bc = p.cases[ci];
   const int nx = bc.nx;
@@ -198,12 +204,12 @@ __global__ void __launch_bounds__(kB) k_b_euler(BPtrs p) {
   // Time2 per sub-step, the last one ending at dt).  alpha is reduced in the
   // state's type; the sub-step scalars are computed once per CTA by thread 0
   // (FP64 in the FP64 build, the quotient in FP32 otherwise) and broadcast.
-  __shared__ TW s_redw[kB / 32];
+  __shared__ TW s_redw[kBE / 32];
   __shared__ double s_dtE;
   __shared__ TW s_kk, s_alw;
   __shared__ int s_flags;  // bit 0: last sub-step, bit 1: stop (error or all free)
   TW amax = TW(0);
-  for (int x = tid; x < nx; x += kB) {
+  for (int x = tid; x < nx; x += kBE) {
     const long long c = bc.c_off + x;
     const double w = bc.all_free ? 0.0 : 1.0 - p.lam[c];
     TW W[3];
@@ -226,7 +232,7 @@ __global__ void __launch_bounds__(kB) k_b_euler(BPtrs p) {
     __syncthreads();
     if (tid == 0) {
       TW alt = TW(0);
-      for (int w = 0; w < kB / 32; ++w) alt = alt > s_redw[w] ? alt : s_redw[w];
+      for (int w = 0; w < kBE / 32; ++w) alt = alt > s_redw[w] ? alt : s_redw[w];
       const double al = (double)alt;
       if (s == 0) a0 = al;
       int flags = 0;
@@ -265,7 +271,7 @@ __global__ void __launch_bounds__(kB) k_b_euler(BPtrs p) {
       // every cell from them (boundary cells by the case's rule)
       TW* Gp = W1 + 3 * nx;
       TW* Gm = Gp + 3 * nx;
-      for (int x = tid; x < nx; x += kB) {
+      for (int x = tid; x < nx; x += kBE) {
         TW U[3], F[3];
         for (int i = 0; i < 3; ++i) U[i] = src[i * nx + x];
         euler_flux<TW, 1>(U, 0, F);
@@ -275,7 +281,7 @@ __global__ void __launch_bounds__(kB) k_b_euler(BPtrs p) {
         }
       }
       __syncthreads();
-      for (int x = tid; x < nx; x += kB) {
+      for (int x = tid; x < nx; x += kBE) {
         int xx[5];
         for (int o = 0; o < 5; ++o) xx[o] = b_index(x + o - 2, nx, bc.bc);
         TW Wn[3];
@@ -299,7 +305,7 @@ __global__ void __launch_bounds__(kB) k_b_euler(BPtrs p) {
         }
       }
     } else {
-    for (int x = tid; x < nx; x += kB) {
+    for (int x = tid; x < nx; x += kBE) {
       TW Us[5][3], Fs[5][3], Wn[3];
       for (int o = 0; o < 5; ++o) {
         const int xx = b_index(x + o - 2, nx, bc.bc);
@@ -342,7 +348,7 @@ __global__ void __launch_bounds__(kB) k_b_euler(BPtrs p) {
     p.alpha[ci] = a0;
   }
   const TW* res = (m & 1) ? W1 : W0;
-  for (int x = tid; x < nx; x += kB)
+  for (int x = tid; x < nx; x += kBE)
     for (int i = 0; i < 3; ++i) p.UE[i * nc + bc.c_off + x] = (double)res[i * nx + x];
 }
 
@@ -352,6 +358,7 @@ __global__ void k_b_kinetic(BPtrs p) {
   __shared__ int s_item;
   __shared__ BCase s_case;
   __shared__ int s_slot[kMaxV1], s_delta[kMaxV1];
+  __shared__ TC s_v[kMaxV1];
   const long long n = *p.step;
   const long long nc = p.ncells;
   const TC* prm = (const TC*)p.prm;
@@ -370,6 +377,7 @@ __global__ void k_b_kinetic(BPtrs p) {
       const long long o1 = transport_offset(kg, n + 1, bc.p);
       s_slot[k] = wrap(o1, bc.nx);
       s_delta[k] = (int)(o1 - transport_offset(kg, n, bc.p));
+      s_v[k] = (TC)((double)kg * bc.dv);
     }
     __syncthreads();
     const TS* G = (const TS*)p.ghost + bc.ghost_off;
@@ -395,18 +403,43 @@ __global__ void k_b_kinetic(BPtrs p) {
         const TC fv = clamped ? StoreT<TS>::load(G + 2 * k + (s == 0 ? 0 : 1))
                               : StoreT<TS>::load(F + (long long)k * bc.nx + q);
         const long long cs = bc.c_off + s;
-        const TC v = (TC)((double)(bc.kmin + k) * bc.dv);
+        const TC v = s_v[k];
         const TC v2 = v * v;
-        const TC du = v - prm[prm_at(row_u(0), cs, nc)];
-        const TC ex = prm[prm_at(row_L(), cs, nc)] - prm[prm_at(row_h(1), cs, nc)] * du * du;
-        const TC M = sizeof(TC) == 8 ? (TC)exp2((double)ex) : (TC)exp2f((float)ex);
-        const TC lm = prm[prm_at(row_mu(1, 0), cs, nc)] + prm[prm_at(row_mu(1, 1), cs, nc)] * v +
-                      prm[prm_at(row_mu(1, 2), cs, nc)] * v2;
+        // source parameters (d = 1 rows: lambda L u h | nu0 nu1 nu2 mu0 | mu1 mu2)
+        TC plam, pL, pu, ph, n0, n1, n2, m0, m1, m2;
+        if constexpr (sizeof(TC) == 4) {
+          const float4* pg = reinterpret_cast<const float4*>(prm);
+          const float4 g0 = __ldg(pg + cs), g1 = __ldg(pg + nc + cs), g2 = __ldg(pg + 2 * nc + cs);
+          plam = g0.x; pL = g0.y; pu = g0.z; ph = g0.w;
+          n0 = g1.x; n1 = g1.y; n2 = g1.z; m0 = g1.w;
+          m1 = g2.x; m2 = g2.y;
+        } else {
+          plam = prm[prm_at(row_lam(), cs, nc)];
+          pL = prm[prm_at(row_L(), cs, nc)];
+          pu = prm[prm_at(row_u(0), cs, nc)];
+          ph = prm[prm_at(row_h(1), cs, nc)];
+          n0 = prm[prm_at(row_nu(1, 0), cs, nc)];
+          n1 = prm[prm_at(row_nu(1, 1), cs, nc)];
+          n2 = prm[prm_at(row_nu(1, 2), cs, nc)];
+          m0 = prm[prm_at(row_mu(1, 0), cs, nc)];
+          m1 = prm[prm_at(row_mu(1, 1), cs, nc)];
+          m2 = prm[prm_at(row_mu(1, 2), cs, nc)];
+        }
+        const TC du = v - pu;
+        const TC ex = pL - ph * du * du;
+        TC M;
+        if constexpr (sizeof(TC) == 8) {
+          M = (TC)exp2((double)ex);
+        } else {
+          float y;
+          asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"((float)ex));
+          M = y;
+        }
+        const TC lm = m0 + m1 * v + m2 * v2;
         TC fnew;
         if (HOFKS) {
-          const TC ln = prm[prm_at(row_nu(1, 0), cs, nc)] + prm[prm_at(row_nu(1, 1), cs, nc)] * v +
-                        prm[prm_at(row_nu(1, 2), cs, nc)] * v2;
-          const TC a = prm[prm_at(row_lam(), cs, nc)] * (fv + ln);  // T(lambda f^n)
+          const TC ln = n0 + n1 * v + n2 * v2;
+          const TC a = plam * (fv + ln);  // T(lambda f^n)
           const TC b = M + lm;                                        // T((1 - lambda) E^n)
           fnew = a + b;
           r[0] += a; r[1] += a * v; r[2] += a * v2;
@@ -594,13 +627,13 @@ void launch_kinetic(dvm_batch* b, cudaStream_t s) {
 template <typename TS, typename TW>
 void launch_euler_t(dvm_batch* b, cudaStream_t s) {
   const size_t sm = b->euler_smem;
-  if (b->scheme == DVM_FKS) k_b_euler<TS, TW, true, false, false><<<b->ncases, kB, sm, s>>>(b->p);
+  if (b->scheme == DVM_FKS) k_b_euler<TS, TW, true, false, false><<<b->ncases, kBE, sm, s>>>(b->p);
   else if (b->split_euler) {
-    if (b->scheme == DVM_HOFKS) k_b_euler<TS, TW, true, true, true><<<b->ncases, kB, sm, s>>>(b->p);
-    else k_b_euler<TS, TW, false, true, true><<<b->ncases, kB, sm, s>>>(b->p);
+    if (b->scheme == DVM_HOFKS) k_b_euler<TS, TW, true, true, true><<<b->ncases, kBE, sm, s>>>(b->p);
+    else k_b_euler<TS, TW, false, true, true><<<b->ncases, kBE, sm, s>>>(b->p);
   } else {
-    if (b->scheme == DVM_HOFKS) k_b_euler<TS, TW, true, true, false><<<b->ncases, kB, sm, s>>>(b->p);
-    else k_b_euler<TS, TW, false, true, false><<<b->ncases, kB, sm, s>>>(b->p);
+    if (b->scheme == DVM_HOFKS) k_b_euler<TS, TW, true, true, false><<<b->ncases, kBE, sm, s>>>(b->p);
+    else k_b_euler<TS, TW, false, true, false><<<b->ncases, kBE, sm, s>>>(b->p);
   }
 }
 
