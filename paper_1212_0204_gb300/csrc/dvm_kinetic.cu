@@ -10,6 +10,8 @@
 #include <math.h>
 #include <stdlib.h>
 
+#include <type_traits>
+
 #include "dvm_internal.cuh"
 
 namespace dvm {
@@ -187,15 +189,26 @@ __device__ __forceinline__ float ex2_ftz(float x) {
   return y;
 }
 
-// Parameters of source cell src (grouped layout, four rows per float4),
-// folded with the fixed velocity components vx (and vz).
+// Parameters of source cell src (grouped layout, four rows per float4):
+// loaded one step before they are folded, so that the loads are in flight
+// while the current step computes.
+struct RawSlot {
+  float4 g0, g1, g2, g3;
+};
+
+__device__ __forceinline__ RawSlot load_raw(const float4* __restrict__ pg, long long nc4, int src) {
+  RawSlot r;
+  r.g0 = __ldg(pg + src);
+  r.g1 = __ldg(pg + nc4 + src);
+  r.g2 = __ldg(pg + 2 * nc4 + src);
+  r.g3 = __ldg(pg + 3 * nc4 + src);
+  return r;
+}
+
+// The raw parameters folded with the fixed velocity components vx (and vz).
 template <int D>
-__device__ __forceinline__ Slot load_slot(const float4* __restrict__ pg, long long nc4, int src,
-                                          float vx, float vz, float vxz2) {
-  const float4 g0 = __ldg(pg + src);
-  const float4 g1 = __ldg(pg + nc4 + src);
-  const float4 g2 = __ldg(pg + 2 * nc4 + src);
-  const float4 g3 = __ldg(pg + 3 * nc4 + src);
+__device__ __forceinline__ Slot fold_slot(const RawSlot& r, float vx, float vz, float vxz2) {
+  const float4 g0 = r.g0, g1 = r.g1, g2 = r.g2, g3 = r.g3;
   float ux, uy, uz = 0.f, L, h, nu0, nux, nuy, nuz = 0.f, nu4, mu0, mux, muy, muz = 0.f, mu4;
   const float lam = g0.x;
   L = g0.y; ux = g0.z; uy = g0.w;
@@ -233,6 +246,12 @@ __device__ __forceinline__ Slot load_slot(const float4* __restrict__ pg, long lo
   return s;
 }
 
+template <int D>
+__device__ __forceinline__ Slot load_slot(const float4* __restrict__ pg, long long nc4, int src,
+                                          float vx, float vz, float vxz2) {
+  return fold_slot<D>(load_raw(pg, nc4, src), vx, vz, vxz2);
+}
+
 // 4-byte asynchronous global -> shared copy (zero fill when !pred: no bytes
 // are read, the address is still a valid one), commit and wait.
 __device__ __forceinline__ void cp_async4(float* smem, const float* gmem, bool pred) {
@@ -265,28 +284,32 @@ struct WinLaunch {
   int splits;  // velocity chunks across CTAs (partial-sum slices)
 };
 
-// Warps per CTA of the windowed pass (each on every S-th velocity pair; their
-// parameter loads share L1 lines) and resident CTAs per SM it is compiled for
-// (register cap 65536 / (32 * DVM_WIN_S * DVM_WIN_MINB)).
-#ifndef DVM_WIN_S
-#define DVM_WIN_S 8
-#endif
-constexpr int kWinS = DVM_WIN_S;
-constexpr int kWinT = 32 * kWinS;
-#ifndef DVM_WIN_MINB
-#define DVM_WIN_MINB 2
-#endif
+// Shape of the windowed pass per dimension, measured on GB300: warps per CTA
+// (each on every S-th velocity pair; their parameter loads share L1 lines),
+// resident CTAs per SM it is compiled for (register cap 65536 / (32 S MINB)),
+// and how many of the four parameter groups of the next source row are loaded
+// a step ahead of their fold (the others at fold time: more in flight costs
+// registers).
+template <int D> struct WinShape {
+  static constexpr int S = 8, MINB = 2, EARLY = 2;
+};
+template <> struct WinShape<3> {
+  static constexpr int S = 4, MINB = 3, EARLY = 1;
+};
+int win_warps(int d) { return d == 3 ? WinShape<3>::S : WinShape<2>::S; }
 
-// CTA = S = 4 warps on the same 32 x Y targets; warp s takes the velocity
-// pairs pb + s, pb + s + 4, ...: at any time the four warps read source rows
-// shifted by one column from each other, so their parameter loads share L1
-// lines.
+// CTA = S warps on the same 32 x Y targets; warp s takes the velocity pairs
+// pb + s, pb + s + S, ...: at any time the warps read source rows shifted by
+// one column from each other, so their parameter loads share L1 lines.
 template <typename TS, int D, int Y, bool HOFKS, bool ASYNC, bool LEARN>
-__global__ void __launch_bounds__(kWinT, DVM_WIN_MINB) k_kpass_window(Geom g, DevPtrs p, WinLaunch wl) {
+__global__ void __launch_bounds__(32 * WinShape<D>::S, WinShape<D>::MINB)
+    k_kpass_window(Geom g, DevPtrs p, WinLaunch wl) {
   constexpr int NM = D + 2;
   constexpr int NA = HOFKS ? 2 * NM : NM;
   constexpr int NT = HOFKS ? 2 : 1;
-  constexpr int S = kWinS;
+  constexpr int S = WinShape<D>::S;
+  constexpr int kWinT = 32 * S;
+  constexpr int EARLY = WinShape<D>::EARLY;
   __shared__ int s_ox[kMaxV1], s_oy[kMaxV1], s_oz[kMaxV1];
   // dynamic: FP64 sums per (moment, target) and lane, shared by the S warps,
   // then each thread's FP32 sums of the current kz plane
@@ -426,7 +449,7 @@ __global__ void __launch_bounds__(kWinT, DVM_WIN_MINB) k_kpass_window(Geom g, De
 #pragma unroll
       for (int j = 0; j < Y; ++j) in0[t][j] = in1[t][j] = in2[t][j] = 0.f;
     for (int kb = nvy - 1; kb >= 0; kb -= Y) {
-      float fv[Y][Y];
+      float fv[ASYNC ? 1 : Y][Y];
       if constexpr (ASYNC) {
         // this block's values landed in shared memory (prefetched one block
         // ahead); queue the next block (or the next pair's first) meanwhile;
@@ -436,11 +459,6 @@ __global__ void __launch_bounds__(kWinT, DVM_WIN_MINB) k_kpass_window(Geom g, De
         else if (base + S < pe) issue(base + S, nvy - 1, stage ^ 1);
         cp_async_commit();
         cp_async_wait<1>();
-#pragma unroll
-        for (int jj = 0; jj < Y; ++jj)
-#pragma unroll
-          for (int j = 0; j < Y; ++j) fv[jj][j] = s_fb[((stage * Y + jj) * Y + j) * kWinT + tid];
-        stage ^= 1;
       } else {
         // the F loads of Y steps first: Y*Y independent loads in flight
 #pragma unroll
@@ -462,56 +480,85 @@ __global__ void __launch_bounds__(kWinT, DVM_WIN_MINB) k_kpass_window(Geom g, De
           }
         }
       }
+      // rows of the Y steps' targets; one CTA-uniform test per block picks
+      // the body without periodic wraps (a single basic block over the Y
+      // steps, so the parameter loads of one step overlap the next ones)
+      bool nowrap = true;
 #pragma unroll
       for (int jj = 0; jj < Y; ++jj) {
-        const int ky = kb - jj;
-        const float vy = (g.kmin[1] + ky) * dv;
-        const float vy2 = vy * vy;
-        float fn[Y];
-#pragma unroll
-        for (int j = 0; j < Y; ++j) {
-          const Slot& sl = win[(jj + j) % Y];
-          const float M = ex2_ftz(fmaf(sl.c2, vy2, fmaf(sl.c1, vy, sl.c0)));
-          const float lm = fmaf(sl.b2, vy2, fmaf(sl.b1, vy, sl.b0));
-          if (HOFKS) {
-            const float a = fmaf(sl.lam, fv[jj][j], fmaf(sl.a2, vy2, fmaf(sl.a1, vy, sl.a0)));
-            const float b = M + lm;  // T((1 - lambda) E^n)
-            fn[j] = a + b;           // a = T(lambda f^n)
-            in0[0][j] += a;
-            in1[0][j] = fmaf(a, vy, in1[0][j]);
-            in2[0][j] = fmaf(a, vy2, in2[0][j]);
-            in0[NT - 1][j] += b;
-            in1[NT - 1][j] = fmaf(b, vy, in1[NT - 1][j]);
-            in2[NT - 1][j] = fmaf(b, vy2, in2[NT - 1][j]);
-          } else {
-            const float fs = fv[jj][j] + M + lm;  // transported f
-            fn[j] = lam_c[j] * fs;                // its lambda part; the rest is deferred
-            in0[0][j] += fs;
-            in1[0][j] = fmaf(fs, vy, in1[0][j]);
-            in2[0][j] = fmaf(fs, vy2, in2[0][j]);
-          }
-        }
-        TS* Fk = Fb + ky * kystep;
-        int r = y0 - s_oy[ky];
+        int r = y0 - s_oy[kb - jj];
         if (r < 0) r += Ny;
-        if (r + Y <= Ny) {
-          TS* Fr = Fk + r * Nx;
+        nowrap = nowrap && r + Y <= Ny;
+      }
+      auto steps = [&](auto fast) {
+#pragma unroll
+        for (int jj = 0; jj < Y; ++jj) {
+          const int ky = kb - jj;
+          // the source row that enters the window after this step: its loads
+          // are issued before this step's arithmetic (after the last step of
+          // a pair the row is loaded and folded but not used)
+          RawSlot raw;
+          const int src_next = src_base + Nx * rnext;
+          raw.g0 = __ldg(pg + src_next);
+          if (EARLY > 1) raw.g1 = __ldg(pg + nc + src_next);
+          if (EARLY > 2) raw.g2 = __ldg(pg + 2 * nc + src_next);
+          if (EARLY > 3) raw.g3 = __ldg(pg + 3 * nc + src_next);
+          float fj[Y];
 #pragma unroll
           for (int j = 0; j < Y; ++j)
-            if (sact[j]) StreamT<TS>::store(Fr + j * Nx, fn[j]);
-        } else {
+            fj[j] = ASYNC ? s_fb[((stage * Y + jj) * Y + j) * kWinT + tid] : fv[ASYNC ? 0 : jj][j];
+          const float vy = (g.kmin[1] + ky) * dv;
+          const float vy2 = vy * vy;
+          float fn[Y];
 #pragma unroll
           for (int j = 0; j < Y; ++j) {
-            if (sact[j]) StreamT<TS>::store(Fk + r * Nx, fn[j]);
-            if (++r == Ny) r = 0;
+            const Slot& sl = win[(jj + j) % Y];
+            const float M = ex2_ftz(fmaf(sl.c2, vy2, fmaf(sl.c1, vy, sl.c0)));
+            const float lm = fmaf(sl.b2, vy2, fmaf(sl.b1, vy, sl.b0));
+            if (HOFKS) {
+              const float a = fmaf(sl.lam, fj[j], fmaf(sl.a2, vy2, fmaf(sl.a1, vy, sl.a0)));
+              const float b = M + lm;  // T((1 - lambda) E^n)
+              fn[j] = a + b;           // a = T(lambda f^n)
+              in0[0][j] += a;
+              in1[0][j] = fmaf(a, vy, in1[0][j]);
+              in2[0][j] = fmaf(a, vy2, in2[0][j]);
+              in0[NT - 1][j] += b;
+              in1[NT - 1][j] = fmaf(b, vy, in1[NT - 1][j]);
+              in2[NT - 1][j] = fmaf(b, vy2, in2[NT - 1][j]);
+            } else {
+              const float fs = fj[j] + M + lm;  // transported f
+              fn[j] = lam_c[j] * fs;            // its lambda part; the rest is deferred
+              in0[0][j] += fs;
+              in1[0][j] = fmaf(fs, vy, in1[0][j]);
+              in2[0][j] = fmaf(fs, vy2, in2[0][j]);
+            }
           }
-        }
-        // slide: the slot just left by target 0 takes the next source row
-        if (ky > 0) {
-          win[jj % Y] = load_slot<D>(pg, nc, src_base + Nx * rnext, vx, vz, vxz2);
+          TS* Fk = Fb + ky * kystep;
+          int r = y0 - s_oy[ky];
+          if (r < 0) r += Ny;
+          if constexpr (decltype(fast)::value) {
+            TS* Fr = Fk + r * Nx;
+#pragma unroll
+            for (int j = 0; j < Y; ++j)
+              if (sact[j]) StreamT<TS>::store(Fr + j * Nx, fn[j]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < Y; ++j) {
+              if (sact[j]) StreamT<TS>::store(Fk + r * Nx, fn[j]);
+              if (++r == Ny) r = 0;
+            }
+          }
+          // slide: the slot just left by target 0 takes the next source row
+          if (EARLY <= 1) raw.g1 = __ldg(pg + nc + src_next);
+          if (EARLY <= 2) raw.g2 = __ldg(pg + 2 * nc + src_next);
+          if (EARLY <= 3) raw.g3 = __ldg(pg + 3 * nc + src_next);
+          win[jj % Y] = fold_slot<D>(raw, vx, vz, vxz2);
           if (++rnext == Ny) rnext = 0;
         }
-      }
+      };
+      if (nowrap) steps(std::true_type{});
+      else steps(std::false_type{});
+      if (ASYNC) stage ^= 1;
     }
     // fold the row sums into the plane sums: m = (1, vx, vy, [vz], |v|^2/2)
 #pragma unroll
@@ -567,17 +614,17 @@ bool window_eligible(const Geom& g) {
   if (g.d < 2 || g.precision == DVM_F64 || g.p != 1) return false;
   for (int i = 0; i < g.d; ++i)
     if (g.bc[i] != DVM_BC_PERIODIC) return false;
-  // 32-bit cell indices; rows wrap with one subtraction; the four warps of a
+  // 32-bit cell indices; rows wrap with one subtraction; the S warps of a
   // CTA end every kz plane in the same round
-  return g.nv[1] % kWinY == 0 && g.nv[0] % kWinS == 0 && g.nx[1] >= kWinY && g.nc < (1LL << 31);
+  return g.nv[1] % kWinY == 0 && g.nv[0] % win_warps(g.d) == 0 && g.nx[1] >= kWinY && g.nc < (1LL << 31);
 }
 
 // Velocity splits across CTAs: the smallest divisor (of the kz planes in 3D,
-// of nvx / 4 in 2D) that gives two waves of three CTAs per SM, at most 8.
+// of nvx / S in 2D) that gives two waves of three CTAs per SM, at most 8.
 WinLaunch window_shape(const Geom& g) {
   const long long tiles = ((g.nx[0] + 31) / 32) * ((g.nx[1] + kWinY - 1) / kWinY) * g.nx[2];
   const long long target_ctas = 152LL * 3 * 2;
-  const int units = g.d == 3 ? g.nv[2] : g.nv[0] / kWinS;
+  const int units = g.d == 3 ? g.nv[2] : g.nv[0] / win_warps(g.d);
   int sp = 1;
   for (int c = 1; c <= 8 && c <= units; ++c) {
     if (units % c) continue;
@@ -585,14 +632,15 @@ WinLaunch window_shape(const Geom& g) {
     if (tiles * c >= target_ctas) break;
   }
   WinLaunch wl;
-  wl.S = kWinS;
+  wl.S = win_warps(g.d);
   wl.splits = sp;
   return wl;
 }
 
 constexpr size_t window_smem(int d, bool hofks, bool async) {
-  return (size_t)(hofks ? 2 : 1) * (d + 2) * kWinY * (32 * sizeof(double) + kWinT * sizeof(float)) +
-         (async ? (size_t)2 * kWinY * kWinY * kWinT * sizeof(float) : 0);
+  const size_t t = 32 * (d == 3 ? WinShape<3>::S : WinShape<2>::S);
+  return (size_t)(hofks ? 2 : 1) * (d + 2) * kWinY * (32 * sizeof(double) + t * sizeof(float)) +
+         (async ? (size_t)2 * kWinY * kWinY * t * sizeof(float) : 0);
 }
 
 // FP32 staging of the F loads through shared memory: on by default (with 8
@@ -616,8 +664,9 @@ void launch_window_a(const Geom& g, const DevPtrs& p, const WinLaunch& wl, cudaS
   }
   dim3 grid((unsigned)((g.nx[0] + 31) / 32), (unsigned)((g.nx[1] + kWinY - 1) / kWinY),
             (unsigned)(g.nx[2] * wl.splits));
-  if (g.learn) k_kpass_window<TS, D, kWinY, HO, AS, true><<<grid, kWinT, sm, s>>>(g, p, wl);
-  else k_kpass_window<TS, D, kWinY, HO, AS, false><<<grid, kWinT, sm, s>>>(g, p, wl);
+  constexpr int T = 32 * WinShape<D>::S;
+  if (g.learn) k_kpass_window<TS, D, kWinY, HO, AS, true><<<grid, T, sm, s>>>(g, p, wl);
+  else k_kpass_window<TS, D, kWinY, HO, AS, false><<<grid, T, sm, s>>>(g, p, wl);
 }
 
 template <typename TS, int D, bool HO>
