@@ -138,7 +138,7 @@ int make_geom(const dvm_config* cfg, Geom* g, std::string* msg) {
 namespace {
 
 struct Layout {
-  size_t F, ghost, U, lam, W0, W1, acc, prm, eqp, UE, UM, Us, A, small, offs, total;
+  size_t F, ghost, U, lam, W0, W1, acc, prm, wprm, eqp, UE, UM, Us, A, small, offs, total;
 };
 
 Layout layout(const Geom& g) {
@@ -156,6 +156,7 @@ Layout layout(const Geom& g) {
   L.W1 = take(8 * nm * nc);
   L.acc = take(8 * (size_t)g.nsplit * 2 * nm * nc);
   L.prm = take(tc * (size_t)prm_rows(g.d) * nc);
+  L.wprm = take(g.d >= 2 && g.precision != DVM_F64 ? 4 * 16 * nc : 0);
   L.eqp = take(8 * (size_t)prm_rows(g.d) * nc);
   L.UE = take(8 * nm * nc);
   L.UM = take(8 * nm * nc);
@@ -227,6 +228,7 @@ void bind(dvm_handle* h, char* base, const Layout& L) {
   p.W1 = base + L.W1;
   p.acc = (double*)(base + L.acc);
   p.prm = base + L.prm;
+  p.wprm = (float*)(base + L.wprm);
   p.eqp = (double*)(base + L.eqp);
   p.UE = (double*)(base + L.UE);
   p.UM = (double*)(base + L.UM);
@@ -297,11 +299,11 @@ int enqueue_step(dvm_handle* h, cudaStream_t s, cudaEvent_t e0 = nullptr,
     ++n;
   }
   if (e0) cudaEventRecord(e0, s);
-  launch_kinetic_pass(g, h->p, s);
+  n += launch_kinetic_pass(g, h->p, s);
   if (e1) cudaEventRecord(e1, s);
   if (fork) cudaStreamWaitEvent(s, h->join, 0);
   launch_finalize(g, h->p, s);
-  n += 2;
+  ++n;
   h->launches = n;
   return cuda_check(h, cudaGetLastError(), "kernel launch");
 }

@@ -87,6 +87,7 @@ struct DevPtrs {
   void* W1;
   double* acc;        // nsplit x 2nm x nc partial moment sums
   void* prm;          // NP x nc, compute type
+  float* wprm;        // 16 x nc, the window pass's per-cell parameters (FP32 tiers, d >= 2)
   double* eqp;        // NP x nc, FP64 parameters of E[U] (initial state only)
   double* UE;         // nm x nc, last step's U_E (FP64 copy)
   double* UM;         // nm x nc, last step's U_M
@@ -163,7 +164,7 @@ void launch_finalize(const Geom& g, const DevPtrs& p, cudaStream_t s);
 void launch_materialize(const Geom& g, const DevPtrs& p, double* out, cudaStream_t s);
 void launch_offsets(const Geom& g, long long n, long long* out, int width, cudaStream_t s);
 // dvm_kinetic.cu
-void launch_kinetic_pass(const Geom& g, const DevPtrs& p, cudaStream_t s);
+int launch_kinetic_pass(const Geom& g, const DevPtrs& p, cudaStream_t s);  // kernels launched
 void kinetic_pass_prepare(const Geom& g);
 int kinetic_pass_splits(const Geom& g);
 

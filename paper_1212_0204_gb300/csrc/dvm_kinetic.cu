@@ -205,45 +205,81 @@ __device__ __forceinline__ RawSlot load_raw(const float4* __restrict__ pg, long 
   return r;
 }
 
-// The raw parameters folded with the fixed velocity components vx (and vz).
+// Per-cell parameters of the window pass, folded once per step from the
+// parameter rows (k_window_fold): with L' = L - h |u|^2, h2_i = 2 h u_i and
+// Lambda_i = lambda nu'_i the exponent of the Maxwellian at v is
+//   L' + h2 . v - h |v|^2,
+// and lambda nu'.m and mu''.m are linear in (1, v, |v|^2).  Groups of four:
+//   3D: (lambda, L', h, h2_y) (h2_x, h2_z, Lambda_0, Lambda_x)
+//       (Lambda_y, Lambda_z, Lambda_4, mu_0) (mu_x, mu_y, mu_z, mu_4)
+//   2D: (lambda, L', h, h2_y) (h2_x, Lambda_0, Lambda_x, Lambda_y)
+//       (Lambda_4, mu_0, mu_x, mu_y) (mu_4, 0, 0, 0)
+// (index 4 is the coefficient of |v|^2).  Folding them with the fixed vx and
+// vz of a velocity pair leaves quadratics in vy.
 template <int D>
 __device__ __forceinline__ Slot fold_slot(const RawSlot& r, float vx, float vz, float vxz2) {
   const float4 g0 = r.g0, g1 = r.g1, g2 = r.g2, g3 = r.g3;
-  float ux, uy, uz = 0.f, L, h, nu0, nux, nuy, nuz = 0.f, nu4, mu0, mux, muy, muz = 0.f, mu4;
-  const float lam = g0.x;
-  L = g0.y; ux = g0.z; uy = g0.w;
-  if (D == 3) {
-    // rows: 4 uz 5 h 6 nu0 7 nux | 8 nuy 9 nuz 10 nu4 11 mu0 | 12 mux 13 muy 14 muz 15 mu4
-    uz = g1.x; h = g1.y; nu0 = g1.z; nux = g1.w;
-    nuy = g2.x; nuz = g2.y; nu4 = g2.z; mu0 = g2.w;
-    mux = g3.x; muy = g3.y; muz = g3.z; mu4 = g3.w;
-  } else {
-    // rows: 4 h 5 nu0 6 nux 7 nuy | 8 nu4 9 mu0 10 mux 11 muy | 12 mu4
-    h = g1.x; nu0 = g1.y; nux = g1.z; nuy = g1.w;
-    nu4 = g2.x; mu0 = g2.y; mux = g2.z; muy = g2.w;
-    mu4 = g3.x;
-  }
-  float q = (vx - ux) * (vx - ux);
-  float bn = fmaf(nux, vx, nu0), bm = fmaf(mux, vx, mu0);
-  if (D == 3) {
-    q = fmaf(vz - uz, vz - uz, q);
-    bn = fmaf(nuz, vz, bn);
-    bm = fmaf(muz, vz, bm);
-  }
-  const float n4 = nu4, m4 = mu4;  // coefficients of |v|^2
   Slot s;
-  s.lam = lam;
-  // -h (vx-ux)^2 - h (vz-uz)^2 - h (vy-uy)^2 + L as a quadratic in vy
+  const float h = g0.z;
+  s.lam = g0.x;
   s.c2 = -h;
-  s.c1 = 2.f * h * uy;
-  s.c0 = fmaf(-h, fmaf(uy, uy, q), L);
-  s.a0 = lam * fmaf(n4, vxz2, bn);
-  s.a1 = lam * nuy;
-  s.a2 = lam * n4;
-  s.b0 = fmaf(m4, vxz2, bm);
-  s.b1 = muy;
-  s.b2 = m4;
+  s.c1 = g0.w;
+  if (D == 3) {
+    s.c0 = fmaf(-h, vxz2, fmaf(vz, g1.y, fmaf(vx, g1.x, g0.y)));
+    s.a0 = fmaf(g2.z, vxz2, fmaf(g2.y, vz, fmaf(g1.w, vx, g1.z)));
+    s.a1 = g2.x;
+    s.a2 = g2.z;
+    s.b0 = fmaf(g3.w, vxz2, fmaf(g3.z, vz, fmaf(g3.x, vx, g2.w)));
+    s.b1 = g3.y;
+    s.b2 = g3.w;
+  } else {
+    s.c0 = fmaf(-h, vxz2, fmaf(vx, g1.x, g0.y));
+    s.a0 = fmaf(g2.x, vxz2, fmaf(g1.z, vx, g1.y));
+    s.a1 = g1.w;
+    s.a2 = g2.x;
+    s.b0 = fmaf(g3.x, vxz2, fmaf(g2.z, vx, g2.y));
+    s.b1 = g2.w;
+    s.b2 = g3.x;
+  }
   return s;
+}
+
+// One thread per cell: the parameter rows folded into the layout above.
+template <int D>
+__global__ void __launch_bounds__(256) k_window_fold(Geom g, DevPtrs p) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nc = g.nc;
+  if (c >= nc) return;
+  const float4* __restrict__ pg = (const float4*)p.prm;
+  float r[16];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float4 v = __ldg(pg + q * nc + c);
+    r[4 * q] = v.x, r[4 * q + 1] = v.y, r[4 * q + 2] = v.z, r[4 * q + 3] = v.w;
+  }
+  const float lam = r[row_lam()], L = r[row_L()], h = r[row_h(D)];
+  const float ux = r[row_u(0)], uy = r[row_u(1)], uz = D == 3 ? r[row_u(2)] : 0.f;
+  const float u2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+  float Lam[5], mu[5];
+#pragma unroll
+  for (int i = 0; i < D + 2; ++i) {
+    Lam[i] = lam * r[row_nu(D, i)];
+    mu[i] = r[row_mu(D, i)];
+  }
+  float4 o[4];
+  o[0] = make_float4(lam, fmaf(-h, u2, L), h, 2.f * h * uy);
+  if (D == 3) {
+    o[1] = make_float4(2.f * h * ux, 2.f * h * uz, Lam[0], Lam[1]);
+    o[2] = make_float4(Lam[2], Lam[3], Lam[4], mu[0]);
+    o[3] = make_float4(mu[1], mu[2], mu[3], mu[4]);
+  } else {
+    o[1] = make_float4(2.f * h * ux, Lam[0], Lam[1], Lam[2]);
+    o[2] = make_float4(Lam[3], mu[0], mu[1], mu[2]);
+    o[3] = make_float4(mu[3], 0.f, 0.f, 0.f);
+  }
+  float4* __restrict__ wg = (float4*)p.wprm;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) wg[q * nc + c] = o[q];
 }
 
 template <int D>
@@ -252,12 +288,10 @@ __device__ __forceinline__ Slot load_slot(const float4* __restrict__ pg, long lo
   return fold_slot<D>(load_raw(pg, nc4, src), vx, vz, vxz2);
 }
 
-// 4-byte asynchronous global -> shared copy (zero fill when !pred: no bytes
-// are read, the address is still a valid one), commit and wait.
-__device__ __forceinline__ void cp_async4(float* smem, const float* gmem, bool pred) {
+// 4-byte asynchronous global -> shared copy, commit and wait.
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  const int sz = pred ? 4 : 0;
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz) : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -339,7 +373,7 @@ __global__ void __launch_bounds__(32 * WinShape<D>::S, WinShape<D>::MINB)
   const long long nc = g.nc;
   const int plane = Nx * Ny;
   const float dv = (float)g.dv;
-  const float4* __restrict__ pg = (const float4*)p.prm;
+  const float4* __restrict__ pg = (const float4*)p.wprm;  // folded per cell (k_window_fold)
   TS* __restrict__ F = (TS*)p.F;
   bool tact[Y], sact[Y];
 #pragma unroll
@@ -365,7 +399,7 @@ __global__ void __launch_bounds__(32 * WinShape<D>::S, WinShape<D>::MINB)
 #pragma unroll
     for (int j = 0; j < Y; ++j) {
       const int yy = y0 + j < Ny ? y0 + j : Ny - 1;
-      lam_c[j] = __ldg((const float*)pg + prm_at(row_lam(), x + Nx * yy + plane * z, nc));
+      lam_c[j] = __ldg((const float*)p.prm + prm_at(row_lam(), x + Nx * yy + plane * z, nc));
     }
   }
   // velocity pairs (kz, kx) of this CTA (whole kz planes in 3D, a multiple of
@@ -397,16 +431,35 @@ __global__ void __launch_bounds__(32 * WinShape<D>::S, WinShape<D>::MINB)
     }
     const float* Fb_i = reinterpret_cast<const float*>(F) +
                         ((long long)kx_i + (long long)nvx * nvy * kz_i) * nc + qx_i + plane * qz_i;
+    // every address is a valid one (x clamped, rows wrapped): inactive
+    // targets copy a value nobody reads instead of taking a predicate
+    int rr[Y];
+    bool nowrap = true;
 #pragma unroll
     for (int jj = 0; jj < Y; ++jj) {
-      const int ky = kb_i - jj;
-      int r = y0 - s_oy[ky];
+      int r = y0 - s_oy[kb_i - jj];
       if (r < 0) r += Ny;
-      const float* Fk = Fb_i + (long long)ky * kystep;
+      rr[jj] = r;
+      nowrap = nowrap && r + Y <= Ny;
+    }
+    float* dst = s_fb + st * Y * Y * kWinT + tid;
+    if (nowrap) {  // no periodic wrap among the rows of the block (CTA-uniform)
 #pragma unroll
-      for (int j = 0; j < Y; ++j) {
-        cp_async4(s_fb + ((st * Y + jj) * Y + j) * kWinT + tid, Fk + r * Nx, tact[j]);
-        if (++r == Ny) r = 0;
+      for (int jj = 0; jj < Y; ++jj) {
+        const float* Fr = Fb_i + (long long)(kb_i - jj) * kystep + rr[jj] * Nx;
+#pragma unroll
+        for (int j = 0; j < Y; ++j) cp_async4(dst + (jj * Y + j) * kWinT, Fr + j * Nx);
+      }
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < Y; ++jj) {
+        const float* Fk = Fb_i + (long long)(kb_i - jj) * kystep;
+        int r = rr[jj];
+#pragma unroll
+        for (int j = 0; j < Y; ++j) {
+          cp_async4(dst + (jj * Y + j) * kWinT, Fk + r * Nx);
+          if (++r == Ny) r = 0;
+        }
       }
     }
   };
@@ -729,15 +782,19 @@ void kinetic_pass_prepare(const Geom& g) {
 
 bool kinetic_is_windowed(const Geom& g) { return window_eligible(g) && !getenv_generic(); }
 
-void launch_kinetic_pass(const Geom& g, const DevPtrs& p, cudaStream_t s) {
+int launch_kinetic_pass(const Geom& g, const DevPtrs& p, cudaStream_t s) {
   if (kinetic_is_windowed(g)) {
+    const unsigned nb = (unsigned)((g.nc + 255) / 256);
+    if (g.d == 2) k_window_fold<2><<<nb, 256, 0, s>>>(g, p);
+    else k_window_fold<3><<<nb, 256, 0, s>>>(g, p);
     if (g.precision == DVM_F32) launch_window<float>(g, p, s);
     else launch_window<__nv_bfloat16>(g, p, s);
-    return;
+    return 2;
   }
   if (g.precision == DVM_F64) launch_generic<double, double>(g, p, s);
   else if (g.precision == DVM_F32) launch_generic<float, float>(g, p, s);
   else launch_generic<__nv_bfloat16, float>(g, p, s);
+  return 1;
 }
 
 }  // namespace dvm
