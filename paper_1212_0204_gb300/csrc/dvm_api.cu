@@ -129,6 +129,7 @@ int make_geom(const dvm_config* cfg, Geom* g, std::string* msg) {
   bool outflow = false;
   for (int i = 0; i < d; ++i) outflow |= g->bc[i] == DVM_BC_OUTFLOW;
   g->ghost_mode = outflow ? (d == 1 ? 1 : 2) : 0;
+  g->rows_pass = kinetic_rows_allowed(*g) ? 1 : 0;
   g->nsplit = kinetic_pass_splits(*g);
   return 0;
 }
@@ -771,11 +772,24 @@ int dvm_profile_end(dvm_handle* h, double* kinetic_ms, int* launches) {
 int dvm_launches_per_step(dvm_handle* h, int* launches) {
   if (!h || !launches) return DVM_ERR_ARG;
   if (!h->state_set) return fail(h, DVM_ERR_STATE, "no state yet");
+  if (h->launches > 0) {  // counted by the last enqueued step
+    *launches = h->launches;
+    return 0;
+  }
   int n = 0;
   if (h->g.scheme != DVM_FKS && !h->g.skip_euler) n += 1;
   if (h->g.ghost_mode) n += 1;
-  n += 2;
+  n += kinetic_is_windowed(h->g) ? 2 : 1;  // (folded parameters +) kinetic pass
+  n += 1;                                  // end-of-step kernel
   *launches = n;
+  return 0;
+}
+
+int dvm_kinetic_kernel(const dvm_handle* h, int* kind) {
+  if (!h || !kind) return DVM_ERR_ARG;
+  *kind = !kinetic_is_windowed(h->g)      ? DVM_KPASS_GENERIC
+          : kinetic_rows_eligible(h->g) ? DVM_KPASS_ROWS
+                                        : DVM_KPASS_WINDOW;
   return 0;
 }
 

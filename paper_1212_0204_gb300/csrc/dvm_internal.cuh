@@ -76,6 +76,7 @@ struct Geom {
   int skip_euler;     // every lambda == 1: U_E = 0, no Euler launch
   int euler_blocks;   // grid of the cooperative Euler launch (all co-resident)
   int learn;          // learned regime path on: flagged cells (see dvm_learn.cuh)
+  int rows_pass;      // the kinetic pass runs on whole rows (dvm_kinetic_rows.cu)
 };
 
 struct DevPtrs {
@@ -166,6 +167,12 @@ void launch_offsets(const Geom& g, long long n, long long* out, int width, cudaS
 // dvm_kinetic.cu
 int launch_kinetic_pass(const Geom& g, const DevPtrs& p, cudaStream_t s);  // kernels launched
 void kinetic_pass_prepare(const Geom& g);
+// the row pass (dvm_kinetic_rows.cu): FP32, whole x rows moved by tensor copies
+bool kinetic_rows_allowed(const Geom& g);  // at dvm_create: opt-in and the shape fits
+inline bool kinetic_rows_eligible(const Geom& g) { return g.rows_pass != 0; }
+int kinetic_rows_splits(const Geom& g);
+void kinetic_rows_prepare(const Geom& g);
+cudaError_t launch_kinetic_rows(const Geom& g, const DevPtrs& p, cudaStream_t s);
 int kinetic_pass_splits(const Geom& g);
 
 }  // namespace dvm

@@ -13,6 +13,7 @@
 #include <type_traits>
 
 #include "dvm_internal.cuh"
+#include "dvm_window.cuh"
 
 namespace dvm {
 namespace {
@@ -177,73 +178,6 @@ __global__ void __launch_bounds__(kThreads) k_kpass_generic(Geom g, DevPtrs p) {
 // instead of Y.  The F loads of Y consecutive steps are issued together.
 // Velocity moments: FP32 within a row of ky (<= 256 terms, in practice 24-32),
 // FP32 across the kx of one kz plane, FP64 across planes and warps.
-struct Slot {
-  // M = exp2(c0 + c1 vy + c2 vy^2); lambda (f + nu'.m) = lambda f + a0 + a1 vy + a2 vy^2;
-  // mu''.m = b0 + b1 vy + b2 vy^2 (vx and vz folded in)
-  float lam, c0, c1, c2, a0, a1, a2, b0, b1, b2;
-};
-
-__device__ __forceinline__ float ex2_ftz(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-// Parameters of source cell src (grouped layout, four rows per float4):
-// loaded one step before they are folded, so that the loads are in flight
-// while the current step computes.
-struct RawSlot {
-  float4 g0, g1, g2, g3;
-};
-
-__device__ __forceinline__ RawSlot load_raw(const float4* __restrict__ pg, long long nc4, int src) {
-  RawSlot r;
-  r.g0 = __ldg(pg + src);
-  r.g1 = __ldg(pg + nc4 + src);
-  r.g2 = __ldg(pg + 2 * nc4 + src);
-  r.g3 = __ldg(pg + 3 * nc4 + src);
-  return r;
-}
-
-// Per-cell parameters of the window pass, folded once per step from the
-// parameter rows (k_window_fold): with L' = L - h |u|^2, h2_i = 2 h u_i and
-// Lambda_i = lambda nu'_i the exponent of the Maxwellian at v is
-//   L' + h2 . v - h |v|^2,
-// and lambda nu'.m and mu''.m are linear in (1, v, |v|^2).  Groups of four:
-//   3D: (lambda, L', h, h2_y) (h2_x, h2_z, Lambda_0, Lambda_x)
-//       (Lambda_y, Lambda_z, Lambda_4, mu_0) (mu_x, mu_y, mu_z, mu_4)
-//   2D: (lambda, L', h, h2_y) (h2_x, Lambda_0, Lambda_x, Lambda_y)
-//       (Lambda_4, mu_0, mu_x, mu_y) (mu_4, 0, 0, 0)
-// (index 4 is the coefficient of |v|^2).  Folding them with the fixed vx and
-// vz of a velocity pair leaves quadratics in vy.
-template <int D>
-__device__ __forceinline__ Slot fold_slot(const RawSlot& r, float vx, float vz, float vxz2) {
-  const float4 g0 = r.g0, g1 = r.g1, g2 = r.g2, g3 = r.g3;
-  Slot s;
-  const float h = g0.z;
-  s.lam = g0.x;
-  s.c2 = -h;
-  s.c1 = g0.w;
-  if (D == 3) {
-    s.c0 = fmaf(-h, vxz2, fmaf(vz, g1.y, fmaf(vx, g1.x, g0.y)));
-    s.a0 = fmaf(g2.z, vxz2, fmaf(g2.y, vz, fmaf(g1.w, vx, g1.z)));
-    s.a1 = g2.x;
-    s.a2 = g2.z;
-    s.b0 = fmaf(g3.w, vxz2, fmaf(g3.z, vz, fmaf(g3.x, vx, g2.w)));
-    s.b1 = g3.y;
-    s.b2 = g3.w;
-  } else {
-    s.c0 = fmaf(-h, vxz2, fmaf(vx, g1.x, g0.y));
-    s.a0 = fmaf(g2.x, vxz2, fmaf(g1.z, vx, g1.y));
-    s.a1 = g1.w;
-    s.a2 = g2.x;
-    s.b0 = fmaf(g3.x, vxz2, fmaf(g2.z, vx, g2.y));
-    s.b1 = g2.w;
-    s.b2 = g3.x;
-  }
-  return s;
-}
-
 // One thread per cell: the parameter rows folded into the layout above.
 template <int D>
 __global__ void __launch_bounds__(256) k_window_fold(Geom g, DevPtrs p) {
@@ -280,12 +214,6 @@ __global__ void __launch_bounds__(256) k_window_fold(Geom g, DevPtrs p) {
   float4* __restrict__ wg = (float4*)p.wprm;
 #pragma unroll
   for (int q = 0; q < 4; ++q) wg[q * nc + c] = o[q];
-}
-
-template <int D>
-__device__ __forceinline__ Slot load_slot(const float4* __restrict__ pg, long long nc4, int src,
-                                          float vx, float vz, float vxz2) {
-  return fold_slot<D>(load_raw(pg, nc4, src), vx, vz, vxz2);
 }
 
 // 4-byte asynchronous global -> shared copy, commit and wait.
@@ -760,6 +688,7 @@ void launch_generic(const Geom& g, const DevPtrs& p, cudaStream_t s) {
 // Velocity chunks: enough blocks for several waves on 152 SMs, at least 16
 // velocities per chunk.
 int kinetic_pass_splits(const Geom& g) {
+  if (kinetic_rows_eligible(g) && !getenv_generic()) return kinetic_rows_splits(g);
   if (window_eligible(g)) return window_shape(g).splits;
   const long long blocks = (g.nc + kThreads - 1) / kThreads;
   const long long want = 152LL * 8;
@@ -774,19 +703,28 @@ int kinetic_pass_splits(const Geom& g) {
 // Kernel attributes that must be set before the first launch (outside any
 // stream capture): dynamic shared memory of the windowed pass.
 void kinetic_pass_prepare(const Geom& g) {
+  if (kinetic_rows_eligible(g)) kinetic_rows_prepare(g);
   if (!window_eligible(g)) return;
   DevPtrs none{};
   if (g.precision == DVM_F32) launch_window<float>(g, none, nullptr, true);
   else launch_window<__nv_bfloat16>(g, none, nullptr, true);
 }
 
-bool kinetic_is_windowed(const Geom& g) { return window_eligible(g) && !getenv_generic(); }
+// The windowed or the row pass (both skip CTAs whose targets are all deep in
+// the learned path).
+bool kinetic_is_windowed(const Geom& g) {
+  return (kinetic_rows_eligible(g) || window_eligible(g)) && !getenv_generic();
+}
 
 int launch_kinetic_pass(const Geom& g, const DevPtrs& p, cudaStream_t s) {
   if (kinetic_is_windowed(g)) {
     const unsigned nb = (unsigned)((g.nc + 255) / 256);
     if (g.d == 2) k_window_fold<2><<<nb, 256, 0, s>>>(g, p);
     else k_window_fold<3><<<nb, 256, 0, s>>>(g, p);
+    if (kinetic_rows_eligible(g)) {
+      launch_kinetic_rows(g, p, s);
+      return 2;
+    }
     if (g.precision == DVM_F32) launch_window<float>(g, p, s);
     else launch_window<__nv_bfloat16>(g, p, s);
     return 2;

@@ -28,7 +28,8 @@ EXPORTS = [
     "dvm_workspace_bytes", "dvm_create", "dvm_destroy", "dvm_set_stream", "dvm_last_error",
     "dvm_set_state_moments", "dvm_set_state_primitive", "dvm_step", "dvm_step_async",
     "dvm_sync_status", "dvm_moments", "dvm_get_f", "dvm_last_parts", "dvm_info", "dvm_offsets",
-    "dvm_save", "dvm_load", "dvm_launches_per_step", "dvm_profile_begin", "dvm_profile_end",
+    "dvm_save", "dvm_load", "dvm_launches_per_step", "dvm_kinetic_kernel", "dvm_profile_begin",
+    "dvm_profile_end",
     "dvm_equilibrium_noalloc",
     "dvm_batch_create", "dvm_batch_destroy", "dvm_batch_last_error", "dvm_batch_sizes",
     "dvm_batch_set_state_moments", "dvm_batch_step", "dvm_batch_step_async",
@@ -119,6 +120,7 @@ def lib():
         L.dvm_save.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
         L.dvm_load.argtypes = [vp, vp, C.c_size_t]
         L.dvm_launches_per_step.argtypes = [vp, C.POINTER(C.c_int)]
+        L.dvm_kinetic_kernel.argtypes = [vp, C.POINTER(C.c_int)]
         L.dvm_profile_begin.argtypes = [vp]
         L.dvm_profile_end.argtypes = [vp, dp, C.POINTER(C.c_int)]
         L.dvm_equilibrium_noalloc.argtypes = [C.POINTER(_Config), vp, vp, vp]
@@ -350,6 +352,12 @@ class Solver:
         n = C.c_int()
         self._check(lib().dvm_launches_per_step(self._h, C.byref(n)))
         return n.value
+
+    def kinetic_kernel(self) -> str:
+        """'generic', 'window' or 'rows': the kinetic-pass kernel of this handle."""
+        k = C.c_int()
+        self._check(lib().dvm_kinetic_kernel(self._h, C.byref(k)))
+        return ("generic", "window", "rows")[k.value]
 
     # --------------------------------------------------- learned regime path
     def learn_enable(self, mode=LEARN_GIVEN, mlp_precision=F32, thr=-3.0, check_every=0,
