@@ -166,6 +166,10 @@ void launch_materialize(const Geom& g, const DevPtrs& p, double* out, cudaStream
 void launch_offsets(const Geom& g, long long n, long long* out, int width, cudaStream_t s);
 // dvm_kinetic.cu
 int launch_kinetic_pass(const Geom& g, const DevPtrs& p, cudaStream_t s);  // kernels launched
+// the windowed pass compiled for a configured shape (dvm_kinetic_shapes.cu):
+// launches it (or, with prepare, sets its attributes) and returns true if g is
+// one of them (FP32, HOFKS, learned path off)
+bool launch_window_fixed(const Geom& g, const DevPtrs& p, int splits, cudaStream_t s, bool prepare);
 void kinetic_pass_prepare(const Geom& g);
 // the row pass (dvm_kinetic_rows.cu): FP32, whole x rows moved by tensor copies
 bool kinetic_rows_allowed(const Geom& g);  // at dvm_create: opt-in and the shape fits
