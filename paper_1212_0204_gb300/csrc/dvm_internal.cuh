@@ -168,7 +168,7 @@ void launch_offsets(const Geom& g, long long n, long long* out, int width, cudaS
 int launch_kinetic_pass(const Geom& g, const DevPtrs& p, cudaStream_t s);  // kernels launched
 // the windowed pass compiled for a configured shape (dvm_kinetic_shapes.cu):
 // launches it (or, with prepare, sets its attributes) and returns true if g is
-// one of them (FP32, HOFKS, learned path off)
+// one of them (FP32, HOFKS; in 3D without the learned path)
 bool launch_window_fixed(const Geom& g, const DevPtrs& p, int splits, cudaStream_t s, bool prepare);
 void kinetic_pass_prepare(const Geom& g);
 // the row pass (dvm_kinetic_rows.cu): FP32, whole x rows moved by tensor copies

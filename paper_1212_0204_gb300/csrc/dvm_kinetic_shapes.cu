@@ -2,20 +2,21 @@
 // extents and velocity counts of the configured workloads fixed at compile
 // time (2D 128^2, 256^2, 512^2 x 32^2; 3D 32^3, 64^3, 96^3 x 24^3): the index
 // and address arithmetic of the pass then works on constants (on GB300 about
-// a quarter of its instructions).  FP32 storage, HOFKS, without the learned
-// path; every other configuration runs the same kernel with the extents read
+// a quarter of its instructions).  FP32 storage, HOFKS (2D also with the
+// learned path); every other configuration runs the same kernel with the extents read
 // at run time (dvm_kinetic.cu).
 #include "dvm_window_kernel.cuh"
 
 namespace dvm {
 namespace {
 
-template <int D, int CX, int CY, int CZ, int CV>
+template <int D, int CX, int CY, int CZ, int CV, bool LE>
 bool try_shape(const Geom& g, const DevPtrs& p, int splits, cudaStream_t s, bool prepare) {
   if (g.nx[0] != CX || g.nx[1] != CY || (D == 3 && g.nx[2] != CZ)) return false;
   if (g.nv[0] != CV || g.nv[1] != CV || (D == 3 && g.nv[2] != CV)) return false;
+  if (!prepare && (g.learn != 0) != LE) return false;
   constexpr size_t sm = window_smem(D, true, true);
-  auto* k = k_kpass_window<float, D, kWinY, true, true, false, CX, CY, CZ, CV>;
+  auto* k = k_kpass_window<float, D, kWinY, true, true, LE, CX, CY, CZ, CV>;
   if (prepare) {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     return true;
@@ -32,15 +33,23 @@ bool try_shape(const Geom& g, const DevPtrs& p, int splits, cudaStream_t s, bool
 }  // namespace
 
 bool launch_window_fixed(const Geom& g, const DevPtrs& p, int splits, cudaStream_t s, bool prepare) {
-  if (g.precision != DVM_F32 || g.scheme == DVM_FKS || g.learn) return false;
-  if (g.d == 2)
-    return try_shape<2, 256, 256, 1, 32>(g, p, splits, s, prepare) ||
-           try_shape<2, 512, 512, 1, 32>(g, p, splits, s, prepare) ||
-           try_shape<2, 128, 128, 1, 32>(g, p, splits, s, prepare);
-  if (g.d == 3)
-    return try_shape<3, 64, 64, 64, 24>(g, p, splits, s, prepare) ||
-           try_shape<3, 96, 96, 96, 24>(g, p, splits, s, prepare) ||
-           try_shape<3, 32, 32, 32, 24>(g, p, splits, s, prepare);
+  if (g.precision != DVM_F32 || g.scheme == DVM_FKS) return false;
+  if (g.d == 2) {
+    // with and without the learned path (both prepared at creation)
+    bool hit = false;
+    hit |= try_shape<2, 256, 256, 1, 32, false>(g, p, splits, s, prepare) ||
+           try_shape<2, 512, 512, 1, 32, false>(g, p, splits, s, prepare) ||
+           try_shape<2, 128, 128, 1, 32, false>(g, p, splits, s, prepare);
+    if (hit && !prepare) return true;
+    hit |= try_shape<2, 256, 256, 1, 32, true>(g, p, splits, s, prepare) ||
+           try_shape<2, 512, 512, 1, 32, true>(g, p, splits, s, prepare) ||
+           try_shape<2, 128, 128, 1, 32, true>(g, p, splits, s, prepare);
+    return hit;
+  }
+  if (g.d == 3 && !g.learn)
+    return try_shape<3, 64, 64, 64, 24, false>(g, p, splits, s, prepare) ||
+           try_shape<3, 96, 96, 96, 24, false>(g, p, splits, s, prepare) ||
+           try_shape<3, 32, 32, 32, 24, false>(g, p, splits, s, prepare);
   return false;
 }
 
