@@ -639,10 +639,7 @@ int dvm_get_f(dvm_handle* h, double* out, int on_device) {
 int dvm_last_parts(dvm_handle* h, double* UE, double* UM, double* Ustar) {
   int rc = ready(h);
   if (rc) return rc;
-  int m = 0;
-  if ((rc = cuda_check(h, cudaMemcpyAsync(h->pinned_status, h->p.msub, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "copy"))) return rc;
   if ((rc = cuda_check(h, cudaStreamSynchronize(h->stream), "sync"))) return rc;
-  m = *h->pinned_status;
   const size_t b = sizeof(double) * h->g.nm * h->g.nc;
   cudaStream_t s = h->stream;
   if (UE) rc |= cuda_check(h, cudaMemcpyAsync(UE, h->p.UE, b, cudaMemcpyDeviceToHost, s), "copy");

@@ -192,7 +192,6 @@ __global__ void k_b_prepare(BPtrs p) {
 template <typename TS, typename TW, bool LIMITED, bool EULER, bool SPLIT>
 __global__ void __launch_bounds__(kBE) k_b_euler(BPtrs p) {
   extern __shared__ unsigned char s_raw[];
-  __shared__ double s_red[kBE / 32];
   const int ci = p.order[blockIdx.x], tid = threadIdx.x;
   const BCase& bc = p.cases[ci];
   const int nx = bc.nx;
