@@ -5,6 +5,8 @@
 // a quarter of its instructions).  FP32 storage, HOFKS (2D also with the
 // learned path); every other configuration runs the same kernel with the extents read
 // at run time (dvm_kinetic.cu).
+#include <stdlib.h>
+
 #include "dvm_window_kernel.cuh"
 
 namespace dvm {
@@ -32,8 +34,12 @@ bool try_shape(const Geom& g, const DevPtrs& p, int splits, cudaStream_t s, bool
 
 }  // namespace
 
+// DVM_FIXED_SHAPES=0 runs the runtime-extent kernel for every shape (for
+// comparison runs and the test that both give the same result).
 bool launch_window_fixed(const Geom& g, const DevPtrs& p, int splits, cudaStream_t s, bool prepare) {
   if (g.precision != DVM_F32 || g.scheme == DVM_FKS) return false;
+  const char* e = getenv("DVM_FIXED_SHAPES");
+  if (e && e[0] == '0' && !prepare) return false;
   if (g.d == 2) {
     // with and without the learned path (both prepared at creation)
     bool hit = false;
