@@ -385,6 +385,21 @@ int dvm_mlp_train(dvm_mlp* m, long long n, const float* X, const float* t,
 int dvm_equilibrium_noalloc(const dvm_config* cfg, const double* U, double* f,
                             void* cuda_stream);
 
+/* Self-test of the device-side failure detection (no handle, no GPU fault):
+ * runs one of the library's bounded waits on an event that never comes and
+ * returns the device status word it left in *status, which is
+ * DVM_ERR_TIMEOUT when the wait gave up as designed; the context stays
+ * usable.
+ *   which: DVM_SELFTEST_GRID_BARRIER -- the grid barrier of the Euler
+ *            launches, one of two blocks leaving without arriving (about one
+ *            second at 2 GHz);
+ *          DVM_SELFTEST_MBARRIER -- the mbarrier wait of the tensor-core
+ *            kernels on a barrier nobody arrives at (about one second).
+ *   stream: cudaStream_t or NULL; the call synchronises it.
+ * Returns 0, DVM_ERR_ARG for another `which`, DVM_ERR_OOM or DVM_ERR_CUDA. */
+enum { DVM_SELFTEST_GRID_BARRIER = 0, DVM_SELFTEST_MBARRIER = 1 };
+int dvm_selftest_timeout(int which, void* cuda_stream, int* status);
+
 #ifdef __cplusplus
 }
 #endif

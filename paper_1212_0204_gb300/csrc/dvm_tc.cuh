@@ -89,13 +89,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait on phase `parity`: false after about 2^26 polls
+// bounded wait on phase `parity`: false after 2^31 SM clock cycles (about a
+// second); a poll count would not bound the time, the back-off sleeps can
+// last far longer than asked
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, unsigned parity) {
-  for (int i = 0; i < (1 << 26); ++i) {
+  if (mbar_try_wait(mbar, parity)) return true;
+  const long long t0 = clock64();
+  for (int i = 0;; ++i) {
     if (mbar_try_wait(mbar, parity)) return true;
+    if (clock64() - t0 > (1LL << 31)) return false;
     if (i > 64) __nanosleep(32);
   }
-  return false;
 }
 
 // 16 consecutive FP32 columns of this thread's TMEM lane (warp w reads lanes

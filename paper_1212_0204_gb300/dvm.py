@@ -22,6 +22,7 @@ ERR_TOO_LARGE = -9
 PERIODIC, OUTFLOW = 0, 1
 FKS, HOFKS, HOFKS_UNLIMITED = 0, 1, 2
 F64, F32, BF16S = 0, 1, 2
+SELFTEST_GRID_BARRIER, SELFTEST_MBARRIER = 0, 1
 
 # every symbol include/dvm.h declares (checked by the CPU tests)
 EXPORTS = [
@@ -30,7 +31,7 @@ EXPORTS = [
     "dvm_sync_status", "dvm_moments", "dvm_get_f", "dvm_last_parts", "dvm_info", "dvm_offsets",
     "dvm_save", "dvm_load", "dvm_launches_per_step", "dvm_kinetic_kernel", "dvm_profile_begin",
     "dvm_profile_end",
-    "dvm_equilibrium_noalloc",
+    "dvm_equilibrium_noalloc", "dvm_selftest_timeout",
     "dvm_batch_create", "dvm_batch_destroy", "dvm_batch_last_error", "dvm_batch_sizes",
     "dvm_batch_set_state_moments", "dvm_batch_step", "dvm_batch_step_async",
     "dvm_batch_sync_status", "dvm_batch_moments", "dvm_batch_get_f", "dvm_batch_info",
@@ -124,6 +125,7 @@ def lib():
         L.dvm_profile_begin.argtypes = [vp]
         L.dvm_profile_end.argtypes = [vp, dp, C.POINTER(C.c_int)]
         L.dvm_equilibrium_noalloc.argtypes = [C.POINTER(_Config), vp, vp, vp]
+        L.dvm_selftest_timeout.argtypes = [C.c_int, vp, C.POINTER(C.c_int)]
         L.dvm_batch_create.argtypes = [C.POINTER(_Config), ip, vp, C.POINTER(vp)]
         L.dvm_batch_destroy.argtypes = [vp]
         L.dvm_batch_destroy.restype = None
@@ -210,6 +212,20 @@ def equilibrium_noalloc(cfg, U, f, stream=None) -> int:
     s = stream if stream is not None else torch.cuda.current_stream()
     return lib().dvm_equilibrium_noalloc(C.byref(cfg), C.c_void_p(U.data_ptr()),
                                          C.c_void_p(f.data_ptr()), C.c_void_p(s.cuda_stream))
+
+
+def selftest_timeout(which: int, stream=None) -> int:
+    """Run one of the library's bounded device waits on an event that never
+    comes (dvm_selftest_timeout); returns the device status word it left
+    (ERR_TIMEOUT when the wait gave up as designed)."""
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libdvm needs a CUDA GPU; no CPU fallback exists")
+    st = C.c_int(0)
+    rc = lib().dvm_selftest_timeout(int(which), C.c_void_p(stream), C.byref(st))
+    if rc:
+        raise DvmError(rc, "selftest launch failed")
+    return st.value
 
 
 def workspace_bytes(cfg) -> int:
