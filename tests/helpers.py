@@ -44,3 +44,27 @@ def velocity_indices(g: oracle.Grid) -> np.ndarray:
           for i in range(3)]
     KZ, KY, KX = np.meshgrid(ks[2], ks[1], ks[0], indexing="ij")
     return np.stack([KX.ravel(), KY.ravel(), KZ.ravel()]).astype(np.int64)
+
+
+def paper_vortex_errors() -> dict:
+    """{(scheme, norm): errors at the meshes 25, 50, 100, 200, 300, 400} from the
+    isentropic-vortex table of Section 5.2 (tests/golden/vortex_errors.txt)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "vortex_errors.txt")
+    out = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            name, norm, *vals = line.split()
+            out[(getattr(oracle, name), norm)] = np.array([float(v) for v in vals])
+    return out
+
+
+VORTEX_MESHES = (25, 50, 100, 200, 300, 400)
+
+
+def vortex_errors(case, rho) -> tuple:
+    """The relative L1 and L-infinity density errors of Section 5.2 against the
+    translated exact vortex."""
+    ex = case.extra["rho_exact"]
+    return (np.abs(rho - ex).sum() / np.abs(ex).sum(),
+            np.abs(rho - ex).max() / np.abs(ex).max())

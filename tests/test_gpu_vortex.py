@@ -1,0 +1,75 @@
+"""Section 5.2's advected isentropic vortex on the GPU.
+
+* parity: the 50^2 x 40^2 vortex (two steps, 50 Euler sub-steps each) against the
+  FP64 oracle for FKS, unlimited HOFKS and HOFKS -- FP64 to 1e-12, FP32 to 1e-5 on
+  the moments;
+* the convergence study of the paper's table on all six meshes 25^2 .. 400^2 in
+  FP64: every L1 error within a factor 1.5 of the printed one (2 for FKS, whose
+  coarse-mesh errors depend most on the velocity grid), the L1 rates on the three
+  finest mesh pairs no more than 0.2 below the printed rates and no more than 0.5
+  above the table's expected order (1 for FKS, 2 for both HOFKS), and the order of
+  the schemes in the table (unlimited HOFKS and HOFKS far below FKS; the limiter's
+  L-infinity error above the unlimited scheme's).  The printed unlimited rates fall
+  to 1.69 on the finest pair, where a velocity-grid error floor shows; on the finer
+  velocity grid used here they stay at 2.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1212_0204_gb300 import workloads as W
+from tests.helpers import VORTEX_MESHES, conserved, oracle_run, paper_vortex_errors, vortex_errors
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1212_0204_gb300 import dvm  # noqa: E402
+
+SCHEMES = {oracle.FKS: dvm.FKS, oracle.HOFKS_UNLIMITED: dvm.HOFKS_UNLIMITED,
+           oracle.HOFKS: dvm.HOFKS}
+
+
+def moment_err(Ug, Uo):
+    scale = np.maximum(np.abs(Uo).max(axis=1), np.abs(Uo[0]).max())
+    return (np.abs(Ug - Uo).max(axis=1) / scale).max()
+
+
+def run(case, scheme, precision=dvm.F64):
+    s = dvm.Solver.from_case(case, precision=precision, scheme=SCHEMES[scheme])
+    s.set_moments(conserved(case))
+    s.step(case.steps)
+    U = s.moments()
+    s.close()
+    return U
+
+
+@pytest.mark.parametrize("scheme", list(SCHEMES))
+def test_vortex_50_matches_oracle(scheme):
+    case = W.isentropic_vortex_2d(50, scheme=scheme)
+    Uo = oracle_run(case).moments()
+    assert moment_err(run(case, scheme, dvm.F64), Uo) <= 1e-12
+    assert moment_err(run(case, scheme, dvm.F32), Uo) <= 1e-5
+
+
+def test_vortex_convergence_follows_the_table():
+    paper = paper_vortex_errors()
+    errs = {}
+    for scheme in SCHEMES:
+        e = np.array([vortex_errors(c, run(c, scheme)[0])
+                      for c in (W.isentropic_vortex_2d(n, scheme=scheme) for n in VORTEX_MESHES)])
+        errs[scheme] = e
+        factor = 2.0 if scheme == oracle.FKS else 1.5
+        ratio = e[:, 0] / paper[(scheme, "L1")]
+        assert np.all((ratio > 1 / factor) & (ratio < factor)), (scheme, e[:, 0])
+        m = np.array(VORTEX_MESHES, dtype=float)
+        rates = np.log(e[:-1, 0] / e[1:, 0]) / np.log(m[1:] / m[:-1])
+        prates = (np.log(paper[(scheme, "L1")][:-1] / paper[(scheme, "L1")][1:])
+                  / np.log(m[1:] / m[:-1]))
+        order = 1.0 if scheme == oracle.FKS else 2.0
+        assert np.all((rates[-3:] > prates[-3:] - 0.2) & (rates[-3:] < order + 0.5)), (scheme, rates)
+    for scheme in (oracle.HOFKS_UNLIMITED, oracle.HOFKS):
+        assert np.all(errs[scheme][2:, 0] < 0.25 * errs[oracle.FKS][2:, 0])
+    assert np.all(errs[oracle.HOFKS][2:, 1] > 1.5 * errs[oracle.HOFKS_UNLIMITED][2:, 1])

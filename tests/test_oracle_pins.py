@@ -15,7 +15,8 @@ import pytest
 
 import oracle
 from paper_1212_0204_gb300 import workloads as W
-from tests.helpers import conserved, grid, oracle_run, velocities, velocity_indices
+from tests.helpers import (VORTEX_MESHES, conserved, grid, oracle_run, paper_vortex_errors,
+                           velocities, velocity_indices, vortex_errors)
 
 
 def rand_U(rng, d, n):
@@ -350,6 +351,33 @@ def test_spatial_order_on_a_smooth_advected_wave():
         assert np.all(rates[scheme] > max(1.5, paper[scheme].min())), rates[scheme]
     lo, hi = paper[oracle.FKS].min() - 0.1, paper[oracle.FKS].max() + 0.1
     assert np.all((rates[oracle.FKS] > lo) & (rates[oracle.FKS] < hi)), rates[oracle.FKS]
+
+
+def test_isentropic_vortex_errors_and_rates_follow_the_table():
+    """Section 5.2's advected isentropic vortex (t = 1, tau = 1e-4, Euler sub-steps
+    of order dx^2) on the 25^2, 50^2 and 100^2 meshes: for unlimited HOFKS and
+    HOFKS the L1 density errors lie within a factor 1.5 of the printed ones and the
+    L1 rates within 0.2 of the printed rates; the limited scheme's L-infinity error
+    stays above the unlimited one's at 100^2 (extrema clipped by the limiter), as in
+    the table.  A dropped or mis-signed slope term, a wrong limiter or a transposed
+    direction leaves these rates near 1 or the error far from the table."""
+    paper = paper_vortex_errors()
+    rates = paper_rates()
+    linf100 = {}
+    for scheme in (oracle.HOFKS_UNLIMITED, oracle.HOFKS):
+        e1 = []
+        for n in VORTEX_MESHES[:3]:
+            case = W.isentropic_vortex_2d(n, scheme=scheme)
+            s = oracle_run(case)
+            l1, linf = vortex_errors(case, s.moments()[0])
+            e1.append(l1)
+        linf100[scheme] = linf
+        e1 = np.array(e1)
+        ratio = e1 / paper[(scheme, "L1")][:3]
+        assert np.all((ratio > 1 / 1.5) & (ratio < 1.5)), (scheme, e1)
+        r = np.log2(e1[:-1] / e1[1:])
+        assert np.all(np.abs(r - rates[scheme][:2]) < 0.2), (scheme, r)
+    assert linf100[oracle.HOFKS] > 1.5 * linf100[oracle.HOFKS_UNLIMITED]
 
 
 # ----------------------------------------------------------- brute force, one step
