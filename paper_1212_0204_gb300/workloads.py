@@ -8,6 +8,7 @@ moments are done by each side on its own.
 
 Workloads (analytic initial data, no dataset):
   * ``sod_1d``          1D-1V Riemann tube (Section 5.1 shape).
+  * ``sod_1d_300x100``  Section 5.1's Sod tube itself: 300 cells, 100 velocities.
   * ``quadrant_2d``     2D-2V four-quadrant Riemann problem with a 1 % seeded
                         density perturbation (counter-based SplitMix64).
   * ``density_wave_3d`` 3D-3V periodic smooth density wave.
@@ -156,6 +157,17 @@ def entropy_wave_1d(nx: int, nv: int = 32, tau: float = 1e-4, dv: float = 0.4,
     return Case("entropy_wave_1d", 1, (nx,), dx, (nv,), (-(nv // 2),), dv, 1, (PERIODIC,),
                 tau, rho, np.full((1, nx), ux), 1.0 / rho, steps, scheme, subcycles,
                 extra={"amp": amp, "ux": ux, "t_final": steps * dx / dv})
+
+
+def sod_1d_300x100(tau: float, scheme: int = HOFKS) -> Case:
+    """Section 5.1's Sod tube: 300 cells on [0, 1], 100 velocities on [-15, 15)
+    (dv = 0.3), left (rho, u, T) = (1, 0, 5), right (0.125, 0, 4), outflow, up to
+    t = 0.05, for the relaxation times 1e-2, 1e-3, 5e-4 and 1e-4 of the paper.
+    The paper gives no time step; dt = dx / v_max (p = v_max / dv = 50, 225 steps)
+    is the one at which these four tau run from the kinetic (dt / tau = 0.02) to
+    the fluid regime (2.2)."""
+    return sod_1d(nx=300, nv=100, tau=tau, dv=0.3, p=50, t_final=0.05,
+                  left=(1.0, 5.0), right=(0.125, 4.0), scheme=scheme)
 
 
 def isentropic_vortex_2d(n: int, nv: int = 40, vmax: float = 8.0, tau: float = 1e-4,

@@ -353,6 +353,33 @@ def test_spatial_order_on_a_smooth_advected_wave():
     assert np.all((rates[oracle.FKS] > lo) & (rates[oracle.FKS] < hi)), rates[oracle.FKS]
 
 
+def test_sod_300x100_regimes_follow_section_5_1():
+    """Section 5.1's Sod tube (300 x 100, T 5 / 4, t = 0.05) at the four relaxation
+    times: HOFKS and FKS give almost identical densities at tau = 1e-2 (kinetic
+    regime, both reduce to the kinetic step) and move apart as tau falls; at
+    tau = 1e-4 (fluid regime) HOFKS is much closer than FKS to the exact Euler
+    solution (gamma = 3, reading R4), and closer already at 5e-4.  A scheme whose
+    HOFKS part were lost (no U_E - U_M correction, no MUSCL slopes) would leave the
+    two schemes equal at every tau."""
+    nx = 300
+    x = (np.arange(nx) + 0.5) / nx
+    exact, *_ = oracle.riemann_exact(3.0, (1.0, 0.0, 5.0), (0.125, 0.0, 0.5), (x - 0.5) / 0.05)
+    gaps, errs = [], []
+    for tau in (1e-2, 1e-3, 5e-4, 1e-4):
+        rho = {}
+        for scheme in (oracle.FKS, oracle.HOFKS):
+            case = W.sod_1d_300x100(tau, scheme)
+            assert case.steps * case.dt == pytest.approx(0.05)
+            rho[scheme] = oracle_run(case).moments()[0]
+        gaps.append(np.abs(rho[oracle.FKS] - rho[oracle.HOFKS]).sum() / np.abs(rho[oracle.HOFKS]).sum())
+        errs.append([np.abs(rho[k] - exact).sum() / np.abs(exact).sum()
+                     for k in (oracle.FKS, oracle.HOFKS)])
+    assert np.all(np.diff(gaps) > 0), gaps
+    assert gaps[0] < 0.01 * gaps[-1], gaps
+    assert errs[3][1] < 0.5 * errs[3][0], errs
+    assert errs[2][1] < errs[2][0], errs
+
+
 def test_isentropic_vortex_errors_and_rates_follow_the_table():
     """Section 5.2's advected isentropic vortex (t = 1, tau = 1e-4, Euler sub-steps
     of order dx^2) on the 25^2, 50^2 and 100^2 meshes: for unlimited HOFKS and
