@@ -213,17 +213,32 @@ bool window_eligible(const Geom& g) {
   return g.nv[1] % kWinY == 0 && g.nv[0] % win_warps(g.d) == 0 && g.nx[1] >= kWinY && g.nc < (1LL << 31);
 }
 
-// Velocity splits across CTAs: the smallest divisor (of the kz planes in 3D,
-// of nvx / S in 2D) that gives two waves of three CTAs per SM, at most 8.
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+  }
+  return n;
+}
+
+// Velocity splits across CTAs (slices of the kz planes in 3D, of the nvx / S
+// groups in 2D).  Among the divisors c <= 4 that leave a CTA at least 2^16
+// updates, the one with the fewest CTA waves per unit of work,
+// ceil(tiles c / R) / c with R the resident CTAs, so that the last wave is
+// nearly full; ties go to the larger c (finer load balance).
 WinLaunch window_shape(const Geom& g) {
   const long long tiles = ((g.nx[0] + 31) / 32) * ((g.nx[1] + kWinY - 1) / kWinY) * g.nx[2];
-  const long long target_ctas = 152LL * 3 * 2;
+  const long long resident = (long long)sm_count() * (g.d == 3 ? WinShape<3>::MINB : WinShape<2>::MINB);
+  const long long cta_updates = 32LL * kWinY * g.nvel;
   const int units = g.d == 3 ? g.nv[2] : g.nv[0] / win_warps(g.d);
   int sp = 1;
-  for (int c = 1; c <= 8 && c <= units; ++c) {
-    if (units % c) continue;
-    sp = c;
-    if (tiles * c >= target_ctas) break;
+  double best = 1e30;
+  for (int c = 1; c <= 4 && c <= units; ++c) {
+    if (units % c || (c > 1 && cta_updates / c < (1LL << 16))) continue;
+    const double waves = (double)((tiles * c + resident - 1) / resident) / c;
+    if (waves <= best) { best = waves; sp = c; }
   }
   WinLaunch wl;
   wl.S = win_warps(g.d);
