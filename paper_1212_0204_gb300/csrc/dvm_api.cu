@@ -242,7 +242,7 @@ void bind(dvm_handle* h, char* base, const Layout& L) {
   p.msub = (int*)(sm + 72);
   p.status = (int*)(sm + 76);
   p.counter = (unsigned int*)(sm + 80);
-  p.gbar = (unsigned int*)(sm + 96);                  // 2 unsigned
+  p.gbar = (unsigned long long*)(sm + 96);            // 1 count
   p.mlast = (int*)(sm + 104);
   p.alpha_prev = (double*)(sm + 112);                 // 3 doubles
   p.aslot = (unsigned long long*)(sm + 144);          // 9
@@ -371,7 +371,7 @@ int init_from_moments(dvm_handle* h) {
   if ((rc = cuda_check(h, cudaMemsetAsync(h->p.msub, 0, sizeof(int), s), "memset"))) return rc;
   if ((rc = cuda_check(h, cudaMemsetAsync(h->p.mlast, 0, sizeof(int), s), "memset"))) return rc;
   if ((rc = cuda_check(h, cudaMemsetAsync(h->p.alpha_prev, 0, 3 * sizeof(double), s), "memset"))) return rc;
-  if ((rc = cuda_check(h, cudaMemsetAsync(h->p.gbar, 0, 2 * sizeof(unsigned), s), "memset"))) return rc;
+  if ((rc = cuda_check(h, cudaMemsetAsync(h->p.gbar, 0, sizeof(unsigned long long), s), "memset"))) return rc;
   if ((rc = cuda_check(h, cudaMemsetAsync(h->p.aslot, 0, 9 * sizeof(unsigned long long), s), "memset"))) return rc;
   if (h->lmem) {
     // a new state: no cell is flagged (f = E[U] everywhere anyway)

@@ -315,10 +315,8 @@ __global__ void __launch_bounds__(ETile<D, TF>::THREADS) k_euler(Geom g, DevPtrs
     TF* dst = (TF*)((s & 1) ? p.W0 : p.W1);
     // thread 0 issues its reads of the barrier generation and of this
     // sub-step's alpha first; their latency overlaps the first tile's staging
-    unsigned gen = 0;
     double ad[3] = {0.0, 0.0, 0.0};
     if (tid == 0) {
-      gen = *reinterpret_cast<volatile unsigned*>(p.gbar + 1);
       // alpha of this sub-step's initial state: slot s % 3, complete since the
       // barrier that ended the previous sub-step
 #pragma unroll
@@ -428,7 +426,7 @@ __global__ void __launch_bounds__(ETile<D, TF>::THREADS) k_euler(Geom g, DevPtrs
       if (blockIdx.x == 0 && tid == 0) set_status(p.status, DVM_ERR_CFL);
       break;
     }
-    if (!grid_sync(p.gbar, p.status, gen)) return;
+    if (!grid_sync(p.gbar, p.status)) return;
   }
   if (blockIdx.x == 0 && tid == 0) {
     *p.msub = s + 1;
@@ -510,10 +508,8 @@ __global__ void __launch_bounds__(GTile<D, TF>::THREADS, 4) k_euler_g(Geom g, De
   for (;; ++s) {
     const TF* src = (const TF*)((s & 1) ? p.W1 : p.W0);
     TF* dst = (TF*)((s & 1) ? p.W0 : p.W1);
-    unsigned gen = 0;
     double ad[3] = {0.0, 0.0, 0.0};
     if (tid == 0) {
-      gen = *reinterpret_cast<volatile unsigned*>(p.gbar + 1);
 #pragma unroll
       for (int d = 0; d < 3; ++d) ad[d] = __longlong_as_double((long long)__ldcg(p.aslot + (s % 3) * 3 + d));
     }
@@ -642,7 +638,7 @@ __global__ void __launch_bounds__(GTile<D, TF>::THREADS, 4) k_euler_g(Geom g, De
       if (blockIdx.x == 0 && tid == 0) set_status(p.status, DVM_ERR_CFL);
       break;
     }
-    if (!grid_sync(p.gbar, p.status, gen)) return;
+    if (!grid_sync(p.gbar, p.status)) return;
   }
   if (blockIdx.x == 0 && tid == 0) {
     *p.msub = s + 1;

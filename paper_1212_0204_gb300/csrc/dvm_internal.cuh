@@ -102,7 +102,7 @@ struct DevPtrs {
   int* status;        // first error code
   long long* step;    // step index n
   unsigned int* counter;  // finished-block counter of the alpha reduction
-  unsigned int* gbar;     // grid barrier of the Euler launch: count, generation
+  unsigned long long* gbar;  // grid barrier of the Euler launch: arrival count
   unsigned long long* aslot;  // 3 x 3: alpha (bit patterns) of Euler sub-steps s, s+1, s+2
   // learned path (null unless Geom::learn): flags of the step, cells whose
   // every source is flagged too, 1 / (1 - lambda)

@@ -117,32 +117,39 @@ __device__ inline TF slope(TF a, TF b) {
   return ab > TF(0) ? e_div(ab + ab, a + b) : TF(0);
 }
 
-// Grid-wide barrier of the cooperative Euler launch: arrive on a counter, the
-// last block to arrive advances the generation word.  The wait is bounded
-// (2^31 SM clock cycles, about a second); on timeout the status word gets
-// DVM_ERR_TIMEOUT and false is returned so that the kernel can leave.
-// gen: the generation word as thread 0 read it before its block did the work
-// of this phase (it can only change once every block has arrived).
-__device__ bool grid_sync(unsigned* bar, int* status, unsigned gen) {
+// Grid-wide barrier of the cooperative Euler launch on a 64-bit arrival
+// counter that only grows: a block takes a ticket and waits until the count
+// reaches the end of its ticket's generation, ceil((ticket + 1) / n) n with n
+// the blocks of the launch (every launch of a handle completes whole
+// generations, so the count is a multiple of n between launches).  No block
+// resets or republishes anything, so the last arrival releases the others
+// with its own atomic.  The wait is bounded (2^31 SM clock cycles, about a
+// second); on timeout the status word gets DVM_ERR_TIMEOUT and false is
+// returned so that the kernel can leave.
+__device__ inline unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ bool grid_sync(unsigned long long* bar, int* status) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 1;
+    const unsigned long long n = gridDim.x;
     __threadfence();
+    const unsigned long long ticket = atomicAdd(bar, 1ull);
+    const unsigned long long target = (ticket / n + 1) * n;
     int good = 1;
-    if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
+    if (ticket + 1 != target) {
       const long long t0 = clock64();
-      while (*vgen == gen) {
+      while (ld_acquire_u64(bar) < target) {
         if (clock64() - t0 > (1LL << 31)) {
           set_status(status, DVM_ERR_TIMEOUT);
           good = 0;
           break;
         }
-        __nanosleep(100);
+        __nanosleep(20);
       }
     }
     __threadfence();

@@ -13,11 +13,9 @@
 namespace dvm {
 namespace {
 
-__global__ void k_selftest_grid(unsigned* bar, int* status) {
+__global__ void k_selftest_grid(unsigned long long* bar, int* status) {
   if (blockIdx.x == 1) return;  // never arrives
-  unsigned gen = 0;
-  if (threadIdx.x == 0) gen = *reinterpret_cast<volatile unsigned*>(bar + 1);
-  grid_sync(bar, status, gen);
+  grid_sync(bar, status);
 }
 
 __global__ void k_selftest_mbar(int* status) {
@@ -37,7 +35,7 @@ extern "C" int dvm_selftest_timeout(int which, void* cuda_stream, int* status) {
   using namespace dvm;
   if (!status || (which != DVM_SELFTEST_GRID_BARRIER && which != DVM_SELFTEST_MBARRIER)) return DVM_ERR_ARG;
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  unsigned* scratch = nullptr;  // bar[0], bar[1], status
+  unsigned* scratch = nullptr;  // barrier count (2 words), status
   if (cudaMalloc((void**)&scratch, 4 * sizeof(unsigned)) != cudaSuccess) {
     cudaGetLastError();
     return DVM_ERR_OOM;
@@ -46,7 +44,7 @@ extern "C" int dvm_selftest_timeout(int which, void* cuda_stream, int* status) {
   int* st = reinterpret_cast<int*>(scratch + 2);
   if (cudaMemsetAsync(scratch, 0, 4 * sizeof(unsigned), s) != cudaSuccess) rc = DVM_ERR_CUDA;
   if (!rc) {
-    if (which == DVM_SELFTEST_GRID_BARRIER) k_selftest_grid<<<2, 64, 0, s>>>(scratch, st);
+    if (which == DVM_SELFTEST_GRID_BARRIER) k_selftest_grid<<<2, 64, 0, s>>>(reinterpret_cast<unsigned long long*>(scratch), st);
     else k_selftest_mbar<<<1, 32, 0, s>>>(st);
     int host = 0;
     if (cudaGetLastError() != cudaSuccess ||
