@@ -139,6 +139,30 @@ int dvm_sync_status(dvm_handle* h);
  * (d+2) x N_c FP64 into the caller's buffer (host or device). */
 int dvm_moments(dvm_handle* h, double* out, int on_device);
 
+/* Pipelined read-back of the same moments after every step enqueued so far,
+ * for a caller that reads each step's result while later steps run.  The
+ * moments and the status word are copied on the device in stream order into
+ * one of two snapshot slots, and from there into `out` ((d+2) x N_c FP64,
+ * host -- pinned for an asynchronous copy -- or device; caller-owned, left
+ * untouched by the library after dvm_moments_wait returns, and not to be read
+ * or freed before) on a private copy stream.  At most two read-backs are in
+ * flight: the stream of the steps waits (on the device) until a slot's
+ * previous copy has left it before reusing it.  *ticket (0, 1, 2, ... per
+ * handle) names the read-back for dvm_moments_wait.  The first call allocates
+ * the two slots (2 (d+2) N_c doubles) and must come before any capture of
+ * the handle's stream.  Errors: DVM_ERR_ARG (null out or ticket), a CUDA
+ * failure (DVM_ERR_CUDA). */
+int dvm_moments_async(dvm_handle* h, double* out, int on_device, long long* ticket);
+
+/* Blocks until read-back `ticket` is in its output buffer (copies complete
+ * in ticket order), then returns the device status word as that ticket's
+ * snapshot found it: DVM_OK or the error code, which also becomes the
+ * handle's sticky error like dvm_step's.  The statuses of the last 64
+ * tickets are kept; an older ticket waits for the newest read-back and
+ * reports its status (the device status is sticky, so it holds at least the
+ * older ticket's error).  DVM_ERR_ARG for a ticket not issued. */
+int dvm_moments_wait(dvm_handle* h, long long ticket);
+
 /* f^n at the cell centres, N_v x N_c FP64 (velocity-major), materialised
  * from the piece storage (the library never moves f; see dvm_offsets). */
 int dvm_get_f(dvm_handle* h, double* out, int on_device);

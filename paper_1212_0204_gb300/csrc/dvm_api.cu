@@ -52,6 +52,16 @@ struct dvm_handle {
   cudaGraphExec_t exec_chk = nullptr;
   float* scratch = nullptr;        // read-back staging (features, labels)
   size_t scratch_bytes = 0;
+  // pipelined read-back (dvm_moments_async / dvm_moments_wait): two device
+  // slots of the moments plus the status word, copied out on `copy`
+  static constexpr int kRing = 64; // read-backs whose status is kept apart
+  cudaStream_t copy = nullptr;
+  double* snap = nullptr;          // 2 slots of snap_stride doubles
+  long long snap_stride = 0;       // nm nc + 2 (status word at the end)
+  cudaEvent_t snap_ev[2] = {nullptr, nullptr};
+  int* rb_status = nullptr;        // pinned, status of ticket t at [t % kRing]
+  cudaEvent_t rb_ev[kRing] = {};   // ticket t's copies done
+  long long rb_issued = 0;
 };
 
 namespace {
@@ -337,20 +347,23 @@ int ensure_graph(dvm_handle* h, int check = 0) {
   return cuda_check(h, cudaGraphInstantiate(ex, graph, 0), "graph instantiate");
 }
 
+// A device status word read back to the host: 0, or the handle's sticky error.
+int device_status(dvm_handle* h, int st) {
+  if (!st) return 0;
+  const char* what = st == DVM_ERR_NONFINITE ? "non-finite moments"
+                   : st == DVM_ERR_NONPHYSICAL ? "rho <= 0 or theta <= 0 in some cell"
+                   : st == DVM_ERR_CFL ? "Euler sub-steps exceed the launch cap"
+                   : st == DVM_ERR_TIMEOUT ? "a bounded device wait timed out"
+                   : "device error";
+  return fail(h, st, what);
+}
+
 int sync_status(dvm_handle* h) {
   int rc = cuda_check(h, cudaMemcpyAsync(h->pinned_status, h->p.status, sizeof(int),
                                          cudaMemcpyDeviceToHost, h->stream), "status copy");
   if (rc) return rc;
   if ((rc = cuda_check(h, cudaStreamSynchronize(h->stream), "stream sync"))) return rc;
-  const int st = *h->pinned_status;
-  if (st) {
-    const char* what = st == DVM_ERR_NONFINITE ? "non-finite moments"
-                     : st == DVM_ERR_NONPHYSICAL ? "rho <= 0 or theta <= 0 in some cell"
-                     : st == DVM_ERR_CFL ? "Euler sub-steps exceed the launch cap"
-                     : "device error";
-    return fail(h, st, what);
-  }
-  return 0;
+  return device_status(h, *h->pinned_status);
 }
 
 int ready(dvm_handle* h) {
@@ -510,6 +523,16 @@ void dvm_destroy(dvm_handle* h) {
   if (h->own_ws && h->ws) cudaFree(h->ws);
   if (h->lmem) cudaFree(h->lmem);
   if (h->scratch) cudaFree(h->scratch);
+  if (h->copy) {
+    cudaStreamSynchronize(h->copy);
+    cudaStreamDestroy(h->copy);
+  }
+  for (int i = 0; i < 2; ++i)
+    if (h->snap_ev[i]) cudaEventDestroy(h->snap_ev[i]);
+  for (int i = 0; i < dvm_handle::kRing; ++i)
+    if (h->rb_ev[i]) cudaEventDestroy(h->rb_ev[i]);
+  if (h->snap) cudaFree(h->snap);
+  if (h->rb_status) cudaFreeHost(h->rb_status);
   delete h;
 }
 
@@ -616,6 +639,66 @@ int dvm_moments(dvm_handle* h, double* out, int on_device) {
                                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                           h->stream), "moments copy"))) return rc;
   return cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
+}
+
+int dvm_moments_async(dvm_handle* h, double* out, int on_device, long long* ticket) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!out || !ticket) return fail(h, DVM_ERR_ARG, "null output or ticket");
+  constexpr int R = dvm_handle::kRing;
+  const long long n = (long long)h->g.nm * h->g.nc;
+  if (!h->snap) {
+    h->snap_stride = n + 2;
+    if ((rc = cuda_check(h, cudaMalloc(&h->snap, sizeof(double) * 2 * h->snap_stride), "read-back slots")))
+      return rc;
+    if ((rc = cuda_check(h, cudaMallocHost(&h->rb_status, R * sizeof(int)), "read-back status"))) return rc;
+    for (int i = 0; i < R; ++i) h->rb_status[i] = 0;
+    if ((rc = cuda_check(h, cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking), "copy stream")))
+      return rc;
+    for (int i = 0; i < 2; ++i)
+      if ((rc = cuda_check(h, cudaEventCreateWithFlags(&h->snap_ev[i], cudaEventDisableTiming), "event")))
+        return rc;
+    for (int i = 0; i < R; ++i)
+      if ((rc = cuda_check(h, cudaEventCreateWithFlags(&h->rb_ev[i], cudaEventDisableTiming), "event")))
+        return rc;
+  }
+  const long long t = h->rb_issued;
+  const int slot = (int)(t & 1), r = (int)(t % R);
+  double* snap = h->snap + slot * h->snap_stride;
+  cudaStream_t s = h->stream;
+  // the slot's previous user, ticket t - 2, has been copied out of it
+  if (t >= 2 && (rc = cuda_check(h, cudaStreamWaitEvent(s, h->rb_ev[(t - 2) % R], 0), "slot wait"))) return rc;
+  if ((rc = cuda_check(h, cudaMemcpyAsync(snap, h->p.U, sizeof(double) * n, cudaMemcpyDeviceToDevice, s),
+                       "moments snapshot")))
+    return rc;
+  if ((rc = cuda_check(h, cudaMemcpyAsync(snap + n, h->p.status, sizeof(int), cudaMemcpyDeviceToDevice, s),
+                       "status snapshot")))
+    return rc;
+  if ((rc = cuda_check(h, cudaEventRecord(h->snap_ev[slot], s), "event"))) return rc;
+  if ((rc = cuda_check(h, cudaStreamWaitEvent(h->copy, h->snap_ev[slot], 0), "copy wait"))) return rc;
+  if ((rc = cuda_check(h, cudaMemcpyAsync(out, snap, sizeof(double) * n,
+                                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->copy),
+                       "moments copy")))
+    return rc;
+  if ((rc = cuda_check(h, cudaMemcpyAsync(h->rb_status + r, snap + n, sizeof(int), cudaMemcpyDeviceToHost,
+                                          h->copy), "status copy")))
+    return rc;
+  if ((rc = cuda_check(h, cudaEventRecord(h->rb_ev[r], h->copy), "event"))) return rc;
+  *ticket = t;
+  h->rb_issued = t + 1;
+  return 0;
+}
+
+int dvm_moments_wait(dvm_handle* h, long long ticket) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (ticket < 0 || ticket >= h->rb_issued) return fail(h, DVM_ERR_ARG, "read-back ticket not issued");
+  constexpr int R = dvm_handle::kRing;
+  // a ticket whose ring entry a later one took: the newest read-back (copies
+  // complete in ticket order, and the device status is sticky)
+  const long long t = ticket < h->rb_issued - R ? h->rb_issued - 1 : ticket;
+  if ((rc = cuda_check(h, cudaEventSynchronize(h->rb_ev[t % R]), "read-back wait"))) return rc;
+  return device_status(h, h->rb_status[t % R]);
 }
 
 int dvm_get_f(dvm_handle* h, double* out, int on_device) {

@@ -28,7 +28,7 @@ SELFTEST_GRID_BARRIER, SELFTEST_MBARRIER = 0, 1
 EXPORTS = [
     "dvm_workspace_bytes", "dvm_create", "dvm_destroy", "dvm_set_stream", "dvm_last_error",
     "dvm_set_state_moments", "dvm_set_state_primitive", "dvm_step", "dvm_step_async",
-    "dvm_sync_status", "dvm_moments", "dvm_get_f", "dvm_last_parts", "dvm_info", "dvm_offsets",
+    "dvm_sync_status", "dvm_moments", "dvm_moments_async", "dvm_moments_wait", "dvm_get_f", "dvm_last_parts", "dvm_info", "dvm_offsets",
     "dvm_save", "dvm_load", "dvm_launches_per_step", "dvm_kinetic_kernel", "dvm_profile_begin",
     "dvm_profile_end",
     "dvm_equilibrium_noalloc", "dvm_selftest_timeout",
@@ -114,6 +114,8 @@ def lib():
         L.dvm_step_async.argtypes = [vp, ip]
         L.dvm_sync_status.argtypes = [vp]
         L.dvm_moments.argtypes = [vp, vp, ip]
+        L.dvm_moments_async.argtypes = [vp, vp, ip, C.POINTER(C.c_longlong)]
+        L.dvm_moments_wait.argtypes = [vp, C.c_longlong]
         L.dvm_get_f.argtypes = [vp, vp, ip]
         L.dvm_last_parts.argtypes = [vp, vp, vp, vp]
         L.dvm_info.argtypes = [vp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_int), dp]
@@ -264,6 +266,7 @@ class Solver:
         if rc:
             raise DvmError(rc, "dvm_create failed")
         self._h = h
+        self._pending = {}
 
     @classmethod
     def from_case(cls, case, precision=F64, scheme=None, subcycles=None, **kw):
@@ -318,6 +321,31 @@ class Solver:
         a = np.zeros((self.nm, self.nc))
         self._check(lib().dvm_moments(self._h, a.ctypes.data_as(C.c_void_p), 0))
         return a
+
+    def moments_async(self, out):
+        """Enqueue a read-back of the moments after the steps enqueued so far into
+        `out` (a float64 (d+2, N_c) torch tensor, pinned host or CUDA, or a numpy
+        array); returns a ticket for moments_wait.  `out` is kept alive until then."""
+        t = self._torch
+        if isinstance(out, t.Tensor):
+            assert out.dtype == t.float64 and out.is_contiguous() and out.numel() == self.nm * self.nc
+            ptr, dev = out.data_ptr(), 1 if out.is_cuda else 0
+        else:
+            assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == self.nm * self.nc
+            ptr, dev = out.ctypes.data, 0
+        ticket = C.c_longlong()
+        self._check(lib().dvm_moments_async(self._h, C.c_void_p(ptr), dev, C.byref(ticket)))
+        self._pending[ticket.value] = out
+        return ticket.value
+
+    def moments_wait(self, ticket):
+        """Block until read-back `ticket` is in its buffer; raises DvmError with the
+        device status as that read-back's snapshot found it."""
+        try:
+            self._check(lib().dvm_moments_wait(self._h, int(ticket)))
+        finally:
+            for k in [k for k in self._pending if k <= ticket]:
+                del self._pending[k]
 
     def f(self):
         a = np.zeros((self.nvel, self.nc))
