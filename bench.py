@@ -457,29 +457,23 @@ def main():
 
     # ---- end to end through the public API with host buffers: the initial
     # moments uploaded from pinned memory, then every step advanced and its
-    # moments read back into pinned host memory.  A single problem reads step
-    # i's moments with dvm_moments_async while step i + 1 runs and waits for
-    # them (status included) before enqueuing step i + 2; a batch reads them
-    # with the synchronous dvm_batch_moments.
+    # moments read back into pinned host memory: step i's moments are read
+    # with the pipelined read-back while step i + 1 runs, and waited for
+    # (status included) before step i + 2 is enqueued.
     outs = [torch.empty((job.rows, job.cells), dtype=torch.float64).pin_memory() for _ in range(2)]
     barrier()
     t0 = time.perf_counter()
     job.set_moments(U0)             # H2D of the initial moments, builds f^0
-    if job.batch:
-        for _ in range(args.steps):
-            job.obj.step(1)
-            job.obj.moments(outs[0])    # D2H of this step's moments
-        how = "dvm_batch_moments after each step"
-    else:
-        prev = None
-        for i in range(args.steps):
-            job.obj.step_async(1)
-            t = job.obj.moments_async(outs[i & 1])   # D2H of this step's moments
-            if prev is not None:
-                job.obj.moments_wait(prev)           # step i - 1's moments are on the host
-            prev = t
-        job.obj.moments_wait(prev)
-        how = "dvm_moments_async after each step, waited one step later"
+    prev = None
+    for i in range(args.steps):
+        job.obj.step_async(1)
+        t = job.obj.moments_async(outs[i & 1])   # D2H of this step's moments
+        if prev is not None:
+            job.obj.moments_wait(prev)           # step i - 1's moments are on the host
+        prev = t
+    job.obj.moments_wait(prev)
+    how = ("dvm_batch_moments_async" if job.batch else "dvm_moments_async") + \
+        " after each step, waited one step later"
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     mom_bytes = 8 * job.rows * job.cells

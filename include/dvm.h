@@ -241,6 +241,12 @@ int dvm_batch_step_async(dvm_batch* b, int nsteps);
 int dvm_batch_sync_status(dvm_batch* b);
 /* Packed moments of all cases into the caller's buffer (host or device). */
 int dvm_batch_moments(dvm_batch* b, double* out, int on_device);
+/* Pipelined read-back of the packed moments (3 x total cells FP64), with the
+ * semantics of dvm_moments_async / dvm_moments_wait: snapshot on the device in
+ * stream order, copy on a private stream, at most two in flight, the status
+ * word as each ticket's snapshot found it. */
+int dvm_batch_moments_async(dvm_batch* b, double* out, int on_device, long long* ticket);
+int dvm_batch_moments_wait(dvm_batch* b, long long ticket);
 /* f of case icase at its cell centres, N_v x N_x FP64, host buffer. */
 int dvm_batch_get_f(dvm_batch* b, int icase, double* out);
 /* Step index, per-case Euler sub-steps and alpha of the last step (host

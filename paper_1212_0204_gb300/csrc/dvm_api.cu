@@ -11,6 +11,7 @@
 
 #include "dvm_internal.cuh"
 #include "dvm_learn.cuh"
+#include "dvm_readback.cuh"
 
 using namespace dvm;
 
@@ -52,16 +53,7 @@ struct dvm_handle {
   cudaGraphExec_t exec_chk = nullptr;
   float* scratch = nullptr;        // read-back staging (features, labels)
   size_t scratch_bytes = 0;
-  // pipelined read-back (dvm_moments_async / dvm_moments_wait): two device
-  // slots of the moments plus the status word, copied out on `copy`
-  static constexpr int kRing = 64; // read-backs whose status is kept apart
-  cudaStream_t copy = nullptr;
-  double* snap = nullptr;          // 2 slots of snap_stride doubles
-  long long snap_stride = 0;       // nm nc + 2 (status word at the end)
-  cudaEvent_t snap_ev[2] = {nullptr, nullptr};
-  int* rb_status = nullptr;        // pinned, status of ticket t at [t % kRing]
-  cudaEvent_t rb_ev[kRing] = {};   // ticket t's copies done
-  long long rb_issued = 0;
+  dvm::ReadBack rb;                // dvm_moments_async / dvm_moments_wait
 };
 
 namespace {
@@ -523,16 +515,7 @@ void dvm_destroy(dvm_handle* h) {
   if (h->own_ws && h->ws) cudaFree(h->ws);
   if (h->lmem) cudaFree(h->lmem);
   if (h->scratch) cudaFree(h->scratch);
-  if (h->copy) {
-    cudaStreamSynchronize(h->copy);
-    cudaStreamDestroy(h->copy);
-  }
-  for (int i = 0; i < 2; ++i)
-    if (h->snap_ev[i]) cudaEventDestroy(h->snap_ev[i]);
-  for (int i = 0; i < dvm_handle::kRing; ++i)
-    if (h->rb_ev[i]) cudaEventDestroy(h->rb_ev[i]);
-  if (h->snap) cudaFree(h->snap);
-  if (h->rb_status) cudaFreeHost(h->rb_status);
+  h->rb.release();
   delete h;
 }
 
@@ -645,60 +628,17 @@ int dvm_moments_async(dvm_handle* h, double* out, int on_device, long long* tick
   int rc = ready(h);
   if (rc) return rc;
   if (!out || !ticket) return fail(h, DVM_ERR_ARG, "null output or ticket");
-  constexpr int R = dvm_handle::kRing;
-  const long long n = (long long)h->g.nm * h->g.nc;
-  if (!h->snap) {
-    h->snap_stride = n + 2;
-    if ((rc = cuda_check(h, cudaMalloc(&h->snap, sizeof(double) * 2 * h->snap_stride), "read-back slots")))
-      return rc;
-    if ((rc = cuda_check(h, cudaMallocHost(&h->rb_status, R * sizeof(int)), "read-back status"))) return rc;
-    for (int i = 0; i < R; ++i) h->rb_status[i] = 0;
-    if ((rc = cuda_check(h, cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking), "copy stream")))
-      return rc;
-    for (int i = 0; i < 2; ++i)
-      if ((rc = cuda_check(h, cudaEventCreateWithFlags(&h->snap_ev[i], cudaEventDisableTiming), "event")))
-        return rc;
-    for (int i = 0; i < R; ++i)
-      if ((rc = cuda_check(h, cudaEventCreateWithFlags(&h->rb_ev[i], cudaEventDisableTiming), "event")))
-        return rc;
-  }
-  const long long t = h->rb_issued;
-  const int slot = (int)(t & 1), r = (int)(t % R);
-  double* snap = h->snap + slot * h->snap_stride;
-  cudaStream_t s = h->stream;
-  // the slot's previous user, ticket t - 2, has been copied out of it
-  if (t >= 2 && (rc = cuda_check(h, cudaStreamWaitEvent(s, h->rb_ev[(t - 2) % R], 0), "slot wait"))) return rc;
-  if ((rc = cuda_check(h, cudaMemcpyAsync(snap, h->p.U, sizeof(double) * n, cudaMemcpyDeviceToDevice, s),
-                       "moments snapshot")))
-    return rc;
-  if ((rc = cuda_check(h, cudaMemcpyAsync(snap + n, h->p.status, sizeof(int), cudaMemcpyDeviceToDevice, s),
-                       "status snapshot")))
-    return rc;
-  if ((rc = cuda_check(h, cudaEventRecord(h->snap_ev[slot], s), "event"))) return rc;
-  if ((rc = cuda_check(h, cudaStreamWaitEvent(h->copy, h->snap_ev[slot], 0), "copy wait"))) return rc;
-  if ((rc = cuda_check(h, cudaMemcpyAsync(out, snap, sizeof(double) * n,
-                                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->copy),
-                       "moments copy")))
-    return rc;
-  if ((rc = cuda_check(h, cudaMemcpyAsync(h->rb_status + r, snap + n, sizeof(int), cudaMemcpyDeviceToHost,
-                                          h->copy), "status copy")))
-    return rc;
-  if ((rc = cuda_check(h, cudaEventRecord(h->rb_ev[r], h->copy), "event"))) return rc;
-  *ticket = t;
-  h->rb_issued = t + 1;
-  return 0;
+  return cuda_check(h, h->rb.issue(h->stream, h->p.U, (long long)h->g.nm * h->g.nc, h->p.status, out,
+                                   on_device != 0, ticket), "moments read-back");
 }
 
 int dvm_moments_wait(dvm_handle* h, long long ticket) {
   int rc = ready(h);
   if (rc) return rc;
-  if (ticket < 0 || ticket >= h->rb_issued) return fail(h, DVM_ERR_ARG, "read-back ticket not issued");
-  constexpr int R = dvm_handle::kRing;
-  // a ticket whose ring entry a later one took: the newest read-back (copies
-  // complete in ticket order, and the device status is sticky)
-  const long long t = ticket < h->rb_issued - R ? h->rb_issued - 1 : ticket;
-  if ((rc = cuda_check(h, cudaEventSynchronize(h->rb_ev[t % R]), "read-back wait"))) return rc;
-  return device_status(h, h->rb_status[t % R]);
+  if (ticket < 0 || ticket >= h->rb.issued) return fail(h, DVM_ERR_ARG, "read-back ticket not issued");
+  int st = 0;
+  if ((rc = cuda_check(h, h->rb.wait(ticket, &st), "read-back wait"))) return rc;
+  return device_status(h, st);
 }
 
 int dvm_get_f(dvm_handle* h, double* out, int on_device) {

@@ -23,6 +23,7 @@
 
 #include "dvm_internal.cuh"
 #include "dvm_math.cuh"
+#include "dvm_readback.cuh"
 
 namespace dvm {
 namespace {
@@ -546,6 +547,7 @@ struct dvm_batch {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaStream_t side = nullptr;       // high-priority stream of the Euler kernel
   cudaEvent_t fork = nullptr, join = nullptr;
+  dvm::ReadBack rb;                  // dvm_batch_moments_async / _wait
 };
 
 namespace {
@@ -864,6 +866,7 @@ void dvm_batch_destroy(dvm_batch* b) {
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->join) cudaEventDestroy(b->join);
   if (b->side) cudaStreamDestroy(b->side);
+  b->rb.release();
   delete b;
 }
 
@@ -925,6 +928,23 @@ int dvm_batch_moments(dvm_batch* b, double* out, int on_device) {
   if (b->status) return b->status;
   int rc = bcheck(b, cudaMemcpyAsync(out, b->p.U, 8 * 3 * b->ncells, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream), "copy");
   return rc ? rc : bcheck(b, cudaStreamSynchronize(b->stream), "sync");
+}
+
+int dvm_batch_moments_async(dvm_batch* b, double* out, int on_device, long long* ticket) {
+  if (!b || !out || !ticket) return DVM_ERR_ARG;
+  if (b->status) return b->status;
+  return bcheck(b, b->rb.issue(b->stream, b->p.U, 3 * b->ncells, b->p.status, out, on_device != 0, ticket),
+                "moments read-back");
+}
+
+int dvm_batch_moments_wait(dvm_batch* b, long long ticket) {
+  if (!b) return DVM_ERR_ARG;
+  if (b->status) return b->status;
+  if (ticket < 0 || ticket >= b->rb.issued) return bfail(b, DVM_ERR_ARG, "read-back ticket not issued");
+  int st = 0;
+  int rc = bcheck(b, b->rb.wait(ticket, &st), "read-back wait");
+  if (rc) return rc;
+  return st ? bfail(b, st, "device error in a batch case") : 0;
 }
 
 int dvm_batch_get_f(dvm_batch* b, int icase, double* out) {

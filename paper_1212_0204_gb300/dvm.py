@@ -34,7 +34,7 @@ EXPORTS = [
     "dvm_equilibrium_noalloc", "dvm_selftest_timeout",
     "dvm_batch_create", "dvm_batch_destroy", "dvm_batch_last_error", "dvm_batch_sizes",
     "dvm_batch_set_state_moments", "dvm_batch_step", "dvm_batch_step_async",
-    "dvm_batch_sync_status", "dvm_batch_moments", "dvm_batch_get_f", "dvm_batch_info",
+    "dvm_batch_sync_status", "dvm_batch_moments", "dvm_batch_moments_async", "dvm_batch_moments_wait", "dvm_batch_get_f", "dvm_batch_info",
     "dvm_batch_set_tiling", "dvm_batch_autotune", "dvm_batch_kinetic_ms",
     "dvm_learn_enable", "dvm_learn_set_params", "dvm_learn_set_flags", "dvm_learn_flags",
     "dvm_learn_predictions", "dvm_learn_get_stats", "dvm_learn_step_checked", "dvm_features",
@@ -116,6 +116,8 @@ def lib():
         L.dvm_moments.argtypes = [vp, vp, ip]
         L.dvm_moments_async.argtypes = [vp, vp, ip, C.POINTER(C.c_longlong)]
         L.dvm_moments_wait.argtypes = [vp, C.c_longlong]
+        L.dvm_batch_moments_async.argtypes = [vp, vp, ip, C.POINTER(C.c_longlong)]
+        L.dvm_batch_moments_wait.argtypes = [vp, C.c_longlong]
         L.dvm_get_f.argtypes = [vp, vp, ip]
         L.dvm_last_parts.argtypes = [vp, vp, vp, vp]
         L.dvm_info.argtypes = [vp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_int), dp]
@@ -565,6 +567,7 @@ class Batch:
         if rc:
             raise DvmError(rc, "dvm_batch_create failed")
         self._h = h
+        self._pending = {}
         cells, pts = C.c_longlong(), C.c_longlong()
         lib().dvm_batch_sizes(h, C.byref(cells), C.byref(pts))
         self.ncells, self.npoints = cells.value, pts.value
@@ -612,6 +615,28 @@ class Batch:
         a = np.zeros((3, self.ncells))
         self._check(lib().dvm_batch_moments(self._h, a.ctypes.data_as(C.c_void_p), 0))
         return a
+
+    def moments_async(self, out):
+        """Pipelined read-back of the packed moments into `out` (float64 (3, cells):
+        pinned host or CUDA torch tensor, or numpy array); returns a ticket."""
+        t = self._torch
+        if isinstance(out, t.Tensor):
+            assert out.dtype == t.float64 and out.is_contiguous() and out.numel() == 3 * self.ncells
+            ptr, dev = out.data_ptr(), 1 if out.is_cuda else 0
+        else:
+            assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == 3 * self.ncells
+            ptr, dev = out.ctypes.data, 0
+        ticket = C.c_longlong()
+        self._check(lib().dvm_batch_moments_async(self._h, C.c_void_p(ptr), dev, C.byref(ticket)))
+        self._pending[ticket.value] = out
+        return ticket.value
+
+    def moments_wait(self, ticket):
+        try:
+            self._check(lib().dvm_batch_moments_wait(self._h, int(ticket)))
+        finally:
+            for k in [k for k in self._pending if k <= ticket]:
+                del self._pending[k]
 
     def case_moments(self, U, i):
         return U[:, self.offsets[i]:self.offsets[i + 1]]

@@ -7,6 +7,8 @@
 * the status word travels with the snapshot: the 50^2 vortex with FKS on the
   coarse 20^2 velocity grid leaves the physical states at step 7, and exactly the
   read-backs from step 7 on report DVM_ERR_NONPHYSICAL;
+* the batch read-back (dvm_batch_moments_async / _wait) of 16 uneven tubes equals
+  the synchronous dvm_batch_moments of the same run, bit for bit;
 * a ticket that was never issued is rejected.
 """
 import numpy as np
@@ -91,3 +93,32 @@ def test_unissued_ticket_is_rejected():
         s.moments_wait(0)
     assert e.value.code == -1
     s.close()
+
+
+def test_batch_pipelined_readback_equals_synchronous():
+    cases = W.batched_tubes(ncases=16, steps=5, nx_range=(40, 300))
+    U0 = None
+    want = []
+    b = dvm.Batch(cases, precision=dvm.F32)
+    U0 = b.pack([conserved(c) for c in cases])
+    b.set_moments(U0)
+    for _ in range(5):
+        b.step(1)
+        want.append(b.moments())
+    b.close()
+    b = dvm.Batch(cases, precision=dvm.F32)
+    b.set_moments(U0)
+    bufs = [torch.empty((3, b.ncells), dtype=torch.float64).pin_memory() for _ in range(2)]
+    got, prev = [], None
+    for i in range(5):
+        b.step_async(1)
+        t = b.moments_async(bufs[i & 1])
+        if prev is not None:
+            b.moments_wait(prev)
+            got.append(bufs[(i - 1) & 1].numpy().copy())
+        prev = t
+    b.moments_wait(prev)
+    got.append(bufs[4 & 1].numpy().copy())
+    b.close()
+    for i in range(5):
+        assert np.array_equal(got[i], want[i]), i
