@@ -1,0 +1,82 @@
+"""Planted mistakes in a copy of the oracle must fail its CPU pins.
+
+Each mutant is one plausible error in one step of the method -- a dropped term, a
+wrong sign, a swapped ratio, a wrong exponent -- made in a temporary copy of
+``oracle/`` (the committed oracle is never touched).  The copy is built by its own
+loader with the same compiler flags, then the pin tests of
+``tests/test_oracle_pins.py`` (all but the 18 s vortex study) run against it in a
+subprocess whose ``import oracle`` resolves to the copy.  The unmodified copy must
+pass; every mutant must make at least one pin fail.  This shows that the pins fix
+the oracle from outside itself: none of them merely re-evaluates the oracle's own
+formula.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# (what is wrong, file, original line fragment, planted line fragment)
+MUTANTS = [
+    ("piece rule: the 1/2 of the offset rounding dropped (Section 4.2)",
+     "dvm_oracle.c", "long long num = 2 * k * n + p;", "long long num = 2 * k * n;"),
+    ("Maxwellian: exponent -|v-u|^2/theta instead of /(2 theta) (Eq. M)",
+     "dvm_oracle.c", "M[k] = pref * exp(-q / (2.0 * theta));", "M[k] = pref * exp(-q / theta);"),
+    ("collision invariant |v|^2 instead of |v|^2 / 2 (Section 3)",
+     "dvm_oracle.c", "m[d + 1] = 0.5 * v2;", "m[d + 1] = v2;"),
+    ("relaxation factor exp(-tau/dt) instead of exp(-dt/tau) (Section 4.3.1)",
+     "dvm_oracle.c", "S->lam[c] = exp(-S->dt / t);", "S->lam[c] = exp(-t / S->dt);"),
+    ("HOFKS correction with U_M - U_E instead of U_E - U_M (Eq. minim_full)",
+     "dvm_oracle.c", "r[i] = S->UE[i * nc + c] - um[i];", "r[i] = um[i] - S->UE[i * nc + c];"),
+    ("MUSCL face flux with sigma+ + sigma- instead of sigma+ - sigma- (Eq. discmom)",
+     "dvm_oracle.c", "0.25 * (sp - sm);", "0.25 * (sp + sm);"),
+    ("flux splitting G+ = F - alpha U (Eq. discmom)",
+     "dvm_oracle.c", "Gp[s] = Fs[s][i] + alpha * Us[s][i];", "Gp[s] = Fs[s][i] - alpha * Us[s][i];"),
+    ("van Leer slope without its |a||b| term (Section 4.3.2)",
+     "dvm_oracle.c", "return (fabs(a) * fabs(b) + a * b) / (a + b);", "return (a * b) / (a + b);"),
+    ("exact Riemann solver: rarefaction density (p*/p)^gamma instead of ^(1/gamma)",
+     "riemann.c", "*r = rl * pow(ps / pl, 1.0 / gamma);", "*r = rl * pow(ps / pl, gamma);"),
+    ("network gradient: 1 + tanh^2 instead of the derivative 1 - tanh^2",
+     "mlp.c", "d1[i] = s2 * (1.0 - h1[i] * h1[i]);", "d1[i] = s2 * (1.0 + h1[i] * h1[i]);"),
+]
+
+
+def oracle_copy(tmp_path, mutant=None):
+    dst = tmp_path / "oracle"
+    shutil.copytree(os.path.join(ROOT, "oracle"), dst,
+                    ignore=shutil.ignore_patterns("*.so", "*.tmp*", "__pycache__"))
+    if mutant is not None:
+        _, fname, old, new = mutant
+        path = dst / fname
+        src = path.read_text()
+        assert src.count(old) == 1, (fname, old)
+        path.write_text(src.replace(old, new))
+    return tmp_path
+
+
+def run_in(tmp_path, args, timeout=300):
+    env = dict(os.environ, PYTHONPATH=os.pathsep.join([str(tmp_path), ROOT]))
+    return subprocess.run([sys.executable] + args, cwd=str(tmp_path), env=env, capture_output=True,
+                          text=True, timeout=timeout)
+
+
+def pins_against(tmp_path):
+    build = run_in(tmp_path, ["-c", "import oracle; oracle.build(force=True); print(oracle.__file__)"])
+    assert build.returncode == 0, build.stderr[-2000:]
+    assert build.stdout.strip().startswith(str(tmp_path)), build.stdout
+    return run_in(tmp_path, ["-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-x", "-q",
+                             "-p", "no:cacheprovider", "-k", "not isentropic_vortex"])
+
+
+def test_unmodified_copy_passes_the_pins(tmp_path):
+    r = pins_against(oracle_copy(tmp_path))
+    assert r.returncode == 0, r.stdout[-3000:]
+
+
+@pytest.mark.parametrize("mutant", MUTANTS, ids=[m[0].split(":")[0][:40] for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(tmp_path, mutant):
+    r = pins_against(oracle_copy(tmp_path, mutant))
+    assert r.returncode == 1 and " failed" in r.stdout, (mutant[0], r.returncode, r.stdout[-3000:])

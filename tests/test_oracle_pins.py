@@ -256,7 +256,8 @@ def test_muscl_conserves_and_keeps_uniform_states(limited):
 ])
 def test_exact_riemann_solution_satisfies_jump_conditions(gamma, left, right):
     """Textbook facts: Rankine-Hugoniot across shocks, constant entropy and Riemann
-    invariant across rarefactions, continuous u and p across the contact."""
+    invariant across rarefactions (entropy also in the star state behind one),
+    continuous u and p across the contact."""
     xi = np.linspace(-4, 4, 40001)
     r, u, p, ps, us = oracle.riemann_exact(gamma, left, right, xi)
     E = lambda r_, u_, p_: p_ / (gamma - 1) + 0.5 * r_ * u_ ** 2
@@ -282,6 +283,10 @@ def test_exact_riemann_solution_satisfies_jump_conditions(gamma, left, right):
             np.testing.assert_allclose(ent, pk / rk ** gamma, rtol=1e-10)
             inv = u[inside] - sgn * 2 * np.sqrt(gamma * p[inside] / r[inside]) / (gamma - 1)
             np.testing.assert_allclose(inv, uk - sgn * 2 * cs / (gamma - 1), rtol=1e-10, atol=1e-12)
+            # the star state between the tail and the contact has the same entropy
+            star = (xi > min(tail, us) + 1e-3) & (xi < max(tail, us) - 1e-3)
+            assert star.sum() > 10
+            np.testing.assert_allclose(p[star] / r[star] ** gamma, pk / rk ** gamma, rtol=1e-10)
     # contact: u and p continuous, equal to (u*, p*) on both sides
     near = np.abs(xi - us) < 1e-2
     np.testing.assert_allclose(u[near], us, rtol=1e-10, atol=1e-12)
