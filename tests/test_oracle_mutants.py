@@ -3,12 +3,12 @@
 Each mutant is one plausible error in one step of the method -- a dropped term, a
 wrong sign, a swapped ratio, a wrong exponent -- made in a temporary copy of
 ``oracle/`` (the committed oracle is never touched).  The copy is built by its own
-loader with the same compiler flags, then the pin tests of
-``tests/test_oracle_pins.py`` (all but the 18 s vortex study) run against it in a
-subprocess whose ``import oracle`` resolves to the copy.  The unmodified copy must
-pass; every mutant must make at least one pin fail.  This shows that the pins fix
-the oracle from outside itself: none of them merely re-evaluates the oracle's own
-formula.
+loader with the same compiler flags, then the pin tests -- ``tests/test_oracle_pins.py``
+(all but the 18 s vortex study) for the scheme, ``tests/test_oracle_learned.py`` for
+the learned path -- run against it in a subprocess whose ``import oracle`` resolves to
+the copy.  The unmodified copy must pass; every mutant must make at least one pin
+fail.  This shows that the pins fix the oracle from outside itself: none of them
+merely re-evaluates the oracle's own formula.
 """
 import os
 import shutil
@@ -43,6 +43,20 @@ MUTANTS = [
      "mlp.c", "d1[i] = s2 * (1.0 - h1[i] * h1[i]);", "d1[i] = s2 * (1.0 + h1[i] * h1[i]);"),
 ]
 
+# the learned path: flagged step, non-equilibrium label, features
+LEARNED_MUTANTS = [
+    ("flagged cell keeps its lambda instead of the lambda -> 0 form (Theorem 1)",
+     "dvm_oracle.c", "lam_eff[c] = fl ? 0.0 : S->lam[c];", "lam_eff[c] = S->lam[c];"),
+    ("flagged cells not written back as E[U^{n+1}]",
+     "dvm_oracle.c", "if (!(flags[c] != 0 && lam[c] != 1.0)) continue;", "if (1) continue;"),
+    ("label normalised by ||f|| instead of ||E[U]||",
+     "dvm_oracle.c", "den += fabs(E[k]);", "den += fabs(f[k * nc + c]);"),
+    ("shear features with the derivatives transposed (d u_x/dx, d u_y/dy)",
+     "dvm_oracle.c", "t * fabs(Dq[2][1]), t * fabs(Dq[3][0])", "t * fabs(Dq[2][0]), t * fabs(Dq[3][1])"),
+    ("central difference over dx instead of 2 dx",
+     "dvm_oracle.c", "const double h2 = 2.0 * g->dx;", "const double h2 = g->dx;"),
+]
+
 
 def oracle_copy(tmp_path, mutant=None):
     dst = tmp_path / "oracle"
@@ -63,20 +77,27 @@ def run_in(tmp_path, args, timeout=300):
                           text=True, timeout=timeout)
 
 
-def pins_against(tmp_path):
+def pins_against(tmp_path, module="test_oracle_pins.py"):
     build = run_in(tmp_path, ["-c", "import oracle; oracle.build(force=True); print(oracle.__file__)"])
     assert build.returncode == 0, build.stderr[-2000:]
     assert build.stdout.strip().startswith(str(tmp_path)), build.stdout
-    return run_in(tmp_path, ["-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-x", "-q",
+    return run_in(tmp_path, ["-m", "pytest", os.path.join(ROOT, "tests", module), "-x", "-q",
                              "-p", "no:cacheprovider", "-k", "not isentropic_vortex"])
 
 
-def test_unmodified_copy_passes_the_pins(tmp_path):
-    r = pins_against(oracle_copy(tmp_path))
+@pytest.mark.parametrize("module", ["test_oracle_pins.py", "test_oracle_learned.py"])
+def test_unmodified_copy_passes_the_pins(tmp_path, module):
+    r = pins_against(oracle_copy(tmp_path), module)
     assert r.returncode == 0, r.stdout[-3000:]
 
 
 @pytest.mark.parametrize("mutant", MUTANTS, ids=[m[0].split(":")[0][:40] for m in MUTANTS])
 def test_planted_mistake_fails_a_pin(tmp_path, mutant):
     r = pins_against(oracle_copy(tmp_path, mutant))
+    assert r.returncode == 1 and " failed" in r.stdout, (mutant[0], r.returncode, r.stdout[-3000:])
+
+
+@pytest.mark.parametrize("mutant", LEARNED_MUTANTS, ids=[m[0][:40] for m in LEARNED_MUTANTS])
+def test_planted_mistake_in_the_learned_path_fails_a_pin(tmp_path, mutant):
+    r = pins_against(oracle_copy(tmp_path, mutant), "test_oracle_learned.py")
     assert r.returncode == 1 and " failed" in r.stdout, (mutant[0], r.returncode, r.stdout[-3000:])
