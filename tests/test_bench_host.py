@@ -1,0 +1,74 @@
+"""Host-side logic of bench.py that needs no GPU: the clock/throttle summary of the
+nvidia-smi samples, the DRAM-traffic record keyed by the kernel sources, the bounded
+oracle sample of the CPU baseline, the GPU index under CUDA_VISIBLE_DEVICES and the
+roofline peak."""
+import json
+import os
+
+import numpy as np
+
+import bench
+from paper_1212_0204_gb300 import workloads as W
+
+
+def test_clock_summary_takes_median_max_and_active_reasons():
+    c = bench.ClockSampler(0)
+    c.lines = [
+        "2070, 2070, Not Active, Not Active, Not Active, Not Active",
+        "2040, 2070, Not Active, Not Active, Not Active, Active",
+        "garbage line",
+        "1980, 2070, Not Active, Not Active, Not Active, Not Active",
+        "[N/A], 2070, Not Active, Not Active, Not Active, Not Active",
+    ]
+    s = c.summary()
+    assert s["sm_mhz"] == 2040.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 3
+
+
+def test_clock_summary_without_samples():
+    s = bench.ClockSampler(0).summary()
+    assert s == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_recorded_traffic_only_for_the_current_kernel_source(monkeypatch, tmp_path):
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "kinetic_pass_traffic.txt").write_text(
+        "# comment line\n"
+        "workload=quadrant_2d source=aaaaaaaaaaaaaaaa dram_bytes_per_launch=495203584\n"
+        "workload=density_wave_3d_64 source=bbbbbbbbbbbbbbbb dram_bytes_per_launch=28584552448\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kinetic_source_hash", lambda: "aaaaaaaaaaaaaaaa")
+    assert bench.recorded_traffic("quadrant_2d") == 495203584.0
+    assert bench.recorded_traffic("density_wave_3d_64") is None  # taken on other sources
+    assert bench.recorded_traffic("no_such_workload") is None
+
+
+def test_kinetic_source_hash_covers_the_kernel_sources():
+    h = bench.kinetic_source_hash()
+    assert len(h) == 16 and int(h, 16) >= 0
+
+
+def test_oracle_sample_is_bounded_and_keeps_the_velocity_grid():
+    case = W.quadrant_2d(n=256, nv=32, tau=1e-3, steps=500)
+    cases, what = bench.oracle_sample(case, 4e6)
+    (c,) = cases
+    assert c.nv == case.nv and c.dv == case.dv and c.tau == case.tau
+    assert c.points <= 1.1 * 4e6 and c.nx[0] < 256 and "cells" in what
+    tubes = W.batched_tubes(ncases=64, steps=2)
+    picked, what = bench.oracle_sample(tubes, 1e6)
+    pts = sum(t.points for t in picked)
+    assert picked == tubes[:len(picked)] and pts >= 1e6 and pts - picked[-1].points < 1e6
+
+
+def test_physical_gpu_index_follows_visible_devices(monkeypatch):
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "5,3")
+    assert bench.physical_gpu_index(0) == 5 and bench.physical_gpu_index(1) == 3
+    monkeypatch.delenv("CUDA_VISIBLE_DEVICES")
+    assert bench.physical_gpu_index(2) == 2
+
+
+def test_peak_is_the_measured_copy_bandwidth():
+    peak, kind = bench.load_peaks()
+    with open(os.path.join(bench.ROOT, "MEASURED_PEAKS.json")) as fh:
+        assert np.isclose(peak, float(json.load(fh)["hbm_gbs"]))
+    assert kind == "measured"
