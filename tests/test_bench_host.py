@@ -67,8 +67,10 @@ def test_physical_gpu_index_follows_visible_devices(monkeypatch):
     assert bench.physical_gpu_index(2) == 2
 
 
-def test_peak_is_the_measured_copy_bandwidth():
+def test_peak_is_the_measured_copy_bandwidth(monkeypatch, tmp_path):
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6769.4, "bf16_tflops": 1900.0}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     peak, kind = bench.load_peaks()
-    with open(os.path.join(bench.ROOT, "MEASURED_PEAKS.json")) as fh:
-        assert np.isclose(peak, float(json.load(fh)["hbm_gbs"]))
-    assert kind == "measured"
+    assert np.isclose(peak, 6769.4) and kind == "measured"
+    os.remove(tmp_path / "MEASURED_PEAKS.json")
+    assert bench.load_peaks() == (6800.0, "fallback")
