@@ -41,6 +41,8 @@ MUTANTS = [
      "riemann.c", "*r = rl * pow(ps / pl, 1.0 / gamma);", "*r = rl * pow(ps / pl, gamma);"),
     ("network gradient: 1 + tanh^2 instead of the derivative 1 - tanh^2",
      "mlp.c", "d1[i] = s2 * (1.0 - h1[i] * h1[i]);", "d1[i] = s2 * (1.0 + h1[i] * h1[i]);"),
+    ("network forward: second layer reads W2 transposed",
+     "mlp.c", "s += W2[j * NH + i] * h1[i];", "s += W2[i * NH + j] * h1[i];"),
 ]
 
 # the learned path: flagged step, non-equilibrium label, features

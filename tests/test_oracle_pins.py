@@ -481,6 +481,39 @@ def test_nonphysical_state_is_reported():
 # ------------------------------------------------------------------------- network
 
 
+def test_mlp_forward_special_cases():
+    """The 10-64-64-1 tanh network on parameter vectors that reduce it to scalar
+    compositions of tanh, one layer and one weight at a time: all weights zero gives
+    W3 . tanh(b2) + b3; a single non-zero weight per layer (W1[3][5] = a, W2[7][3] = c,
+    W3[7] = 1) gives tanh(c tanh(a x_5 + b1_3) + b2_7) + b3.  This fixes each layer's
+    matrix-vector product, the activation and the packed row-major layout
+    W1[64][10], b1[64], W2[64][64], b2[64], W3[64], b3."""
+    nin, nh = 10, 64
+    o_b1, o_w2 = nh * nin, nh * nin + nh
+    o_b2 = o_w2 + nh * nh
+    o_w3, o_b3 = o_b2 + nh, o_b2 + 2 * nh
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((5, nin))
+    P = np.zeros(o_b3 + 1)
+    P[o_b1:o_b1 + nh] = rng.standard_normal(nh)
+    P[o_b2:o_b2 + nh] = rng.standard_normal(nh)
+    P[o_w3:o_w3 + nh] = rng.standard_normal(nh)
+    P[o_b3] = 0.7
+    want = P[o_w3:o_w3 + nh] @ np.tanh(P[o_b2:o_b2 + nh]) + 0.7
+    np.testing.assert_allclose(oracle.mlp_forward(P, X), want, rtol=1e-14)
+    a, c, b13, b27 = 0.8, -1.3, 0.2, -0.4
+    P = np.zeros(o_b3 + 1)
+    P[3 * nin + 5] = a
+    P[o_b1 + 3] = b13
+    P[o_w2 + 7 * nh + 3] = c
+    P[o_b2 + 7] = b27
+    P[o_w3 + 7] = 1.0
+    P[o_b3] = 0.1
+    # every other hidden unit is tanh(0) = 0 in both layers, and only W3[7] is non-zero
+    want = np.tanh(c * np.tanh(a * X[:, 5] + b13) + b27) + 0.1
+    np.testing.assert_allclose(oracle.mlp_forward(P, X), want, rtol=1e-14)
+
+
 def test_mlp_gradient_matches_finite_differences():
     rng = np.random.default_rng(21)
     npar = 64 * 10 + 64 + 64 * 64 + 64 + 64 + 1
