@@ -1,9 +1,12 @@
 """CPU checks of the boundary: libdvm.so builds, loads without a GPU and exports
-every function include/dvm.h declares; the binding's list agrees with the header.
-No compute call is made here."""
+every function include/dvm.h declares; the binding's list agrees with the header;
+the header is plain C99 that a C program compiles (-pedantic -Werror) and links
+against libdvm.so.  No compute call is made here."""
 import ctypes
 import os
 import re
+import shutil
+import subprocess
 
 import pytest
 
@@ -56,3 +59,26 @@ def test_product_path_has_no_cpu_fallback():
         pytest.skip("GPU present")
     with pytest.raises(RuntimeError):
         dvm.Solver.from_case(workloads.sod_1d(nx=16, nv=8))
+
+
+def test_header_is_c99_and_a_c_program_links_and_calls_the_library(libdvm, tmp_path):
+    """tests/abi_check.c fills a dvm_config as a C program would and asks for the
+    workspace size (a host-only call): valid FP32/FP64 configs give the FP64 f twice
+    the f bytes of FP32 plus the same per-cell buffers; invalid ones give DVM_ERR_ARG."""
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    from paper_1212_0204_gb300 import build
+    libdir = os.path.dirname(build.build())
+    exe = tmp_path / "abi_check"
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                    "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "abi_check.c"),
+                    "-L", libdir, "-ldvm", "-Wl,-rpath," + libdir, "-lm", "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    rows = {ln.split()[0]: [int(v) for v in ln.split()[1:]] for ln in out if ln.strip()}
+    (rc32, b32), (rc64, b64) = rows["f32"], rows["f64"]
+    assert rc32 == 0 and rc64 == 0
+    f_bytes = 64 * 64 * 32 * 32
+    assert b32 >= 4 * f_bytes and b64 - b32 >= 4 * f_bytes
+    assert rows["bad_dim"][0] == -1 and rows["null"][0] == -1
+    assert rows["tau_inf"][0] == 0
