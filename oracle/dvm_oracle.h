@@ -3,7 +3,7 @@
  * scheme of Dimarco & Loubere, "Towards an ultra efficient kinetic scheme,
  * Part II: the high order case" (FKS of Section 4.2, HOFKS of Section 4.3).
  *
- * TEST INFRASTRUCTURE ONLY.  This code is the checker the GPU library is
+ * TEST INFRASTRUCTURE ONLY.  This code is the FP64 reference the GPU library is
  * compared against.  It is slow on purpose: every step is written in the
  * order the paper gives it, with no blocking, fusion or reordering, so that
  * it can be read against the paper line by line.  It shares no source with

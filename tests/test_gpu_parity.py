@@ -1,6 +1,6 @@
 """GPU-vs-oracle parity through the C ABI (libdvm.so via the ctypes binding).
 
-Tolerances (BASELINE the benchmark spec): shift indexing bit-exact; moments 1e-12 relative
+Tolerances: shift indexing bit-exact; moments 1e-12 relative
 in the FP64 build and 1e-5 relative in the FP32 build; BF16 storage reports its
 error against a stated bound.  A moment row's error is measured against
 max(|U_i|_inf, |rho|_inf): the scale of a sum of f_k m_k with |m_k| = O(1), which
