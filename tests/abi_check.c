@@ -48,5 +48,34 @@ int main(void) {
   printf("tau_inf %d %zu\n", rc, bytes);
   rc = dvm_workspace_bytes(NULL, &bytes);
   printf("null %d\n", rc);
+
+  /* degenerate and invalid configurations: each must give DVM_ERR_ARG */
+  c = quadrant(64, 32, DVM_F32); c.grid.nx[0] = 0;
+  printf("bad_empty_grid %d\n", dvm_workspace_bytes(&c, &bytes));
+  c = quadrant(64, 32, DVM_F32); c.vel.n[1] = 0;
+  printf("bad_no_velocities %d\n", dvm_workspace_bytes(&c, &bytes));
+  c = quadrant(64, 32, DVM_F32); c.grid.dx = 0.0;
+  printf("bad_dx %d\n", dvm_workspace_bytes(&c, &bytes));
+  c = quadrant(64, 32, DVM_F32); c.vel.dv = -0.4;
+  printf("bad_dv %d\n", dvm_workspace_bytes(&c, &bytes));
+  c = quadrant(64, 32, DVM_F32); c.vel.shift_den = 0;
+  printf("bad_shift_den %d\n", dvm_workspace_bytes(&c, &bytes));
+  c = quadrant(64, 32, DVM_F32); c.tau = -1.0;
+  printf("bad_tau %d\n", dvm_workspace_bytes(&c, &bytes));
+  c = quadrant(64, 32, DVM_F32); c.tau = NAN;
+  printf("bad_tau_nan %d\n", dvm_workspace_bytes(&c, &bytes));
+  c = quadrant(64, 32, DVM_F32); c.bc[1][1] = DVM_BC_OUTFLOW;
+  printf("bad_faces %d\n", dvm_workspace_bytes(&c, &bytes));
+  c = quadrant(64, 32, DVM_F32); c.scheme = 7;
+  printf("bad_scheme %d\n", dvm_workspace_bytes(&c, &bytes));
+  c = quadrant(64, 32, DVM_F32); c.precision = 9;
+  printf("bad_precision %d\n", dvm_workspace_bytes(&c, &bytes));
+  c = quadrant(8, 258, DVM_F32);
+  printf("bad_too_many_velocities %d\n", dvm_workspace_bytes(&c, &bytes));
+  c = quadrant(64, 32, DVM_F32); c.grid.nx[2] = 2;
+  printf("bad_unused_dimension %d\n", dvm_workspace_bytes(&c, &bytes));
+  /* the largest velocity grid per dimension is accepted */
+  c = quadrant(8, 256, DVM_F32);
+  printf("max_velocities %d\n", dvm_workspace_bytes(&c, &bytes));
   return 0;
 }

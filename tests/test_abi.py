@@ -64,7 +64,10 @@ def test_product_path_has_no_cpu_fallback():
 def test_header_is_c99_and_a_c_program_links_and_calls_the_library(libdvm, tmp_path):
     """tests/abi_check.c fills a dvm_config as a C program would and asks for the
     workspace size (a host-only call): valid FP32/FP64 configs give the FP64 f twice
-    the f bytes of FP32 plus the same per-cell buffers; invalid ones give DVM_ERR_ARG."""
+    the f bytes of FP32 plus the same per-cell buffers; degenerate and invalid ones
+    (empty grid, no velocities, dx = 0, dv < 0, shift_den = 0, tau < 0 or NaN,
+    mismatched faces, unknown scheme or precision, more than 256 velocities per
+    dimension, a non-unit unused dimension) give DVM_ERR_ARG; 256 is accepted."""
     gcc = shutil.which("gcc")
     if gcc is None:
         pytest.skip("no C compiler")
@@ -82,3 +85,6 @@ def test_header_is_c99_and_a_c_program_links_and_calls_the_library(libdvm, tmp_p
     assert b32 >= 4 * f_bytes and b64 - b32 >= 4 * f_bytes
     assert rows["bad_dim"][0] == -1 and rows["null"][0] == -1
     assert rows["tau_inf"][0] == 0
+    bad = {k: v[0] for k, v in rows.items() if k.startswith("bad_")}
+    assert len(bad) == 13 and all(v == -1 for v in bad.values()), bad
+    assert rows["max_velocities"][0] == 0
