@@ -220,6 +220,47 @@ def time_oracle(cases, steps: int, warmup: int = 0):
     return total_pts / secs, secs
 
 
+def moment_err(Ug, Uo) -> float:
+    """Largest relative moment error; each row scaled by max(|U_i|_inf, |rho|_inf)."""
+    scale = np.maximum(np.abs(Uo).max(axis=1), np.abs(Uo[0]).max())
+    return float((np.abs(Ug - Uo).max(axis=1) / scale).max())
+
+
+def precision_error(dvm, sample, precision, batch: bool, steps: int = 2):
+    """The error of the bench's precision tier against the FP64 oracle, stated with
+    the result: the library at that precision and the oracle advance the same bounded
+    sample of the workload from the same initial moments for `steps` steps; the
+    largest relative moment error over the sample's cases."""
+    import oracle
+    from tests.helpers import grid
+    cases = sample[:8]
+    ref = []
+    for c in cases:
+        o = oracle.Scheme(grid(c), tau=c.tau)
+        o.set_moments(conserved(c))
+        o.step(steps)
+        ref.append(o.moments())
+    if batch:
+        b = dvm.Batch(cases, precision=precision)
+        b.set_moments(b.pack([conserved(c) for c in cases]))
+        b.step(steps)
+        U = b.moments()
+        got = [b.case_moments(U, i) for i in range(len(cases))]
+        kernel = "batch"
+        b.close()
+    else:
+        got = []
+        for c in cases:
+            s = dvm.Solver.from_case(c, precision=precision)
+            s.set_moments(conserved(c))
+            s.step(steps)
+            got.append(s.moments())
+            kernel = s.kinetic_kernel()
+            s.close()
+    return {"max_rel_moment_err": max(moment_err(g, r) for g, r in zip(got, ref)),
+            "steps": steps, "cases": len(cases), "kinetic_kernel": kernel}
+
+
 def run_reference(args, case, descr, rank):
     """Reference arm: the FP64 CPU oracle, untuned, on bounded samples of the workload."""
     if rank != 0:
@@ -493,6 +534,13 @@ def main():
         v, secs = time_oracle(sample, steps=max(1, int(round(15.0 * 2e7 / pts))))
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{what}, {secs:.1f} s of single-thread FP64 oracle"}
+        try:
+            err = precision_error(dvm, sample, precision, job.batch)
+            err["sample"] = what
+        except Exception as e:  # the stated error is a report, not part of the timing
+            err = {"unavailable": f"{type(e).__name__}: {e}"}
+    else:
+        err = None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -506,6 +554,7 @@ def main():
                      "peak_source": peak_kind,
                      "kernel_ms": kin_ms, "bytes_per_launch": bytes_alg},
         "cpu_baseline": cpu,
+        "error_vs_oracle": err,
         "e2e": e2e,
         "gpu_launches": launches * args.steps,
         "clocks": clk.summary(),

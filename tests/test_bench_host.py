@@ -74,3 +74,57 @@ def test_peak_is_the_measured_copy_bandwidth(monkeypatch, tmp_path):
     assert np.isclose(peak, 6769.4) and kind == "measured"
     os.remove(tmp_path / "MEASURED_PEAKS.json")
     assert bench.load_peaks() == (6800.0, "fallback")
+
+
+class _FakeSolver:
+    """Stand-in for dvm.Solver on the CPU: advances with the oracle and adds a
+    planted relative error `eps` to the density row."""
+    eps = 0.0
+
+    def __init__(self, case):
+        import oracle
+        from tests.helpers import grid
+        self.o = oracle.Scheme(grid(case), tau=case.tau)
+
+    @classmethod
+    def from_case(cls, case, precision=None):
+        return cls(case)
+
+    def set_moments(self, U):
+        self.o.set_moments(U)
+
+    def step(self, n):
+        self.o.step(n)
+
+    def moments(self):
+        U = self.o.moments()
+        U[0] *= 1.0 + self.eps
+        return U
+
+    def kinetic_kernel(self):
+        return "fake"
+
+    def close(self):
+        pass
+
+
+class _FakeDvm:
+    Solver = _FakeSolver
+
+
+def test_precision_error_reports_the_moment_error_against_the_oracle():
+    case = W.quadrant_2d(n=256, nv=16, tau=1e-3, steps=500)
+    sample, what = bench.oracle_sample(case, 2e5)
+    _FakeSolver.eps = 0.0
+    r = bench.precision_error(_FakeDvm, sample, None, batch=False)
+    assert r["max_rel_moment_err"] == 0.0 and r["kinetic_kernel"] == "fake" and r["steps"] == 2
+    _FakeSolver.eps = 3e-6
+    r = bench.precision_error(_FakeDvm, sample, None, batch=False)
+    assert np.isclose(r["max_rel_moment_err"], 3e-6, rtol=1e-6)
+
+
+def test_moment_error_scales_rows_by_density():
+    Uo = np.array([[1.0, 2.0], [1e-9, -1e-9], [3.0, 3.0]])
+    Ug = Uo.copy()
+    Ug[1, 0] += 1e-6  # a near-zero momentum row is measured against |rho|_inf = 2
+    assert np.isclose(bench.moment_err(Ug, Uo), 5e-7)
