@@ -101,6 +101,9 @@ class _FakeSolver:
         U[0] *= 1.0 + self.eps
         return U
 
+    def f(self):
+        return self.o.f() * (1.0 + self.eps)
+
     def kinetic_kernel(self):
         return "fake"
 
@@ -117,10 +120,12 @@ def test_precision_error_reports_the_moment_error_against_the_oracle():
     sample, what = bench.oracle_sample(case, 2e5)
     _FakeSolver.eps = 0.0
     r = bench.precision_error(_FakeDvm, sample, None, batch=False)
-    assert r["max_rel_moment_err"] == 0.0 and r["kinetic_kernel"] == "fake" and r["steps"] == 2
+    assert r["max_rel_moment_err"] == 0.0 and r["max_rel_f_err"] == 0.0
+    assert r["kinetic_kernel"] == "fake" and r["steps"] == 2
     _FakeSolver.eps = 3e-6
     r = bench.precision_error(_FakeDvm, sample, None, batch=False)
     assert np.isclose(r["max_rel_moment_err"], 3e-6, rtol=1e-6)
+    assert np.isclose(r["max_rel_f_err"], 3e-6, rtol=1e-6)
 
 
 def test_moment_error_scales_rows_by_density():
