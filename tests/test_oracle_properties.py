@@ -8,8 +8,12 @@ free-transport limit, per-cell tau fields and several steps.
 * tau = inf is exact transport (Section 4.2): f^n is f^0 moved by the offsets, bit for
   bit, and the moments are C f^n;
 * a uniform equilibrium is a fixed point (Section 4.1): one step changes nothing
-  beyond rounding.
+  beyond rounding;
+* the offsets are the exact piece geometry for random k, n and p (reading R1);
+* the exact Riemann solution satisfies the textbook relations for random states.
 """
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
@@ -107,3 +111,63 @@ def test_uniform_equilibrium_is_a_fixed_point_on_random_configurations(cfg, log_
     s.step(1)
     np.testing.assert_allclose(s.moments(), U0, rtol=1e-12, atol=1e-14)
     np.testing.assert_allclose(s.f(), f0, rtol=1e-11, atol=1e-14 * np.abs(f0).max())
+
+
+def piece_owner(c, shift):
+    """The piece j whose interval (j - 1/2 + shift, j + 1/2 + shift] (cell units)
+    contains the centre of cell c, by search over the candidates near c - shift."""
+    base = c - int(shift)
+    hits = [j for j in range(base - 3, base + 4)
+            if Fraction(j) - Fraction(1, 2) + shift < c <= Fraction(j) + Fraction(1, 2) + shift]
+    assert len(hits) == 1
+    return hits[0]
+
+
+@settings(max_examples=300, deadline=None, derandomize=True)
+@given(k=st.integers(-300, 300), n=st.integers(0, 1000), p=st.integers(1, 50))
+def test_offset_is_the_exact_piece_geometry_for_random_k_n_p(k, n, p):
+    """Section 4.2 (reading R1): after n steps the pieces of velocity k have moved by
+    k n / p cells; the offset is the cell minus the index of the piece over it."""
+    assert 7 - piece_owner(7, Fraction(k * n, p)) == oracle.offset(k, n, p)
+
+
+@st.composite
+def riemann_states(draw):
+    gamma = draw(st.sampled_from([1.4, 5.0 / 3.0, 2.0, 3.0]))
+    side = lambda: (draw(st.floats(0.5, 2.0)), draw(st.floats(-0.5, 0.5)), draw(st.floats(0.3, 2.0)))
+    return gamma, side(), side()
+
+
+@settings(max_examples=60, deadline=None, derandomize=True)
+@given(st_=riemann_states())
+def test_exact_riemann_solution_relations_for_random_states(st_):
+    """Textbook relations of the exact solution for random states and gamma:
+    u and p continuous at the contact; Rankine-Hugoniot across a shock (three
+    conservation laws with the shock speed from the mass jump); constant entropy
+    p / rho^gamma across a rarefaction and in the star state behind it."""
+    gamma, left, right = st_
+    xi = np.linspace(-6, 6, 60001)
+    r, u, p, ps, us = oracle.riemann_exact(gamma, left, right, xi)
+    assert ps > 0 and np.all(r > 0) and np.all(p > 0)
+    near = np.abs(xi - us) < 2e-3
+    np.testing.assert_allclose(u[near], us, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(p[near], ps, rtol=1e-10)
+    E = lambda r_, u_, p_: p_ / (gamma - 1) + 0.5 * r_ * u_ ** 2
+    flux = lambda r_, u_, p_: np.array([r_ * u_, r_ * u_ ** 2 + p_, (E(r_, u_, p_) + p_) * u_])
+    cons = lambda r_, u_, p_: np.array([r_, r_ * u_, E(r_, u_, p_)])
+    for sgn, (rk, uk, pk) in ((-1, left), (1, right)):
+        # the star state of this side, just beside the contact
+        rs = r[np.argmin(np.abs(xi - us)) + 5 * sgn]
+        if ps > pk * (1 + 1e-6):
+            S = (rs * us - rk * uk) / (rs - rk)
+            np.testing.assert_allclose(flux(rs, us, ps) - flux(rk, uk, pk),
+                                       S * (cons(rs, us, ps) - cons(rk, uk, pk)),
+                                       rtol=1e-8, atol=1e-10)
+        elif ps < pk * (1 - 1e-6):
+            np.testing.assert_allclose(ps / rs ** gamma, pk / rk ** gamma, rtol=1e-10)
+            cs = np.sqrt(gamma * pk / rk)
+            head = uk + sgn * cs
+            tail = us + sgn * np.sqrt(gamma * ps / rs)
+            lo, hi = sorted((head, tail))
+            fan = (xi > lo + 1e-3) & (xi < hi - 1e-3)
+            np.testing.assert_allclose(p[fan] / r[fan] ** gamma, pk / rk ** gamma, rtol=1e-10)
