@@ -133,3 +133,33 @@ def test_moment_error_scales_rows_by_density():
     Ug = Uo.copy()
     Ug[1, 0] += 1e-6  # a near-zero momentum row is measured against |rho|_inf = 2
     assert np.isclose(bench.moment_err(Ug, Uo), 5e-7)
+
+
+def _run_bench(args, env_extra=None):
+    import subprocess
+    import sys
+    env = dict(os.environ, **(env_extra or {}))
+    return subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py")] + args,
+                          cwd=bench.ROOT, env=env, capture_output=True, text=True, timeout=300)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference: the untuned FP64 oracle on the host, one JSON line with
+    the arm's metric and unit, at least 3 warm-up steps, and cpu_baseline / e2e
+    describing the same run (no host-device copies)."""
+    r = _run_bench(["--impl", "reference", "--workload", "sod_1d", "--steps", "2", "--warmup", "1"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["value"] > 0 and line["steps"] == 2 and line["warmup"] == 3
+    assert line["higher_is_better"] is True and line["dtype"] == "f64"
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT,
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    r = _run_bench(["--impl", "reference", "--workload", "sod_1d", "--steps", "2"],
+                   {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert r.returncode == 0 and r.stdout.strip() == ""
