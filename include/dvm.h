@@ -52,6 +52,9 @@ typedef enum {
 
 /* Size of the fixed device scratch array used by dvm_equilibrium_noalloc. */
 #define DVM_NOALLOC_SCRATCH_BYTES (8u << 20)
+/* Bytes at the start of that array before the per-cell parameters (status
+ * word and (C C^T)^{-1}). */
+#define DVM_NOALLOC_HEADER_BYTES 512u
 
 typedef enum { DVM_BC_PERIODIC = 0, DVM_BC_OUTFLOW = 1 } dvm_bc;
 typedef enum { DVM_FKS = 0, DVM_HOFKS = 1, DVM_HOFKS_UNLIMITED = 2 } dvm_scheme;
@@ -202,6 +205,12 @@ int dvm_launches_per_step(dvm_handle* h, int* launches);
  * whole x rows moved by tensor copies through shared memory). */
 enum { DVM_KPASS_GENERIC = 0, DVM_KPASS_WINDOW = 1, DVM_KPASS_ROWS = 2 };
 int dvm_kinetic_kernel(const dvm_handle* h, int* kind);
+
+/* Velocity chunks of the kinetic pass (chosen at dvm_create from the grid and
+ * the SM count): the velocity loop of every target cell is split over this
+ * many CTAs, each writing its own FP64 partial moment sums, which the
+ * end-of-step kernel adds (Eq. DM summed in parts).  1 = no split. */
+int dvm_kinetic_splits(const dvm_handle* h, int* splits);
 
 /* Kinetic-pass timing.  Between dvm_profile_begin and dvm_profile_end the
  * steps are enqueued launch by launch (not through the graph) with a pair of
@@ -401,9 +410,10 @@ int dvm_mlp_train(dvm_mlp* m, long long n, const float* X, const float* t,
  *   f:      device pointer, N_v x N_c FP64 output (velocity-major, cell
  *           positions), caller-owned.
  *   stream: cudaStream_t or NULL; the call synchronises it before returning.
- * Size limit: 256 + 8 N_c (P + 1) bytes must fit in the scratch, P the padded
- * count of per-cell parameter rows (12 in 1D, 16 in 2D and 3D), i.e. at most
- * 61679 cells in 2D or 3D and 80657 in 1D; larger problems return
+ * Size limit: DVM_NOALLOC_HEADER_BYTES + 8 N_c (P + 1) bytes must fit in the
+ * scratch, P the padded count of per-cell parameter rows (12 in 1D, 16 in 2D
+ * and 3D), i.e. at most 61677 cells in 2D or 3D and 80654 in 1D; larger
+ * problems return
  * DVM_ERR_TOO_LARGE without launching anything.  Returns DVM_ERR_NONPHYSICAL
  * or DVM_ERR_NONFINITE for bad moments, DVM_ERR_CUDA if a CUDA call fails.
  * The first call on each device looks up the device address of the scratch

@@ -813,6 +813,12 @@ int dvm_kinetic_kernel(const dvm_handle* h, int* kind) {
   return 0;
 }
 
+int dvm_kinetic_splits(const dvm_handle* h, int* splits) {
+  if (!h || !splits) return DVM_ERR_ARG;
+  *splits = h->g.nsplit;
+  return 0;
+}
+
 }  // extern "C"
 
 // ------------------------------------------------------------ learned path

@@ -110,6 +110,60 @@ __global__ void k_init_f(Geom g, DevPtrs p) {
   StoreT<TS>::store((TS*)p.F + k * nc + c, f);
 }
 
+// f^0 = E[U^0] for FP32/BF16 storage, the same FP32 arithmetic as k_init_f:
+// one thread per cell converts the cell's FP64 equilibrium parameters once
+// and writes a chunk of velocities (blockIdx.y), consecutive threads writing
+// consecutive cells of each velocity row; the velocity components come from
+// a shared table.  The write of f (4 or 2 bytes a point) is the bound.
+template <typename TS, int D>
+__global__ void __launch_bounds__(kBlock) k_init_f_rows(Geom g, DevPtrs p, int kchunk) {
+  __shared__ float s_v[kMaxD][kMaxV1];
+  for (int t = threadIdx.x; t < D * kMaxV1; t += blockDim.x) {
+    const int i = t / kMaxV1, kk = t % kMaxV1;
+    if (kk < g.nv[i]) s_v[i][kk] = (float)((double)(g.kmin[i] + kk) * g.dv);
+  }
+  __syncthreads();
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= g.nc) return;
+  const long long nc = g.nc;
+  const double* prm = p.eqp;
+  float u[3], m[kMaxD];
+  const float L = (float)prm[prm_at(row_L(), c, nc)], h = (float)prm[prm_at(row_h(D), c, nc)];
+  const float mu0 = (float)prm[prm_at(row_mu(D, 0), c, nc)];
+  const float mu4 = (float)prm[prm_at(row_mu(D, D + 1), c, nc)];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    u[i] = (float)prm[prm_at(row_u(i), c, nc)];
+    m[i] = (float)prm[prm_at(row_mu(D, 1 + i), c, nc)];
+  }
+  const long long kb = (long long)blockIdx.y * kchunk;
+  const long long ke = kb + kchunk < g.nvel ? kb + kchunk : g.nvel;
+  int kk[3] = {(int)(kb % g.nv[0]), D > 1 ? (int)((kb / g.nv[0]) % g.nv[1]) : 0,
+               D > 2 ? (int)(kb / ((long long)g.nv[0] * g.nv[1])) : 0};
+  TS* F = (TS*)p.F + c;
+  for (long long k = kb; k < ke; ++k) {
+    float q = 0.f, vv = 0.f, lin = mu0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const float v = s_v[i][kk[i]];
+      const float du = v - u[i];
+      q += du * du;
+      vv += v * v;
+      lin += m[i] * v;
+    }
+    lin += mu4 * vv;
+    const float e = L - h * q;
+    StoreT<TS>::store(F + k * nc, exp2f(e) + lin);
+    if (++kk[0] == g.nv[0]) {
+      kk[0] = 0;
+      if (D > 1 && ++kk[1] == g.nv[1]) {
+        kk[1] = 0;
+        if (D > 2) ++kk[2];
+      }
+    }
+  }
+}
+
 template <int D>
 __global__ void k_prim_to_cons(Geom g, const double* rho, const double* u, const double* T,
                                double* U) {
@@ -907,13 +961,23 @@ void launch_cell_params(const Geom& g, const DevPtrs& p, int mode, int initial, 
 }
 
 void launch_init_f(const Geom& g, const DevPtrs& p, cudaStream_t s) {
-  const unsigned nb = blocks_for(g.nc * g.nvel);
-  if (g.precision == DVM_F64)
+  if (g.precision == DVM_F64) {
+    const unsigned nb = blocks_for(g.nc * g.nvel);
     DVM_BY_DIM(g, (k_init_f<double, DD><<<nb, kBlock, 0, s>>>(g, p)));
-  else if (g.precision == DVM_F32)
-    DVM_BY_DIM(g, (k_init_f<float, DD><<<nb, kBlock, 0, s>>>(g, p)));
+    return;
+  }
+  // FP32 / BF16: per-cell threads over velocity chunks of about 64 rows
+  // (at least a few waves of CTAs on 152 SMs for small grids)
+  const long long cb = blocks_for(g.nc);
+  long long chunks = (g.nvel + 63) / 64;
+  if (chunks > 65535) chunks = 65535;  // grid y limit
+  const int kchunk = (int)((g.nvel + chunks - 1) / chunks);
+  chunks = (g.nvel + kchunk - 1) / kchunk;
+  const dim3 grid((unsigned)cb, (unsigned)chunks);
+  if (g.precision == DVM_F32)
+    DVM_BY_DIM(g, (k_init_f_rows<float, DD><<<grid, kBlock, 0, s>>>(g, p, kchunk)));
   else
-    DVM_BY_DIM(g, (k_init_f<__nv_bfloat16, DD><<<nb, kBlock, 0, s>>>(g, p)));
+    DVM_BY_DIM(g, (k_init_f_rows<__nv_bfloat16, DD><<<grid, kBlock, 0, s>>>(g, p, kchunk)));
 }
 
 void launch_alpha(const Geom& g, const DevPtrs& p, cudaStream_t s) {
@@ -992,6 +1056,15 @@ namespace {
 
 constexpr size_t kNoAllocBytes = DVM_NOALLOC_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+// Fixed header: the status word at 0, the largest (C C^T)^{-1} (kMaxM^2
+// doubles) from kNoAllocA, and the per-cell parameters from the next 256-byte
+// boundary after it.  The three regions must not overlap: the parameter
+// kernel writes cell 0's rows while other blocks still read the matrix.
+constexpr size_t kNoAllocA = 64;
+constexpr size_t kNoAllocHeader = DVM_NOALLOC_HEADER_BYTES;
+static_assert(kNoAllocA + sizeof(double) * kMaxM * kMaxM <= kNoAllocHeader,
+              "(C C^T)^{-1} must end before the per-cell parameters start");
+static_assert(kNoAllocHeader % 256 == 0, "per-cell parameters start on a 256-byte boundary");
 
 std::mutex g_noalloc_mutex;
 void* g_noalloc_addr[256] = {};
@@ -1024,10 +1097,11 @@ extern "C" int dvm_equilibrium_noalloc(const dvm_config* cfg, const double* U, d
   std::string msg;
   if (make_geom(cfg, &g, &msg) != 0 || !U || !f) return DVM_ERR_ARG;
   g.precision = DVM_F64;  // FP64 output, FP64 parameters
-  // scratch layout: [0, 256) status word and (C C^T)^{-1}; then the
-  // equilibrium parameters (prm_rows x Nc); then Nc doubles read as lambda
+  // scratch layout: the status word at 0, (C C^T)^{-1} from kNoAllocA; the
+  // equilibrium parameters (prm_rows x Nc) from kNoAllocHeader; then Nc
+  // doubles read as lambda
   const size_t nc = (size_t)g.nc;
-  const size_t need = 256 + 8 * (size_t)prm_rows(g.d) * nc + 8 * nc;
+  const size_t need = kNoAllocHeader + 8 * (size_t)prm_rows(g.d) * nc + 8 * nc;
   if (need > kNoAllocBytes) return DVM_ERR_TOO_LARGE;
   double A[kMaxM * kMaxM];
   if (invert_moment_matrix(g, A) != 0) return DVM_ERR_ARG;
@@ -1038,8 +1112,8 @@ extern "C" int dvm_equilibrium_noalloc(const dvm_config* cfg, const double* U, d
   memset(&p, 0, sizeof p);
   char* b = (char*)base;
   p.status = (int*)b;
-  p.A = (double*)(b + 64);
-  p.eqp = (double*)(b + 256);
+  p.A = (double*)(b + kNoAllocA);
+  p.eqp = (double*)(b + kNoAllocHeader);
   p.lam = p.eqp + (size_t)prm_rows(g.d) * nc;
   p.U = const_cast<double*>(U);
   p.F = f;

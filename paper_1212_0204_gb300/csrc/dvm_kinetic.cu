@@ -210,7 +210,8 @@ bool window_eligible(const Geom& g) {
     if (g.bc[i] != DVM_BC_PERIODIC) return false;
   // 32-bit cell indices; rows wrap with one subtraction; the S warps of a
   // CTA end every kz plane in the same round
-  return g.nv[1] % kWinY == 0 && g.nv[0] % win_warps(g.d) == 0 && g.nx[1] >= kWinY && g.nc < (1LL << 31);
+  const int Y = win_y(g.d);
+  return g.nv[1] % Y == 0 && g.nv[0] % win_warps(g.d) == 0 && g.nx[1] >= Y && g.nc < (1LL << 31);
 }
 
 int sm_count() {
@@ -229,9 +230,10 @@ int sm_count() {
 // ceil(tiles c / R) / c with R the resident CTAs, so that the last wave is
 // nearly full; ties go to the larger c (finer load balance).
 WinLaunch window_shape(const Geom& g) {
-  const long long tiles = ((g.nx[0] + 31) / 32) * ((g.nx[1] + kWinY - 1) / kWinY) * g.nx[2];
+  const int Y = win_y(g.d);
+  const long long tiles = ((g.nx[0] + 31) / 32) * ((g.nx[1] + Y - 1) / Y) * g.nx[2];
   const long long resident = (long long)sm_count() * (g.d == 3 ? WinShape<3>::MINB : WinShape<2>::MINB);
-  const long long cta_updates = 32LL * kWinY * g.nvel;
+  const long long cta_updates = 32LL * Y * g.nvel;
   const int units = g.d == 3 ? g.nv[2] : g.nv[0] / win_warps(g.d);
   int sp = 1;
   double best = 1e30;
@@ -265,17 +267,18 @@ void launch_window_a(const Geom& g, const DevPtrs& p, const WinLaunch& wl, cudaS
   }
   constexpr size_t sm = window_smem(D, HO, AS);
   if (prepare) {
-    cudaFuncSetAttribute(k_kpass_window<TS, D, kWinY, HO, AS, false>,
+    cudaFuncSetAttribute(k_kpass_window<TS, D, WinShape<D>::Y, HO, AS, false>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k_kpass_window<TS, D, kWinY, HO, AS, true>,
+    cudaFuncSetAttribute(k_kpass_window<TS, D, WinShape<D>::Y, HO, AS, true>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     return;
   }
-  dim3 grid((unsigned)((g.nx[0] + 31) / 32), (unsigned)((g.nx[1] + kWinY - 1) / kWinY),
+  constexpr int Y = WinShape<D>::Y;
+  dim3 grid((unsigned)((g.nx[0] + 31) / 32), (unsigned)((g.nx[1] + Y - 1) / Y),
             (unsigned)(g.nx[2] * wl.splits));
   constexpr int T = 32 * WinShape<D>::S;
-  if (g.learn) k_kpass_window<TS, D, kWinY, HO, AS, true><<<grid, T, sm, s>>>(g, p, wl);
-  else k_kpass_window<TS, D, kWinY, HO, AS, false><<<grid, T, sm, s>>>(g, p, wl);
+  if (g.learn) k_kpass_window<TS, D, Y, HO, AS, true><<<grid, T, sm, s>>>(g, p, wl);
+  else k_kpass_window<TS, D, Y, HO, AS, false><<<grid, T, sm, s>>>(g, p, wl);
 }
 
 template <typename TS, int D, bool HO>

@@ -18,7 +18,8 @@ bool try_shape(const Geom& g, const DevPtrs& p, int splits, cudaStream_t s, bool
   if (g.nv[0] != CV || g.nv[1] != CV || (D == 3 && g.nv[2] != CV)) return false;
   if (!prepare && (g.learn != 0) != LE) return false;
   constexpr size_t sm = window_smem(D, true, true);
-  auto* k = k_kpass_window<float, D, kWinY, true, true, LE, CX, CY, CZ, CV>;
+  constexpr int Y = WinShape<D>::Y;
+  auto* k = k_kpass_window<float, D, Y, true, true, LE, CX, CY, CZ, CV>;
   if (prepare) {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     return true;
@@ -26,7 +27,7 @@ bool try_shape(const Geom& g, const DevPtrs& p, int splits, cudaStream_t s, bool
   WinLaunch wl;
   wl.S = WinShape<D>::S;
   wl.splits = splits;
-  const dim3 grid((unsigned)((CX + 31) / 32), (unsigned)((CY + kWinY - 1) / kWinY),
+  const dim3 grid((unsigned)((CX + 31) / 32), (unsigned)((CY + Y - 1) / Y),
                   (unsigned)((D == 3 ? CZ : 1) * splits));
   k<<<grid, 32 * WinShape<D>::S, sm, s>>>(g, p, wl);
   return true;

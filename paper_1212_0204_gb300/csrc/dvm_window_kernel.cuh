@@ -60,16 +60,42 @@ struct WinLaunch {
 // Shape of the windowed pass per dimension, measured on GB300: warps per CTA
 // (each on every S-th velocity pair; their parameter loads share L1 lines),
 // resident CTAs per SM it is compiled for (register cap 65536 / (32 S MINB)),
-// and how many of the four parameter groups of the next source row are loaded
+// how many of the four parameter groups of the next source row are loaded
 // a step ahead of their fold (the others at fold time: more in flight costs
-// registers).
+// registers), and the targets (consecutive y cells) per thread.  The DVM_W2_*
+// / DVM_W3_* macros override them at compile time (shape sweeps).
+#ifndef DVM_W2_S
+#define DVM_W2_S 8
+#endif
+#ifndef DVM_W2_MINB
+#define DVM_W2_MINB 2
+#endif
+#ifndef DVM_W2_EARLY
+#define DVM_W2_EARLY 2
+#endif
+#ifndef DVM_W2_Y
+#define DVM_W2_Y 4
+#endif
+#ifndef DVM_W3_S
+#define DVM_W3_S 4
+#endif
+#ifndef DVM_W3_MINB
+#define DVM_W3_MINB 3
+#endif
+#ifndef DVM_W3_EARLY
+#define DVM_W3_EARLY 1
+#endif
+#ifndef DVM_W3_Y
+#define DVM_W3_Y 4
+#endif
 template <int D> struct WinShape {
-  static constexpr int S = 8, MINB = 2, EARLY = 2;
+  static constexpr int S = DVM_W2_S, MINB = DVM_W2_MINB, EARLY = DVM_W2_EARLY, Y = DVM_W2_Y;
 };
 template <> struct WinShape<3> {
-  static constexpr int S = 4, MINB = 3, EARLY = 1;
+  static constexpr int S = DVM_W3_S, MINB = DVM_W3_MINB, EARLY = DVM_W3_EARLY, Y = DVM_W3_Y;
 };
 int win_warps(int d) { return d == 3 ? WinShape<3>::S : WinShape<2>::S; }
+int win_y(int d) { return d == 3 ? WinShape<3>::Y : WinShape<2>::Y; }
 
 // CTA = S warps on the same 32 x Y targets; warp s takes the velocity pairs
 // pb + s, pb + s + S, ...: at any time the warps read source rows shifted by
@@ -402,15 +428,11 @@ __global__ void __launch_bounds__(32 * WinShape<D>::S, WinShape<D>::MINB)
   }
 }
 
-#ifndef DVM_WIN_Y
-#define DVM_WIN_Y 4
-#endif
-constexpr int kWinY = DVM_WIN_Y;  // targets (consecutive y cells) per thread
-
 constexpr size_t window_smem(int d, bool hofks, bool async) {
   const size_t t = 32 * (d == 3 ? WinShape<3>::S : WinShape<2>::S);
-  return (size_t)(hofks ? 2 : 1) * (d + 2) * kWinY * (32 * sizeof(double) + t * sizeof(float)) +
-         (async ? (size_t)2 * kWinY * kWinY * t * sizeof(float) : 0);
+  const size_t y = d == 3 ? WinShape<3>::Y : WinShape<2>::Y;
+  return (size_t)(hofks ? 2 : 1) * (d + 2) * y * (32 * sizeof(double) + t * sizeof(float)) +
+         (async ? (size_t)2 * y * y * t * sizeof(float) : 0);
 }
 
 }  // namespace

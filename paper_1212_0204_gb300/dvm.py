@@ -29,7 +29,7 @@ EXPORTS = [
     "dvm_workspace_bytes", "dvm_create", "dvm_destroy", "dvm_set_stream", "dvm_last_error",
     "dvm_set_state_moments", "dvm_set_state_primitive", "dvm_step", "dvm_step_async",
     "dvm_sync_status", "dvm_moments", "dvm_moments_async", "dvm_moments_wait", "dvm_get_f", "dvm_last_parts", "dvm_info", "dvm_offsets",
-    "dvm_save", "dvm_load", "dvm_launches_per_step", "dvm_kinetic_kernel", "dvm_profile_begin",
+    "dvm_save", "dvm_load", "dvm_launches_per_step", "dvm_kinetic_kernel", "dvm_kinetic_splits", "dvm_profile_begin",
     "dvm_profile_end",
     "dvm_equilibrium_noalloc", "dvm_selftest_timeout",
     "dvm_batch_create", "dvm_batch_destroy", "dvm_batch_last_error", "dvm_batch_sizes",
@@ -126,6 +126,7 @@ def lib():
         L.dvm_load.argtypes = [vp, vp, C.c_size_t]
         L.dvm_launches_per_step.argtypes = [vp, C.POINTER(C.c_int)]
         L.dvm_kinetic_kernel.argtypes = [vp, C.POINTER(C.c_int)]
+        L.dvm_kinetic_splits.argtypes = [vp, C.POINTER(C.c_int)]
         L.dvm_profile_begin.argtypes = [vp]
         L.dvm_profile_end.argtypes = [vp, dp, C.POINTER(C.c_int)]
         L.dvm_equilibrium_noalloc.argtypes = [C.POINTER(_Config), vp, vp, vp]
@@ -404,6 +405,12 @@ class Solver:
         k = C.c_int()
         self._check(lib().dvm_kinetic_kernel(self._h, C.byref(k)))
         return ("generic", "window", "rows")[k.value]
+
+    def kinetic_splits(self) -> int:
+        """Velocity chunks of the kinetic pass (CTAs per target tile)."""
+        k = C.c_int()
+        self._check(lib().dvm_kinetic_splits(self._h, C.byref(k)))
+        return k.value
 
     # --------------------------------------------------- learned regime path
     def learn_enable(self, mode=LEARN_GIVEN, mlp_precision=F32, thr=-3.0, check_every=0,
