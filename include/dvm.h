@@ -198,12 +198,9 @@ int dvm_launches_per_step(dvm_handle* h, int* launches);
 
 /* Which kinetic-pass kernel the handle's steps run (chosen at dvm_create
  * from the grid, precision and boundaries): DVM_KPASS_GENERIC (one thread
- * per cell, any configuration), DVM_KPASS_WINDOW (FP32/BF16 storage,
- * periodic 2D/3D, p = 1: per-thread windows of source rows) or
- * DVM_KPASS_ROWS (FP32, periodic 2D/3D, p = 1, N_x a multiple of 32 up to
- * 256, only with the environment variable DVM_ROWS_PASS=1 at dvm_create:
- * whole x rows moved by tensor copies through shared memory). */
-enum { DVM_KPASS_GENERIC = 0, DVM_KPASS_WINDOW = 1, DVM_KPASS_ROWS = 2 };
+ * per cell, any configuration) or DVM_KPASS_WINDOW (FP32/BF16 storage,
+ * periodic 2D/3D, p = 1: per-thread windows of source rows). */
+enum { DVM_KPASS_GENERIC = 0, DVM_KPASS_WINDOW = 1 };
 int dvm_kinetic_kernel(const dvm_handle* h, int* kind);
 
 /* Velocity chunks of the kinetic pass (chosen at dvm_create from the grid and

@@ -131,7 +131,6 @@ int make_geom(const dvm_config* cfg, Geom* g, std::string* msg) {
   bool outflow = false;
   for (int i = 0; i < d; ++i) outflow |= g->bc[i] == DVM_BC_OUTFLOW;
   g->ghost_mode = outflow ? (d == 1 ? 1 : 2) : 0;
-  g->rows_pass = kinetic_rows_allowed(*g) ? 1 : 0;
   g->nsplit = kinetic_pass_splits(*g);
   return 0;
 }
@@ -807,9 +806,7 @@ int dvm_launches_per_step(dvm_handle* h, int* launches) {
 
 int dvm_kinetic_kernel(const dvm_handle* h, int* kind) {
   if (!h || !kind) return DVM_ERR_ARG;
-  *kind = !kinetic_is_windowed(h->g)      ? DVM_KPASS_GENERIC
-          : kinetic_rows_eligible(h->g) ? DVM_KPASS_ROWS
-                                        : DVM_KPASS_WINDOW;
+  *kind = kinetic_is_windowed(h->g) ? DVM_KPASS_WINDOW : DVM_KPASS_GENERIC;
   return 0;
 }
 

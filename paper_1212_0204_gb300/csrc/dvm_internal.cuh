@@ -76,7 +76,6 @@ struct Geom {
   int skip_euler;     // every lambda == 1: U_E = 0, no Euler launch
   int euler_blocks;   // grid of the cooperative Euler launch (all co-resident)
   int learn;          // learned regime path on: flagged cells (see dvm_learn.cuh)
-  int rows_pass;      // the kinetic pass runs on whole rows (dvm_kinetic_rows.cu)
 };
 
 struct DevPtrs {
@@ -171,12 +170,6 @@ int launch_kinetic_pass(const Geom& g, const DevPtrs& p, cudaStream_t s);  // ke
 // one of them (FP32, HOFKS; in 3D without the learned path)
 bool launch_window_fixed(const Geom& g, const DevPtrs& p, int splits, cudaStream_t s, bool prepare);
 void kinetic_pass_prepare(const Geom& g);
-// the row pass (dvm_kinetic_rows.cu): FP32, whole x rows moved by tensor copies
-bool kinetic_rows_allowed(const Geom& g);  // at dvm_create: opt-in and the shape fits
-inline bool kinetic_rows_eligible(const Geom& g) { return g.rows_pass != 0; }
-int kinetic_rows_splits(const Geom& g);
-void kinetic_rows_prepare(const Geom& g);
-cudaError_t launch_kinetic_rows(const Geom& g, const DevPtrs& p, cudaStream_t s);
 int kinetic_pass_splits(const Geom& g);
 
 }  // namespace dvm

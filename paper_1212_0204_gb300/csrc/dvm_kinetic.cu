@@ -319,7 +319,6 @@ void launch_generic(const Geom& g, const DevPtrs& p, cudaStream_t s) {
 // Velocity chunks: enough blocks for several waves on 152 SMs, at least 16
 // velocities per chunk.
 int kinetic_pass_splits(const Geom& g) {
-  if (kinetic_rows_eligible(g) && !getenv_generic()) return kinetic_rows_splits(g);
   if (window_eligible(g)) return window_shape(g).splits;
   const long long blocks = (g.nc + kThreads - 1) / kThreads;
   const long long want = 152LL * 8;
@@ -334,17 +333,16 @@ int kinetic_pass_splits(const Geom& g) {
 // Kernel attributes that must be set before the first launch (outside any
 // stream capture): dynamic shared memory of the windowed pass.
 void kinetic_pass_prepare(const Geom& g) {
-  if (kinetic_rows_eligible(g)) kinetic_rows_prepare(g);
   if (!window_eligible(g)) return;
   DevPtrs none{};
   if (g.precision == DVM_F32) launch_window<float>(g, none, nullptr, true);
   else launch_window<__nv_bfloat16>(g, none, nullptr, true);
 }
 
-// The windowed or the row pass (both skip CTAs whose targets are all deep in
-// the learned path).
+// The windowed pass (it skips CTAs whose targets are all deep in the learned
+// path).
 bool kinetic_is_windowed(const Geom& g) {
-  return (kinetic_rows_eligible(g) || window_eligible(g)) && !getenv_generic();
+  return window_eligible(g) && !getenv_generic();
 }
 
 int launch_kinetic_pass(const Geom& g, const DevPtrs& p, cudaStream_t s) {
@@ -352,10 +350,6 @@ int launch_kinetic_pass(const Geom& g, const DevPtrs& p, cudaStream_t s) {
     const unsigned nb = (unsigned)((g.nc + 255) / 256);
     if (g.d == 2) k_window_fold<2><<<nb, 256, 0, s>>>(g, p);
     else k_window_fold<3><<<nb, 256, 0, s>>>(g, p);
-    if (kinetic_rows_eligible(g)) {
-      launch_kinetic_rows(g, p, s);
-      return 2;
-    }
     if (g.precision == DVM_F32) launch_window<float>(g, p, s);
     else launch_window<__nv_bfloat16>(g, p, s);
     return 2;

@@ -1,11 +1,10 @@
-// dvm_window.cuh -- per-source quantities of the kinetic pass on FP32
-// parameters, shared by the windowed pass (dvm_kinetic.cu) and the row pass
-// (dvm_kinetic_rows.cu).  A thread owns Y consecutive target rows; the
-// sources of its targets at one velocity pair (kx, kz) and consecutive ky
-// form a window of source rows that slides by one row per ky step.  Each
-// window slot holds the source's parameters folded with vx and vz, so that
-// the Maxwellian, the deferred term and the moment-matching term are
-// quadratics in vy.
+// dvm_window.cuh -- per-source quantities of the windowed kinetic pass on
+// FP32 parameters (dvm_window_kernel.cuh).  A thread owns Y consecutive
+// target rows; the sources of its targets at one velocity pair (kx, kz) and
+// consecutive ky form a window of source rows that slides by one row per ky
+// step.  Each window slot holds the source's parameters folded with vx and
+// vz, so that the Maxwellian, the deferred term and the moment-matching term
+// are quadratics in vy.
 #pragma once
 
 #include "dvm_internal.cuh"

@@ -401,10 +401,10 @@ class Solver:
         return n.value
 
     def kinetic_kernel(self) -> str:
-        """'generic', 'window' or 'rows': the kinetic-pass kernel of this handle."""
+        """'generic' or 'window': the kinetic-pass kernel of this handle."""
         k = C.c_int()
         self._check(lib().dvm_kinetic_kernel(self._h, C.byref(k)))
-        return ("generic", "window", "rows")[k.value]
+        return ("generic", "window")[k.value]
 
     def kinetic_splits(self) -> int:
         """Velocity chunks of the kinetic pass (CTAs per target tile)."""
