@@ -361,7 +361,7 @@ class Job:
             self.obj = dvm.Batch(case, precision=precision)
             self.U0 = self.obj.pack([conserved(c) for c in case])
             self.points = sum(c.points for c in case)
-            self.rows, self.cells = 3, self.obj.ncells
+            self.rows, self.cells = self.obj.rows, self.obj.ncells
         else:
             self.obj = dvm.Solver.from_case(case, precision=precision)
             self.U0 = conserved(case)

@@ -218,27 +218,34 @@ int dvm_profile_begin(dvm_handle* h);
 int dvm_profile_end(dvm_handle* h, double* kinetic_ms, int* launches);
 
 /* ----------------------------------------------------------------------
- * Batched 1D-1V cases.  Many independent tubes (each a 1D configuration with
- * its own N_x, N_v, kmin, dv, tau, p and boundary rule; all with the same
- * scheme and precision, N_x <= 4096, scalar tau) advance together: one time
- * step of the batch is three kernel launches for all cases, captured into
- * one CUDA graph (Euler sub-steps per case; one persistent kinetic pass over
- * a work queue of (case, cell tile) items ordered by cost; end-of-step
- * update).  The scheme is the one of dvm_step (Sections 4.2 and 4.3).
- * Packed layout of batch moments: rows rho, rho u, E of N_total cells each,
- * FP64, case i's cells at [c_i, c_i + N_x,i) with c_i the running sum of
- * the N_x of the cases before it. */
+ * Batched 1D-1V and 2D-2V cases.  Many independent problems (each with its
+ * own dimension, grid, velocity set, tau, p and boundary rule; all with the
+ * same scheme and precision, scalar tau; a 1D tube has N_x <= 4096 cells, a
+ * 2D case is periodic in both dimensions with at most 2^20 cells) advance
+ * together: one time step of the batch is three kernel launches for all
+ * cases, captured into one CUDA graph (Euler sub-steps, one CTA per case; one
+ * persistent kinetic pass over a work queue of (case, cell tile, velocity
+ * chunk) items ordered by cost; end-of-step update).  The scheme is the one
+ * of dvm_step (Sections 4.2 and 4.3; Section 4.2 is dimension-generic).
+ * Packed layout of batch moments: R rows (R = dvm_batch_moment_rows: 3 if
+ * every case is 1D, else 4) of N_total cells each, FP64; case i's cells
+ * (x fastest) at [c_i, c_i + N_cells,i), c_i the running sum of the cell
+ * counts of the cases before it; a case of dimension d uses rows 0 .. d+1,
+ * (rho, rho u_1 .. rho u_d, E), and leaves the rows after them zero. */
 typedef struct dvm_batch dvm_batch;
 
-/* cfgs: ncases configurations (dim must be 1).  Device memory is allocated
+/* cfgs: ncases configurations (dim 1 or 2).  Device memory is allocated
  * with cudaMalloc and freed by dvm_batch_destroy.  DVM_ERR_ARG if a case is
- * invalid or the cases disagree on scheme or precision. */
+ * invalid, a 2D case is not periodic or too large, or the cases disagree on
+ * scheme or precision. */
 int dvm_batch_create(const dvm_config* cfgs, int ncases, void* cuda_stream,
                      dvm_batch** out);
 void dvm_batch_destroy(dvm_batch* b);
 const char* dvm_batch_last_error(const dvm_batch* b);
 /* Total cells and phase-space points of the batch. */
 int dvm_batch_sizes(const dvm_batch* b, long long* cells, long long* points);
+/* Rows R of the packed moments (3 or 4, see above). */
+int dvm_batch_moment_rows(const dvm_batch* b, int* rows);
 /* f^0 = E[U^0] for every case (Eq. minimMax); U packed as above, host or
  * device. */
 int dvm_batch_set_state_moments(dvm_batch* b, const double* U, int on_device);
@@ -247,25 +254,34 @@ int dvm_batch_step_async(dvm_batch* b, int nsteps);
 int dvm_batch_sync_status(dvm_batch* b);
 /* Packed moments of all cases into the caller's buffer (host or device). */
 int dvm_batch_moments(dvm_batch* b, double* out, int on_device);
-/* Pipelined read-back of the packed moments (3 x total cells FP64), with the
+/* Pipelined read-back of the packed moments (R x total cells FP64), with the
  * semantics of dvm_moments_async / dvm_moments_wait: snapshot on the device in
  * stream order, copy on a private stream, at most two in flight, the status
  * word as each ticket's snapshot found it. */
 int dvm_batch_moments_async(dvm_batch* b, double* out, int on_device, long long* ticket);
 int dvm_batch_moments_wait(dvm_batch* b, long long ticket);
-/* f of case icase at its cell centres, N_v x N_x FP64, host buffer. */
+/* f of case icase at its cell centres, N_v x N_cells FP64 (velocity-major,
+ * velocities and cells x fastest), host buffer. */
 int dvm_batch_get_f(dvm_batch* b, int icase, double* out);
-/* Step index, per-case Euler sub-steps and alpha of the last step (host
- * arrays of ncases entries; any pointer may be NULL). */
+/* Step index, per-case Euler sub-steps and alpha of the last step's first
+ * sub-step (summed over the directions of a 2D case) (host arrays of ncases
+ * entries; any pointer may be NULL). */
 int dvm_batch_info(dvm_batch* b, long long* n, int* substeps, double* alpha);
-/* Tile of the kinetic pass: threads per CTA (multiple of 32, <= 1024) and
- * cells per thread (1..8). */
-int dvm_batch_set_tiling(dvm_batch* b, int threads, int cells_per_thread);
-/* Times the kinetic pass of every candidate tile (threads 64/128/256 x 1 or
- * 2 cells per thread) on the current state, restores f, keeps the fastest
- * and returns it with its time in ms.  Needs a state. */
-int dvm_batch_autotune(dvm_batch* b, int* threads, int* cells_per_thread,
-                       double* best_ms);
+/* Launch of the kinetic pass: threads per CTA (multiple of 32, <= 1024),
+ * cells per thread (1..8), velocity chunks per case (1..4; a case takes at
+ * most one chunk per 16 velocities; each chunk is its own work item writing
+ * its own FP64 partial moment sums, added in chunk order at the end of the
+ * step) and resident CTAs per SM (0 = as many as fit, else at most that many).
+ * The chunking changes the order in which the partial sums are added, so
+ * results can differ in the last bits of FP64 between launches. */
+int dvm_batch_set_tiling(dvm_batch* b, int threads, int cells_per_thread, int vchunks,
+                         int ctas_per_sm);
+/* Times the kinetic pass of every candidate launch (threads 64/128/256 x 1
+ * or 2 cells per thread x 1/2/4 velocity chunks x 0/2/4 CTAs per SM) on the
+ * current state, restores f, keeps the fastest and returns it with its time
+ * in ms.  Needs a state. */
+int dvm_batch_autotune(dvm_batch* b, int* threads, int* cells_per_thread, int* vchunks,
+                       int* ctas_per_sm, double* best_ms);
 /* Runs nsteps steps launch by launch with CUDA events around the kinetic
  * pass; *ms receives its average time. */
 int dvm_batch_kinetic_ms(dvm_batch* b, int nsteps, double* ms);

@@ -33,6 +33,7 @@ EXPORTS = [
     "dvm_profile_end",
     "dvm_equilibrium_noalloc", "dvm_selftest_timeout",
     "dvm_batch_create", "dvm_batch_destroy", "dvm_batch_last_error", "dvm_batch_sizes",
+    "dvm_batch_moment_rows",
     "dvm_batch_set_state_moments", "dvm_batch_step", "dvm_batch_step_async",
     "dvm_batch_sync_status", "dvm_batch_moments", "dvm_batch_moments_async", "dvm_batch_moments_wait", "dvm_batch_get_f", "dvm_batch_info",
     "dvm_batch_set_tiling", "dvm_batch_autotune", "dvm_batch_kinetic_ms",
@@ -144,8 +145,10 @@ def lib():
         L.dvm_batch_moments.argtypes = [vp, vp, ip]
         L.dvm_batch_get_f.argtypes = [vp, ip, vp]
         L.dvm_batch_info.argtypes = [vp, C.POINTER(C.c_longlong), vp, vp]
-        L.dvm_batch_set_tiling.argtypes = [vp, ip, ip]
-        L.dvm_batch_autotune.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
+        L.dvm_batch_moment_rows.argtypes = [vp, C.POINTER(C.c_int)]
+        L.dvm_batch_set_tiling.argtypes = [vp, ip, ip, ip, ip]
+        L.dvm_batch_autotune.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                         C.POINTER(C.c_int), dp]
         L.dvm_batch_kinetic_ms.argtypes = [vp, ip, dp]
         L.dvm_learn_enable.argtypes = [vp, C.POINTER(_LearnConfig)]
         L.dvm_learn_set_params.argtypes = [vp, vp]
@@ -549,8 +552,9 @@ class Mlp:
 
 
 class Batch:
-    """Many independent 1D-1V cases advanced together (dvm_batch_*).  Moments are
-    packed: rows (rho, rho u, E) over all cells, case after case."""
+    """Many independent 1D-1V and 2D-2V cases advanced together (dvm_batch_*).
+    Moments are packed: `rows` rows (3 if every case is 1D, else 4) over all
+    cells, case after case; a case of dimension d fills its first d + 2 rows."""
 
     def __init__(self, cases, precision=F32, scheme=None, stream=None):
         import torch
@@ -565,8 +569,9 @@ class Batch:
             self._keep += keep
         self._cfgs = arr
         self.ncases = len(cases)
-        self.nx = [int(c.nx[0]) for c in cases]
-        self.nv = [int(c.nv[0]) for c in cases]
+        self.dims = [int(c.d) for c in cases]
+        self.nx = [int(np.prod(c.nx)) for c in cases]     # cells of each case
+        self.nv = [int(np.prod(c.nv)) for c in cases]     # velocities of each case
         self.offsets = np.concatenate([[0], np.cumsum(self.nx)]).astype(int)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
@@ -575,9 +580,10 @@ class Batch:
             raise DvmError(rc, "dvm_batch_create failed")
         self._h = h
         self._pending = {}
-        cells, pts = C.c_longlong(), C.c_longlong()
+        cells, pts, rows = C.c_longlong(), C.c_longlong(), C.c_int()
         lib().dvm_batch_sizes(h, C.byref(cells), C.byref(pts))
-        self.ncells, self.npoints = cells.value, pts.value
+        lib().dvm_batch_moment_rows(h, C.byref(rows))
+        self.ncells, self.npoints, self.rows = cells.value, pts.value, rows.value
 
     def close(self):
         if getattr(self, "_h", None):
@@ -592,8 +598,11 @@ class Batch:
             raise DvmError(rc, lib().dvm_batch_last_error(self._h).decode())
 
     def pack(self, per_case):
-        """Pack a list of (3, N_x,i) moment arrays into the batch layout."""
-        return np.ascontiguousarray(np.concatenate(per_case, axis=1))
+        """Pack a list of (d_i + 2, N_cells,i) moment arrays into the batch layout."""
+        out = np.zeros((self.rows, self.ncells))
+        for i, U in enumerate(per_case):
+            out[:U.shape[0], self.offsets[i]:self.offsets[i + 1]] = U
+        return out
 
     def set_moments(self, U):
         t = self._torch
@@ -619,19 +628,19 @@ class Batch:
             self._check(lib().dvm_batch_moments(self._h, C.c_void_p(out.data_ptr()),
                                                 1 if out.is_cuda else 0))
             return out
-        a = np.zeros((3, self.ncells))
+        a = np.zeros((self.rows, self.ncells))
         self._check(lib().dvm_batch_moments(self._h, a.ctypes.data_as(C.c_void_p), 0))
         return a
 
     def moments_async(self, out):
-        """Pipelined read-back of the packed moments into `out` (float64 (3, cells):
+        """Pipelined read-back of the packed moments into `out` (float64 (rows, cells):
         pinned host or CUDA torch tensor, or numpy array); returns a ticket."""
         t = self._torch
         if isinstance(out, t.Tensor):
-            assert out.dtype == t.float64 and out.is_contiguous() and out.numel() == 3 * self.ncells
+            assert out.dtype == t.float64 and out.is_contiguous() and out.numel() == self.rows * self.ncells
             ptr, dev = out.data_ptr(), 1 if out.is_cuda else 0
         else:
-            assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == 3 * self.ncells
+            assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == self.rows * self.ncells
             ptr, dev = out.ctypes.data, 0
         ticket = C.c_longlong()
         self._check(lib().dvm_batch_moments_async(self._h, C.c_void_p(ptr), dev, C.byref(ticket)))
@@ -646,7 +655,7 @@ class Batch:
                 del self._pending[k]
 
     def case_moments(self, U, i):
-        return U[:, self.offsets[i]:self.offsets[i + 1]]
+        return U[:self.dims[i] + 2, self.offsets[i]:self.offsets[i + 1]]
 
     def f(self, i):
         a = np.zeros((self.nv[i], self.nx[i]))
@@ -661,13 +670,17 @@ class Batch:
                                          a.ctypes.data_as(C.c_void_p)))
         return {"n": n.value, "m": m, "alpha": a}
 
-    def set_tiling(self, threads, cells_per_thread):
-        self._check(lib().dvm_batch_set_tiling(self._h, int(threads), int(cells_per_thread)))
+    def set_tiling(self, threads, cells_per_thread, vchunks=1, ctas_per_sm=0):
+        self._check(lib().dvm_batch_set_tiling(self._h, int(threads), int(cells_per_thread), int(vchunks),
+                                               int(ctas_per_sm)))
 
     def autotune(self):
-        t, c, ms = C.c_int(), C.c_int(), C.c_double()
-        self._check(lib().dvm_batch_autotune(self._h, C.byref(t), C.byref(c), C.byref(ms)))
-        return t.value, c.value, ms.value
+        """(threads, cells per thread, velocity chunks, CTAs per SM, ms) of the
+        fastest kinetic-pass launch, which the batch keeps."""
+        t, c, v, o, ms = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_double()
+        self._check(lib().dvm_batch_autotune(self._h, C.byref(t), C.byref(c), C.byref(v), C.byref(o),
+                                             C.byref(ms)))
+        return t.value, c.value, v.value, o.value, ms.value
 
     def kinetic_ms(self, nsteps=3):
         ms = C.c_double()
@@ -681,8 +694,8 @@ def autotune_cached(batch: "Batch", cases, precision, scheme) -> dict:
     lives in $DVM_CACHE_DIR or ~/.cache/dvm (skipped if not writable)."""
     import hashlib
     import json
-    sig = hashlib.sha256(json.dumps([[int(c.nx[0]), int(c.nv[0])] for c in cases] +
-                                    [precision, scheme]).encode()).hexdigest()[:20]
+    sig = hashlib.sha256(json.dumps([[int(c.d), list(map(int, c.nx)), list(map(int, c.nv))] for c in cases] +
+                                    [precision, scheme, 2]).encode()).hexdigest()[:20]
     d = os.environ.get("DVM_CACHE_DIR", os.path.join(os.path.expanduser("~"), ".cache", "dvm"))
     path = os.path.join(d, "batch_autotune.json")
     table = {}
@@ -692,11 +705,11 @@ def autotune_cached(batch: "Batch", cases, precision, scheme) -> dict:
     except (OSError, ValueError):
         table = {}
     if sig in table:
-        t, c = table[sig]["threads"], table[sig]["cells_per_thread"]
-        batch.set_tiling(t, c)
-        return dict(table[sig], cached=True)
-    t, c, ms = batch.autotune()
-    table[sig] = {"threads": t, "cells_per_thread": c, "kinetic_ms": ms}
+        e = table[sig]
+        batch.set_tiling(e["threads"], e["cells_per_thread"], e["vchunks"], e["ctas_per_sm"])
+        return dict(e, cached=True)
+    t, c, v, o, ms = batch.autotune()
+    table[sig] = {"threads": t, "cells_per_thread": c, "vchunks": v, "ctas_per_sm": o, "kinetic_ms": ms}
     try:
         os.makedirs(d, exist_ok=True)
         with open(path, "w") as fh:
