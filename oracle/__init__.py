@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SOURCES = ["dvm_oracle.c", "riemann.c", "mlp.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
-FKS, HOFKS, HOFKS_UNLIMITED = 0, 1, 2
+FKS, HOFKS, HOFKS_UNLIMITED, HOFKS_WENO = 0, 1, 2, 3
 PERIODIC, OUTFLOW = 0, 1
 
 
@@ -75,6 +75,8 @@ def lib():
         L.orc_euler_alpha.argtypes = [C.POINTER(_Config), dp, dp]
         L.orc_muscl_step.argtypes = [C.POINTER(_Config), dp, C.c_double, dp,
                                      C.c_int, dp]
+        L.orc_weno5_reconstruct.argtypes = [dp, C.c_int, C.c_int, dp]
+        L.orc_weno_step.argtypes = [C.POINTER(_Config), dp, C.c_double, dp, C.c_int, dp]
         L.orc_riemann_exact.argtypes = [C.c_double] * 7 + [dp, C.c_int, dp, dp, dp, dp, dp]
         L.orc_step_flagged.argtypes = [C.c_void_p, C.POINTER(C.c_ubyte), C.c_int]
         L.orc_set_lambda.argtypes = [C.c_void_p, dp]
@@ -207,6 +209,23 @@ def muscl_step(g: Grid, W, dt: float, alpha, limited: bool = True) -> np.ndarray
     cfg = g.cstruct()
     _check(lib().orc_muscl_step(C.byref(cfg), _ptr(W), dt, _ptr(a), int(limited), _ptr(out)),
            "muscl")
+    return out
+
+
+def weno5_reconstruct(v, linear: bool = False) -> np.ndarray:
+    """Left-biased WENO5 values at j+1/2 of the periodic samples v."""
+    v = _f64(v)
+    out = np.zeros_like(v)
+    _check(lib().orc_weno5_reconstruct(_ptr(v), len(v), int(linear), _ptr(out)), "weno5")
+    return out
+
+
+def weno_step(g: Grid, W, dt: float, alpha, linear: bool = False) -> np.ndarray:
+    W = _f64(W)
+    a = _f64(np.asarray(list(alpha) + [0.0] * (3 - len(alpha))))
+    out = np.zeros_like(W)
+    cfg = g.cstruct()
+    _check(lib().orc_weno_step(C.byref(cfg), _ptr(W), dt, _ptr(a), int(linear), _ptr(out)), "weno")
     return out
 
 

@@ -8,7 +8,9 @@
  *   Section 4.3.1   HOFKS: relaxation, transport, U_M replaced by U_E
  *                   (Eqs. UK, mom, cons, minim_full)
  *   Section 4.3.2   MUSCL finite volume Euler solver (Eq. discmom)
- *   Section 4.3.3   Euler time-step rule (Eq. Time2)
+ *   Section 4.3.3   Euler time-step rule (Eq. Time2); the WENO solver the
+ *                   section names as an alternative (finite-difference WENO5
+ *                   of Jiang and Shu, as in Shu's 1998 lecture notes)
  * Readings where the paper is silent are marked "reading:" below.
  *
  * f is stored at cell positions and physically moved every step, the most
@@ -42,7 +44,7 @@ static int check_config(const orc_config* g) {
     if (g->bc[i] != ORC_PERIODIC && g->bc[i] != ORC_OUTFLOW) return ORC_ERR_ARG;
   }
   if (!(g->dx > 0) || !(g->dv > 0) || g->p < 1) return ORC_ERR_ARG;
-  if (g->scheme < ORC_FKS || g->scheme > ORC_HOFKS_UNLIMITED) return ORC_ERR_ARG;
+  if (g->scheme < ORC_FKS || g->scheme > ORC_HOFKS_WENO) return ORC_ERR_ARG;
   if (g->subcycles < 0) return ORC_ERR_ARG;
   return ORC_OK;
 }
@@ -383,6 +385,122 @@ int orc_muscl_step(const orc_config* g, const double* W, double dt,
 }
 
 /* ------------------------------------------------------------------------ */
+/* WENO Euler solver (Section 4.3.3 names WENO as a higher-order alternative  */
+/* to MUSCL; reading: the finite-difference WENO5 scheme of Jiang and Shu,    */
+/* component by component, on the Lax-Friedrichs split fluxes                 */
+/* f+- = (F +- alpha U) / 2 with the same global alpha per direction as the   */
+/* MUSCL flux, advanced by the three-stage SSP Runge-Kutta scheme of Shu and  */
+/* Osher over each Euler sub-step of Eq. Time2 length)                        */
+/* ------------------------------------------------------------------------ */
+
+/* Interface value at j+1/2 from v[0..4] = values at j-2 .. j+2, biased to the
+ * left (upwind for a right-moving flux).  Three candidate quadratics on the
+ * sub-stencils {j-2, j-1, j}, {j-1, j, j+1}, {j, j+1, j+2}, each third-order
+ * accurate at j+1/2, blended with weights d_k / (eps + beta_k)^2 normalised
+ * to one, beta_k the smoothness indicators (sums of squared scaled
+ * derivatives of the candidate over the cell); linear != 0 uses the optimal
+ * weights d = (1/10, 6/10, 3/10) themselves (fifth order, no limiting). */
+static double weno5_left(const double* v, int linear) {
+  const double q0 = (2.0 * v[0] - 7.0 * v[1] + 11.0 * v[2]) / 6.0;
+  const double q1 = (-v[1] + 5.0 * v[2] + 2.0 * v[3]) / 6.0;
+  const double q2 = (2.0 * v[2] + 5.0 * v[3] - v[4]) / 6.0;
+  const double d0 = 0.1, d1 = 0.6, d2 = 0.3;
+  if (linear) return d0 * q0 + d1 * q1 + d2 * q2;
+  const double a0 = v[0] - 2.0 * v[1] + v[2], b0 = v[0] - 4.0 * v[1] + 3.0 * v[2];
+  const double a1 = v[1] - 2.0 * v[2] + v[3], b1 = v[1] - v[3];
+  const double a2 = v[2] - 2.0 * v[3] + v[4], b2 = 3.0 * v[2] - 4.0 * v[3] + v[4];
+  const double beta0 = 13.0 / 12.0 * a0 * a0 + 0.25 * b0 * b0;
+  const double beta1 = 13.0 / 12.0 * a1 * a1 + 0.25 * b1 * b1;
+  const double beta2 = 13.0 / 12.0 * a2 * a2 + 0.25 * b2 * b2;
+  const double eps = 1e-6;
+  const double w0 = d0 / ((eps + beta0) * (eps + beta0));
+  const double w1 = d1 / ((eps + beta1) * (eps + beta1));
+  const double w2 = d2 / ((eps + beta2) * (eps + beta2));
+  return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
+}
+
+int orc_weno5_reconstruct(const double* v, int n, int linear, double* out) {
+  if (!v || !out || n < 5) return ORC_ERR_ARG;
+  for (int j = 0; j < n; ++j) {
+    double s[5];
+    for (int o = 0; o < 5; ++o) s[o] = v[(j + o - 2 + n) % n];
+    out[j] = weno5_left(s, linear);
+  }
+  return ORC_OK;
+}
+
+/* psi_{j+1/2} along dir from the cells jm2 .. jp3 (indices in c[0..5]): the
+ * left-biased value of f+ from j-2 .. j+2 plus the right-biased value of f-
+ * from j+3 .. j-1 (the same formula on the mirrored stencil). */
+static void weno_face_flux(const orc_config* g, const double* W, const long* c, int dir,
+                           double alpha, int linear, double* psi) {
+  const int d = g->d, nm = d + 2;
+  const long nc = ncells(g);
+  double Us[6][MAXM], Fs[6][MAXM];
+  for (int s = 0; s < 6; ++s) {
+    for (int i = 0; i < nm; ++i) Us[s][i] = W[i * nc + c[s]];
+    orc_euler_flux(d, Us[s], dir, Fs[s]);
+  }
+  for (int i = 0; i < nm; ++i) {
+    double fp[5], fm[5];
+    for (int s = 0; s < 5; ++s) {
+      fp[s] = 0.5 * (Fs[s][i] + alpha * Us[s][i]);          /* cells j-2 .. j+2 */
+      fm[s] = 0.5 * (Fs[5 - s][i] - alpha * Us[5 - s][i]);  /* cells j+3 .. j-1 */
+    }
+    psi[i] = weno5_left(fp, linear) + weno5_left(fm, linear);
+  }
+}
+
+/* L(W) = -(1/dx) sum_dir (psi_{j+1/2} - psi_{j-1/2}) (reading: unsplit). */
+static void weno_rhs(const orc_config* g, const double* W, const double* alpha, int linear,
+                     double* L) {
+  const int d = g->d, nm = d + 2;
+  const long nc = ncells(g);
+  for (long c = 0; c < nc; ++c) {
+    double acc[MAXM] = {0};
+    for (int dir = 0; dir < d; ++dir) {
+      long st[7];
+      for (int o = 0; o < 7; ++o) st[o] = neighbour(g, c, dir, o - 3);  /* j-3 .. j+3 */
+      double pr[MAXM], pl[MAXM];
+      weno_face_flux(g, W, st + 1, dir, alpha[dir], linear, pr);  /* j+1/2: j-2 .. j+3 */
+      weno_face_flux(g, W, st, dir, alpha[dir], linear, pl);      /* j-1/2: j-3 .. j+2 */
+      for (int i = 0; i < nm; ++i) acc[i] += pr[i] - pl[i];
+    }
+    for (int i = 0; i < nm; ++i) L[i * nc + c] = -acc[i] / g->dx;
+  }
+}
+
+/* One Euler sub-step of length dt by the three-stage SSP Runge-Kutta scheme:
+ *   W1 = W + dt L(W)
+ *   W2 = 3/4 W + 1/4 (W1 + dt L(W1))
+ *   W' = 1/3 W + 2/3 (W2 + dt L(W2))
+ * with alpha (per direction) held for the three stages. */
+int orc_weno_step(const orc_config* g, const double* W, double dt, const double* alpha,
+                  int linear, double* Wout) {
+  const int nm = g->d + 2;
+  const long nc = ncells(g), n = nm * nc;
+  double* L = malloc(sizeof(double) * n);
+  double* W1 = calloc(n, sizeof(double));
+  double* W2 = calloc(n, sizeof(double));
+  if (!L || !W1 || !W2) {
+    free(L);
+    free(W1);
+    free(W2);
+    return ORC_ERR_OOM;
+  }
+  weno_rhs(g, W, alpha, linear, L);
+  for (long i = 0; i < n; ++i) W1[i] = W[i] + dt * L[i];
+  weno_rhs(g, W1, alpha, linear, L);
+  for (long i = 0; i < n; ++i) W2[i] = 0.75 * W[i] + 0.25 * (W1[i] + dt * L[i]);
+  weno_rhs(g, W2, alpha, linear, L);
+  for (long i = 0; i < n; ++i) Wout[i] = W[i] / 3.0 + 2.0 / 3.0 * (W2[i] + dt * L[i]);
+  free(L);
+  free(W1);
+  free(W2);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* scheme state                                                             */
 /* ------------------------------------------------------------------------ */
 
@@ -598,7 +716,12 @@ static int euler_part(orc_state* S) {
       last = (cfl >= rem);
       dtE = last ? rem : cfl;
     }
-    orc_muscl_step(&S->g, a, dtE, alpha, limited, b);
+    if (S->g.scheme == ORC_HOFKS_WENO) {
+      const int rc = orc_weno_step(&S->g, a, dtE, alpha, 0, b);
+      if (rc) return rc;
+    } else {
+      orc_muscl_step(&S->g, a, dtE, alpha, limited, b);
+    }
     double* tmp = a;
     a = b;
     b = tmp;

@@ -33,6 +33,7 @@ extern "C" {
 #define ORC_FKS 0
 #define ORC_HOFKS 1
 #define ORC_HOFKS_UNLIMITED 2
+#define ORC_HOFKS_WENO 3 /* HOFKS with the WENO5 Euler solver of Section 4.3.3 */
 
 #define ORC_PERIODIC 0
 #define ORC_OUTFLOW 1
@@ -80,6 +81,16 @@ int orc_euler_alpha(const orc_config* cfg, const double* U, double* alpha);
  * limiter to 1. */
 int orc_muscl_step(const orc_config* cfg, const double* W, double dt,
                    const double* alpha, int limited, double* Wout);
+
+/* WENO5 interface values: out[j] = the left-biased value at j+1/2 of the
+ * periodic samples v[0..n-1] (n >= 5); linear != 0 takes the optimal linear
+ * weights instead of the nonlinear ones. */
+int orc_weno5_reconstruct(const double* v, int n, int linear, double* out);
+
+/* One Euler sub-step of length dt of the WENO5 scheme on the split fluxes
+ * (F +- alpha U)/2 (alpha per direction), three-stage SSP Runge-Kutta. */
+int orc_weno_step(const orc_config* cfg, const double* W, double dt,
+                  const double* alpha, int linear, double* Wout);
 
 /* Exact solution of the 1D Euler Riemann problem at the points xi = x/t. */
 int orc_riemann_exact(double gamma, double rl, double ul, double pl,

@@ -60,6 +60,29 @@ LEARNED_MUTANTS = [
 ]
 
 
+# the WENO Euler solver (Section 4.3.3), against tests/test_oracle_weno.py
+WENO_MUTANTS = [
+    ("WENO5 optimal weights in the wrong order (3/10, 6/10, 1/10)",
+     "dvm_oracle.c", "const double d0 = 0.1, d1 = 0.6, d2 = 0.3;", "const double d0 = 0.3, d1 = 0.6, d2 = 0.1;"),
+    ("WENO5 left candidate with 9 v_j instead of 11 v_j",
+     "dvm_oracle.c", "(2.0 * v[0] - 7.0 * v[1] + 11.0 * v[2]) / 6.0", "(2.0 * v[0] - 7.0 * v[1] + 9.0 * v[2]) / 6.0"),
+    ("WENO5 smoothness indicator of the right stencil without its first-derivative term",
+     "dvm_oracle.c", "13.0 / 12.0 * a2 * a2 + 0.25 * b2 * b2;", "13.0 / 12.0 * a2 * a2;"),
+    ("WENO5 nonlinear weights d_k / (eps + beta_k) instead of its square",
+     "dvm_oracle.c", "const double w1 = d1 / ((eps + beta1) * (eps + beta1));", "const double w1 = d1 / (eps + beta1);"),
+    ("WENO f- reconstructed on the left-biased stencil (not mirrored)",
+     "dvm_oracle.c", "fm[s] = 0.5 * (Fs[5 - s][i] - alpha * Us[5 - s][i]);",
+     "fm[s] = 0.5 * (Fs[s + 1][i] - alpha * Us[s + 1][i]);"),
+    ("WENO split flux f- = (F + alpha U)/2",
+     "dvm_oracle.c", "fm[s] = 0.5 * (Fs[5 - s][i] - alpha * Us[5 - s][i]);",
+     "fm[s] = 0.5 * (Fs[5 - s][i] + alpha * Us[5 - s][i]);"),
+    ("SSP-RK3 second stage 1/2 W + 1/2 (...) instead of 3/4 and 1/4",
+     "dvm_oracle.c", "W2[i] = 0.75 * W[i] + 0.25 * (W1[i] + dt * L[i]);", "W2[i] = 0.5 * W[i] + 0.5 * (W1[i] + dt * L[i]);"),
+    ("SSP-RK3 last stage weights 1/2, 1/2 instead of 1/3, 2/3",
+     "dvm_oracle.c", "Wout[i] = W[i] / 3.0 + 2.0 / 3.0 * (W2[i] + dt * L[i]);", "Wout[i] = W[i] / 2.0 + 1.0 / 2.0 * (W2[i] + dt * L[i]);"),
+]
+
+
 def oracle_copy(tmp_path, mutant=None):
     dst = tmp_path / "oracle"
     shutil.copytree(os.path.join(ROOT, "oracle"), dst,
@@ -87,7 +110,7 @@ def pins_against(tmp_path, module="test_oracle_pins.py"):
                              "-p", "no:cacheprovider", "-k", "not isentropic_vortex"])
 
 
-@pytest.mark.parametrize("module", ["test_oracle_pins.py", "test_oracle_learned.py"])
+@pytest.mark.parametrize("module", ["test_oracle_pins.py", "test_oracle_learned.py", "test_oracle_weno.py"])
 def test_unmodified_copy_passes_the_pins(tmp_path, module):
     r = pins_against(oracle_copy(tmp_path), module)
     assert r.returncode == 0, r.stdout[-3000:]
@@ -102,4 +125,10 @@ def test_planted_mistake_fails_a_pin(tmp_path, mutant):
 @pytest.mark.parametrize("mutant", LEARNED_MUTANTS, ids=[m[0][:40] for m in LEARNED_MUTANTS])
 def test_planted_mistake_in_the_learned_path_fails_a_pin(tmp_path, mutant):
     r = pins_against(oracle_copy(tmp_path, mutant), "test_oracle_learned.py")
+    assert r.returncode == 1 and " failed" in r.stdout, (mutant[0], r.returncode, r.stdout[-3000:])
+
+
+@pytest.mark.parametrize("mutant", WENO_MUTANTS, ids=[m[0][:40] for m in WENO_MUTANTS])
+def test_planted_mistake_in_the_weno_solver_fails_a_pin(tmp_path, mutant):
+    r = pins_against(oracle_copy(tmp_path, mutant), "test_oracle_weno.py")
     assert r.returncode == 1 and " failed" in r.stdout, (mutant[0], r.returncode, r.stdout[-3000:])
