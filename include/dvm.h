@@ -57,7 +57,10 @@ typedef enum {
 #define DVM_NOALLOC_HEADER_BYTES 512u
 
 typedef enum { DVM_BC_PERIODIC = 0, DVM_BC_OUTFLOW = 1 } dvm_bc;
-typedef enum { DVM_FKS = 0, DVM_HOFKS = 1, DVM_HOFKS_UNLIMITED = 2 } dvm_scheme;
+/* DVM_HOFKS_WENO: HOFKS with the WENO5 Euler solver of Section 4.3.3 (finite-
+ * difference WENO5 on the split fluxes (F +- alpha U)/2, three-stage SSP
+ * Runge-Kutta per Euler sub-step) in place of MUSCL; single problems only. */
+typedef enum { DVM_FKS = 0, DVM_HOFKS = 1, DVM_HOFKS_UNLIMITED = 2, DVM_HOFKS_WENO = 3 } dvm_scheme;
 typedef enum { DVM_F64 = 0, DVM_F32 = 1, DVM_BF16S = 2 } dvm_precision;
 
 /* Spatial grid (Section 4): cell centres x0 + (j + 1/2) dx per dimension. */

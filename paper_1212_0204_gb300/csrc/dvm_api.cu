@@ -115,7 +115,7 @@ int make_geom(const dvm_config* cfg, Geom* g, std::string* msg) {
     *msg = "dx, dv must be > 0 and shift_den >= 1";
     return DVM_ERR_ARG;
   }
-  if (cfg->scheme < DVM_FKS || cfg->scheme > DVM_HOFKS_UNLIMITED) { *msg = "unknown scheme"; return DVM_ERR_ARG; }
+  if (cfg->scheme < DVM_FKS || cfg->scheme > DVM_HOFKS_WENO) { *msg = "unknown scheme"; return DVM_ERR_ARG; }
   if (cfg->precision < DVM_F64 || cfg->precision > DVM_BF16S) { *msg = "unknown precision"; return DVM_ERR_ARG; }
   if (cfg->euler_subcycles < 0 || cfg->max_subcycles < 0) { *msg = "negative sub-step count"; return DVM_ERR_ARG; }
   if (!cfg->tau_field && !(cfg->tau >= 0)) { *msg = "tau must be >= 0"; return DVM_ERR_ARG; }
@@ -140,7 +140,7 @@ int make_geom(const dvm_config* cfg, Geom* g, std::string* msg) {
 namespace {
 
 struct Layout {
-  size_t F, ghost, U, lam, W0, W1, acc, prm, wprm, eqp, UE, UM, Us, A, small, offs, total;
+  size_t F, ghost, U, lam, W0, W1, Wt, acc, prm, wprm, eqp, UE, UM, Us, A, small, offs, total;
 };
 
 Layout layout(const Geom& g) {
@@ -156,6 +156,7 @@ Layout layout(const Geom& g) {
   L.lam = take(8 * nc);
   L.W0 = take(8 * nm * nc);
   L.W1 = take(8 * nm * nc);
+  L.Wt = take(g.scheme == DVM_HOFKS_WENO ? 8 * nm * nc : 0);  // third Runge-Kutta stage
   L.acc = take(8 * (size_t)g.nsplit * 2 * nm * nc);
   L.prm = take(tc * (size_t)prm_rows(g.d) * nc);
   L.wprm = take(g.d >= 2 && g.precision != DVM_F64 ? 4 * 16 * nc : 0);
@@ -228,6 +229,7 @@ void bind(dvm_handle* h, char* base, const Layout& L) {
   p.lam = (double*)(base + L.lam);
   p.W0 = base + L.W0;
   p.W1 = base + L.W1;
+  p.Wt = base + L.Wt;
   p.acc = (double*)(base + L.acc);
   p.prm = base + L.prm;
   p.wprm = (float*)(base + L.wprm);

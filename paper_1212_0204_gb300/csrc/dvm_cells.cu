@@ -488,6 +488,203 @@ __global__ void __launch_bounds__(ETile<D, TF>::THREADS) k_euler(Geom g, DevPtrs
   }
 }
 
+// ------------------------------------------------------------------ WENO5
+
+// Interface value at j+1/2 from v[0..4] = the samples at j-2 .. j+2, biased
+// to the left: the three third-order candidates of the sub-stencils
+// {j-2, j-1, j}, {j-1, j, j+1}, {j, j+1, j+2} blended with the nonlinear
+// weights d_k / (eps + beta_k)^2 (d = 1/10, 6/10, 3/10; beta_k the Jiang-Shu
+// smoothness indicators; eps = 1e-6), normalised to one.
+template <typename TF>
+__device__ inline TF weno5_left(const TF v[5]) {
+  const TF q0 = (TF(2) * v[0] - TF(7) * v[1] + TF(11) * v[2]) * TF(1.0 / 6.0);
+  const TF q1 = (-v[1] + TF(5) * v[2] + TF(2) * v[3]) * TF(1.0 / 6.0);
+  const TF q2 = (TF(2) * v[2] + TF(5) * v[3] - v[4]) * TF(1.0 / 6.0);
+  const TF a0 = v[0] - TF(2) * v[1] + v[2], b0 = v[0] - TF(4) * v[1] + TF(3) * v[2];
+  const TF a1 = v[1] - TF(2) * v[2] + v[3], b1 = v[1] - v[3];
+  const TF a2 = v[2] - TF(2) * v[3] + v[4], b2 = TF(3) * v[2] - TF(4) * v[3] + v[4];
+  const TF c13 = TF(13.0 / 12.0), eps = TF(1e-6);
+  const TF e0 = eps + c13 * a0 * a0 + TF(0.25) * b0 * b0;
+  const TF e1 = eps + c13 * a1 * a1 + TF(0.25) * b1 * b1;
+  const TF e2 = eps + c13 * a2 * a2 + TF(0.25) * b2 * b2;
+  const TF w0 = e_div(TF(0.1), e0 * e0), w1 = e_div(TF(0.6), e1 * e1), w2 = e_div(TF(0.3), e2 * e2);
+  return e_div(w0 * q0 + w1 * q1 + w2 * q2, w0 + w1 + w2);
+}
+
+// -(psi_{j+1/2} - psi_{j-1/2}) along dir for one cell, from the cells j-3 ..
+// j+3 of the state X (index list st[0..6]): the left-biased WENO5 value of
+// f+ = (F + alpha U)/2 plus the right-biased (mirrored stencil) value of
+// f- = (F - alpha U)/2 at each face.
+template <typename TF, int D>
+__device__ inline void weno_dir(const TF* X, long long nc, const long long st[7], int dir, TF al,
+                                TF R[D + 2]) {
+  constexpr int NM = D + 2;
+  TF fp[7][NM], fm[7][NM];
+#pragma unroll
+  for (int o = 0; o < 7; ++o) {
+    TF U[NM], F[NM];
+#pragma unroll
+    for (int i = 0; i < NM; ++i) U[i] = __ldcg(X + i * nc + st[o]);
+    euler_flux<TF, D>(U, dir, F);
+#pragma unroll
+    for (int i = 0; i < NM; ++i) {
+      fp[o][i] = TF(0.5) * (F[i] + al * U[i]);
+      fm[o][i] = TF(0.5) * (F[i] - al * U[i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NM; ++i) {
+    TF psi[2];
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {  // f = 0: face j-1/2 (cells j-3 .. j+2); f = 1: j+1/2
+      const TF vp[5] = {fp[f][i], fp[f + 1][i], fp[f + 2][i], fp[f + 3][i], fp[f + 4][i]};
+      const TF vm[5] = {fm[f + 5][i], fm[f + 4][i], fm[f + 3][i], fm[f + 2][i], fm[f + 1][i]};
+      psi[f] = weno5_left<TF>(vp) + weno5_left<TF>(vm);
+    }
+    R[i] -= psi[1] - psi[0];
+  }
+}
+
+// All Euler sub-steps of one kinetic step with the WENO5 solver (Section
+// 4.3.3): per sub-step of Eq. Time2 length dt_E (alpha of its initial state,
+// per direction, held for its three stages) the SSP Runge-Kutta stages
+//   X1 = W + dt_E L(W),  X2 = 3/4 W + 1/4 (X1 + dt_E L(X1)),
+//   W' = 1/3 W + 2/3 (X2 + dt_E L(X2)),  L = -(1/dx) sum_dir (psi+ - psi-),
+// X1 and W' in the other ping-pong buffer, X2 in Wt; one cooperative launch,
+// one thread per cell (grid-stride), a bounded grid barrier after each stage.
+template <typename TF, int D>
+__global__ void __launch_bounds__(kBlock) k_euler_weno(Geom g, DevPtrs p) {
+  constexpr int NM = D + 2;
+  __shared__ TF s_amax[3][kBlock / 32];
+  __shared__ double s_dtE;
+  __shared__ TF s_al[3];
+  __shared__ int s_last, s_bad;
+  const long long nc = g.nc;
+  const int tid = threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  TF* Xt = (TF*)p.Wt;
+  double t = 0.0, a0[3] = {0.0, 0.0, 0.0};
+  // R = dt_E L(X) at cell c
+  auto rhs = [&](const TF* X, long long c, const TF al[3], double dtE, TF R[NM]) {
+    int x[3];
+    cell_coords<D>(g, c, x);
+#pragma unroll
+    for (int i = 0; i < NM; ++i) R[i] = TF(0);
+#pragma unroll
+    for (int dir = 0; dir < D; ++dir) {
+      long long st[7];
+      int y[3] = {x[0], x[1], x[2]};
+#pragma unroll
+      for (int o = 0; o < 7; ++o) {
+        y[dir] = bc_index(x[dir] + o - 3, g.nx[dir], g.bc[dir]);
+        st[o] = cell_index(g, y);
+      }
+      weno_dir<TF, D>(X, nc, st, dir, al[dir], R);
+    }
+    const TF k = sizeof(TF) == 8 ? (TF)(dtE / g.dx) : (TF)((float)dtE / (float)g.dx);
+#pragma unroll
+    for (int i = 0; i < NM; ++i) R[i] *= k;
+  };
+  int s = 0;
+  for (;; ++s) {
+    const TF* W = (const TF*)((s & 1) ? p.W1 : p.W0);
+    TF* X = (TF*)((s & 1) ? p.W0 : p.W1);
+    if (tid == 0) {
+      double ad[3], asum = 0.0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) ad[d] = __longlong_as_double((long long)__ldcg(p.aslot + (s % 3) * 3 + d));
+#pragma unroll
+      for (int d = 0; d < D; ++d) asum = __dadd_rn(asum, ad[d]);
+      if (s == 0) a0[0] = ad[0], a0[1] = ad[1], a0[2] = ad[2];
+      if (blockIdx.x == 0)
+        for (int d = 0; d < 3; ++d) p.aslot[((s + 2) % 3) * 3 + d] = 0ull;
+      double dtE = 0.0;
+      int last = 0, bad = 0;
+      if (g.forced_sub > 0) {
+        dtE = g.dt / g.forced_sub;
+        last = s + 1 == g.forced_sub;
+      } else if (!(asum > 0.0)) {
+        bad = 1;
+      } else {
+        const double cfl = sizeof(TF) == 8 ? __ddiv_rn(__dmul_rn(0.5, g.dx), asum)
+                                           : (double)__fdiv_rn(0.5f * (float)g.dx, (float)asum);
+        const double rem = __dsub_rn(g.dt, t);
+        last = cfl >= rem;
+        dtE = last ? rem : cfl;
+      }
+      s_dtE = dtE;
+      for (int d = 0; d < 3; ++d) s_al[d] = (TF)ad[d];
+      s_last = last;
+      s_bad = bad;
+      if (bad && blockIdx.x == 0) set_status(p.status, DVM_ERR_NONPHYSICAL);
+    }
+    __syncthreads();
+    if (s_bad) return;
+    const bool last = s_last != 0;
+    const double dtE = s_dtE;
+    const TF al[3] = {s_al[0], s_al[1], s_al[2]};
+    TF R[NM];
+    // stage 1: X = W + dt_E L(W)
+    for (long long c = blockIdx.x * (long long)blockDim.x + tid; c < nc; c += stride) {
+      rhs(W, c, al, dtE, R);
+#pragma unroll
+      for (int i = 0; i < NM; ++i) X[i * nc + c] = __ldcg(W + i * nc + c) + R[i];
+    }
+    if (!grid_sync(p.gbar, p.status)) return;
+    // stage 2: Xt = 3/4 W + 1/4 (X + dt_E L(X))
+    for (long long c = blockIdx.x * (long long)blockDim.x + tid; c < nc; c += stride) {
+      rhs(X, c, al, dtE, R);
+#pragma unroll
+      for (int i = 0; i < NM; ++i)
+        Xt[i * nc + c] = TF(0.75) * __ldcg(W + i * nc + c) + TF(0.25) * (__ldcg(X + i * nc + c) + R[i]);
+    }
+    if (!grid_sync(p.gbar, p.status)) return;
+    // stage 3: X = 1/3 W + 2/3 (Xt + dt_E L(Xt)), and alpha of the new state
+    TF amax[3] = {TF(0), TF(0), TF(0)};
+    for (long long c = blockIdx.x * (long long)blockDim.x + tid; c < nc; c += stride) {
+      rhs(Xt, c, al, dtE, R);
+      TF Wn[NM];
+#pragma unroll
+      for (int i = 0; i < NM; ++i) {
+        Wn[i] = __ldcg(W + i * nc + c) * TF(1.0 / 3.0) + TF(2.0 / 3.0) * (__ldcg(Xt + i * nc + c) + R[i]);
+        X[i * nc + c] = Wn[i];
+      }
+      if (!last) {
+        TF an[3];
+        state_alpha_of<D>(Wn, an);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) amax[d] = amax[d] > an[d] ? amax[d] : an[d];
+      }
+    }
+    if (tid == 0) t = __dadd_rn(t, dtE);
+    if (last) break;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      TF v = amax[d];
+      for (int o = 16; o > 0; o >>= 1) {
+        const TF w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = v > w ? v : w;
+      }
+      if ((tid & 31) == 0) s_amax[d][tid >> 5] = v;
+    }
+    __syncthreads();
+    if (tid < D) {
+      TF v = TF(0);
+      for (int w = 0; w < kBlock / 32; ++w) v = v > s_amax[tid][w] ? v : s_amax[tid][w];
+      atomicMax(p.aslot + ((s + 1) % 3) * 3 + tid, (unsigned long long)__double_as_longlong((double)v));
+    }
+    if (s + 1 >= g.m_cap) {
+      if (blockIdx.x == 0 && tid == 0) set_status(p.status, DVM_ERR_CFL);
+      break;
+    }
+    if (!grid_sync(p.gbar, p.status)) return;
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    *p.msub = s + 1;
+    for (int d = 0; d < 3; ++d) p.alpha[d] = a0[d];
+  }
+}
+
 // 1D and 2D Euler sub-steps with the split fluxes computed once per staged
 // cell: after a tile and its halo are staged, G+ = F + alpha U and
 // G- = F - alpha U of every staged cell and direction go to shared memory;
@@ -896,6 +1093,31 @@ cudaError_t launch_euler_g(const Geom& g, const DevPtrs& p, cudaStream_t s, bool
   return cudaLaunchKernelEx(&cfg, k_euler_g<TF, LIM, D>, g, p);
 }
 
+template <typename TF, int D>
+cudaError_t launch_euler_weno(const Geom& g, const DevPtrs& p, cudaStream_t s, bool prepare, int* blocks) {
+  if (prepare) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_euler_weno<TF, D>, kBlock, 0);
+    const long long nb = (long long)sms * (per_sm < 1 ? 1 : per_sm);
+    const long long need = (g.nc + kBlock - 1) / kBlock;
+    *blocks = (int)(nb < need ? nb : need);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)g.euler_blocks);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_euler_weno<TF, D>, g, p);
+}
+
 template <typename TF, bool LIM, int D>
 cudaError_t launch_euler_t(const Geom& g, const DevPtrs& p, cudaStream_t s, bool prepare,
                            int* blocks) {
@@ -934,6 +1156,11 @@ cudaError_t euler_dispatch(const Geom& g, const DevPtrs& p, cudaStream_t s, bool
                            int* blocks) {
   const bool lim = g.scheme == DVM_HOFKS;
   cudaError_t e = cudaSuccess;
+  if (g.scheme == DVM_HOFKS_WENO) {
+    if (g.precision == DVM_F64) DVM_BY_DIM(g, e = (launch_euler_weno<double, DD>(g, p, s, prepare, blocks)));
+    else DVM_BY_DIM(g, e = (launch_euler_weno<float, DD>(g, p, s, prepare, blocks)));
+    return e;
+  }
   if (g.precision == DVM_F64) {
     if (lim) DVM_BY_DIM(g, e = (launch_euler_t<double, true, DD>(g, p, s, prepare, blocks)));
     else DVM_BY_DIM(g, e = (launch_euler_t<double, false, DD>(g, p, s, prepare, blocks)));

@@ -85,6 +85,7 @@ struct DevPtrs {
   double* lam;        // nc
   void* W0;           // nm x nc Euler state (ping-pong; FP64 or FP32)
   void* W1;
+  void* Wt;           // nm x nc, the WENO solver's Runge-Kutta stage
   double* acc;        // nsplit x 2nm x nc partial moment sums
   void* prm;          // NP x nc, compute type
   float* wprm;        // 16 x nc, the window pass's per-cell parameters (FP32 tiers, d >= 2)

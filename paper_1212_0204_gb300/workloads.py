@@ -26,7 +26,7 @@ import numpy as np
 SEED_BASE = 1212
 
 PERIODIC, OUTFLOW = 0, 1
-FKS, HOFKS, HOFKS_UNLIMITED = 0, 1, 2
+FKS, HOFKS, HOFKS_UNLIMITED, HOFKS_WENO = 0, 1, 2, 3
 
 
 @dataclass
