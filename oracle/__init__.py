@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SOURCES = ["dvm_oracle.c", "riemann.c", "mlp.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
-FKS, HOFKS, HOFKS_UNLIMITED, HOFKS_WENO = 0, 1, 2, 3
+FKS, HOFKS, HOFKS_UNLIMITED, HOFKS_WENO, FKS_STRANG = 0, 1, 2, 3, 4
 PERIODIC, OUTFLOW = 0, 1
 
 

@@ -4,7 +4,10 @@
  * TEST INFRASTRUCTURE ONLY (see dvm_oracle.h).  Written from the paper:
  *   Section 3       discrete velocity model, moments (Eq. DM)
  *   Section 4.1     conservative projection (Eqs. minim1, minimMax)
- *   Section 4.2     FKS: exact transport, then relaxation (Eq. relaxdvm)
+ *   Section 4.2     FKS: exact transport, then relaxation (Eq. relaxdvm);
+ *                   the Strang splitting the section mentions as the more
+ *                   accurate alternative: half relaxation, transport, half
+ *                   relaxation
  *   Section 4.3.1   HOFKS: relaxation, transport, U_M replaced by U_E
  *                   (Eqs. UK, mom, cons, minim_full)
  *   Section 4.3.2   MUSCL finite volume Euler solver (Eq. discmom)
@@ -44,7 +47,7 @@ static int check_config(const orc_config* g) {
     if (g->bc[i] != ORC_PERIODIC && g->bc[i] != ORC_OUTFLOW) return ORC_ERR_ARG;
   }
   if (!(g->dx > 0) || !(g->dv > 0) || g->p < 1) return ORC_ERR_ARG;
-  if (g->scheme < ORC_FKS || g->scheme > ORC_HOFKS_WENO) return ORC_ERR_ARG;
+  if (g->scheme < ORC_FKS || g->scheme > ORC_FKS_STRANG) return ORC_ERR_ARG;
   if (g->subcycles < 0) return ORC_ERR_ARG;
   return ORC_OK;
 }
@@ -512,6 +515,7 @@ struct orc_state {
   double* C;     /* nm x nv */
   double A[MAXM * MAXM];
   double* lam;   /* nc: lambda = exp(-dt/tau) */
+  double* lamh;  /* nc: exp(-dt/(2 tau)), the half step of the Strang splitting */
   double* f;     /* nv x nc at cell positions */
   double* fnew;  /* nv x nc */
   double* U;     /* nm x nc */
@@ -532,6 +536,7 @@ void orc_destroy(orc_state* S) {
   if (!S) return;
   free(S->C);
   free(S->lam);
+  free(S->lamh);
   free(S->f);
   free(S->fnew);
   free(S->U);
@@ -561,6 +566,7 @@ orc_state* orc_create(const orc_config* g, const double* tau,
   const size_t mom = sizeof(double) * (size_t)S->nc * (size_t)S->nm;
   S->C = malloc(sizeof(double) * S->nm * S->nv);
   S->lam = malloc(sizeof(double) * S->nc);
+  S->lamh = malloc(sizeof(double) * S->nc);
   S->f = calloc(1, phase);
   S->fnew = calloc(1, phase);
   S->Eq = calloc(1, phase);
@@ -572,7 +578,7 @@ orc_state* orc_create(const orc_config* g, const double* tau,
   S->W1 = calloc(1, mom);
   S->tmpM = malloc(sizeof(double) * S->nv);
   S->tmpF = malloc(sizeof(double) * S->nv);
-  if (!S->C || !S->lam || !S->f || !S->fnew || !S->Eq || !S->U || !S->UE ||
+  if (!S->C || !S->lam || !S->lamh || !S->f || !S->fnew || !S->Eq || !S->U || !S->UE ||
       !S->UM || !S->Us || !S->W0 || !S->W1 || !S->tmpM || !S->tmpF ||
       orc_matrices(g, S->C, S->A)) {
     orc_destroy(S);
@@ -582,6 +588,7 @@ orc_state* orc_create(const orc_config* g, const double* tau,
   for (long c = 0; c < S->nc; ++c) {
     const double t = tau ? tau[c] : tau_uniform;
     S->lam[c] = exp(-S->dt / t);
+    S->lamh[c] = exp(-S->dt / (2.0 * t));
   }
   return S;
 }
@@ -816,9 +823,51 @@ static int step_fks(orc_state* S) {
   return ORC_OK;
 }
 
+/* Relaxation over half a step at every cell (Eq. relaxdvm over dt/2):
+ * f <- lambda_h f + (1 - lambda_h) E[U], U the moments of f at the cell,
+ * lambda_h = exp(-dt/(2 tau)).  Leaves U in S->U. */
+static int relax_half(orc_state* S) {
+  const long nc = S->nc, nv = S->nv;
+  const int nm = S->nm;
+  for (long c = 0; c < nc; ++c)
+    for (int i = 0; i < nm; ++i) {
+      double s = 0.0;
+      for (long k = 0; k < nv; ++k) s += S->C[i * nv + k] * S->f[k * nc + c];
+      S->U[i * nc + c] = s;
+    }
+  int rc = equilibria(S, S->U);
+  if (rc) return rc;
+  for (long k = 0; k < nv; ++k)
+    for (long c = 0; c < nc; ++c) {
+      const double l = S->lamh[c];
+      S->f[k * nc + c] = l * S->f[k * nc + c] + (1.0 - l) * S->Eq[k * nc + c];
+    }
+  return ORC_OK;
+}
+
+/* FKS with Strang splitting (Section 4.2 names it as the alternative to the
+ * first-order splitting): relaxation over dt/2, exact transport over dt,
+ * relaxation over dt/2. */
+static int step_fks_strang(orc_state* S) {
+  const long nc = S->nc, nv = S->nv;
+  int rc = relax_half(S);
+  if (rc) return rc;
+  for (long c = 0; c < nc; ++c)
+    for (long k = 0; k < nv; ++k)
+      S->fnew[k * nc + c] = S->f[k * nc + source_cell(S, c, k)];
+  double* t = S->f;
+  S->f = S->fnew;
+  S->fnew = t;
+  rc = relax_half(S);
+  S->last_m = 0;
+  return rc;
+}
+
 int orc_step(orc_state* S, int nsteps) {
   for (int s = 0; s < nsteps; ++s) {
-    int rc = (S->g.scheme == ORC_FKS) ? step_fks(S) : step_hofks(S);
+    int rc = (S->g.scheme == ORC_FKS)          ? step_fks(S)
+             : (S->g.scheme == ORC_FKS_STRANG) ? step_fks_strang(S)
+                                               : step_hofks(S);
     if (rc) return rc;
     S->n += 1;
     for (long c = 0; c < S->nc; ++c) {
@@ -848,7 +897,7 @@ int orc_step(orc_state* S, int nsteps) {
  *         (keep_raw = 1: the one-step check of a flag).
  * A flag on a cell with lambda = 1 (tau = inf) is ignored.  HOFKS only. */
 int orc_step_flagged(orc_state* S, const unsigned char* flags, int keep_raw) {
-  if (S->g.scheme == ORC_FKS) return ORC_ERR_ARG;
+  if (S->g.scheme == ORC_FKS || S->g.scheme == ORC_FKS_STRANG) return ORC_ERR_ARG;
   const long nc = S->nc, nv = S->nv;
   const int nm = S->nm;
   double* lam_eff = malloc(sizeof(double) * nc);
@@ -990,6 +1039,7 @@ orc_state* orc_clone(const orc_state* S) {
   const size_t phase = sizeof(double) * (size_t)S->nc * (size_t)S->nv;
   const size_t mom = sizeof(double) * (size_t)S->nc * (size_t)S->nm;
   memcpy(T->lam, S->lam, sizeof(double) * S->nc);
+  memcpy(T->lamh, S->lamh, sizeof(double) * S->nc);
   memcpy(T->f, S->f, phase);
   memcpy(T->U, S->U, mom);
   memcpy(T->UE, S->UE, mom);

@@ -34,6 +34,7 @@ extern "C" {
 #define ORC_HOFKS 1
 #define ORC_HOFKS_UNLIMITED 2
 #define ORC_HOFKS_WENO 3 /* HOFKS with the WENO5 Euler solver of Section 4.3.3 */
+#define ORC_FKS_STRANG 4 /* FKS with Strang splitting (Section 4.2) */
 
 #define ORC_PERIODIC 0
 #define ORC_OUTFLOW 1

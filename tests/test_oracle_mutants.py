@@ -83,6 +83,18 @@ WENO_MUTANTS = [
 ]
 
 
+# the Strang splitting of FKS (Section 4.2), against tests/test_oracle_strang.py
+STRANG_MUTANTS = [
+    ("Strang half step with the full-step factor exp(-dt/tau)",
+     "dvm_oracle.c", "S->lamh[c] = exp(-S->dt / (2.0 * t));", "S->lamh[c] = exp(-S->dt / t);"),
+    ("Strang step without its first half relaxation",
+     "dvm_oracle.c", "int rc = relax_half(S);", "int rc = 0;"),
+    ("half relaxation with the weights swapped",
+     "dvm_oracle.c", "S->f[k * nc + c] = l * S->f[k * nc + c] + (1.0 - l) * S->Eq[k * nc + c];",
+     "S->f[k * nc + c] = (1.0 - l) * S->f[k * nc + c] + l * S->Eq[k * nc + c];"),
+]
+
+
 def oracle_copy(tmp_path, mutant=None):
     dst = tmp_path / "oracle"
     shutil.copytree(os.path.join(ROOT, "oracle"), dst,
@@ -110,7 +122,8 @@ def pins_against(tmp_path, module="test_oracle_pins.py"):
                              "-p", "no:cacheprovider", "-k", "not isentropic_vortex"])
 
 
-@pytest.mark.parametrize("module", ["test_oracle_pins.py", "test_oracle_learned.py", "test_oracle_weno.py"])
+@pytest.mark.parametrize("module", ["test_oracle_pins.py", "test_oracle_learned.py", "test_oracle_weno.py",
+                                    "test_oracle_strang.py"])
 def test_unmodified_copy_passes_the_pins(tmp_path, module):
     r = pins_against(oracle_copy(tmp_path), module)
     assert r.returncode == 0, r.stdout[-3000:]
@@ -131,4 +144,10 @@ def test_planted_mistake_in_the_learned_path_fails_a_pin(tmp_path, mutant):
 @pytest.mark.parametrize("mutant", WENO_MUTANTS, ids=[m[0][:40] for m in WENO_MUTANTS])
 def test_planted_mistake_in_the_weno_solver_fails_a_pin(tmp_path, mutant):
     r = pins_against(oracle_copy(tmp_path, mutant), "test_oracle_weno.py")
+    assert r.returncode == 1 and " failed" in r.stdout, (mutant[0], r.returncode, r.stdout[-3000:])
+
+
+@pytest.mark.parametrize("mutant", STRANG_MUTANTS, ids=[m[0][:40] for m in STRANG_MUTANTS])
+def test_planted_mistake_in_the_strang_splitting_fails_a_pin(tmp_path, mutant):
+    r = pins_against(oracle_copy(tmp_path, mutant), "test_oracle_strang.py")
     assert r.returncode == 1 and " failed" in r.stdout, (mutant[0], r.returncode, r.stdout[-3000:])
