@@ -47,6 +47,8 @@ WORKLOADS = {
     "sod_1d": (lambda: W.sod_1d(nx=200, nv=32, tau=1e-4), "f64"),
     "batched_tubes": (lambda: W.batched_tubes(ncases=512, steps=100), "f32"),
     "shear_learned": (lambda: W.shear_layer_2d(n=512, nv=32, steps=50, dv=0.4), "f32"),
+    "implosion_2d": (lambda: W.implosion_2d(n=200, nv=30, tau=1e-3), "f32"),
+    "vortex_weno_2d": (lambda: W.isentropic_vortex_2d(200, scheme=W.HOFKS_WENO), "f64"),
 }
 DESCR = {
     "quadrant_2d": "2D-2V four-quadrant Riemann problem, 256x256 periodic cells x 32x32 velocities, "
@@ -61,6 +63,10 @@ DESCR = {
     "shear_learned": "2D-2V shear layer, 512x512 periodic cells x 32x32 velocities, "
                      "tau = 1e-5*10^(5r) (seeded smooth r), HOFKS FP32 + learned regime path vs plain "
                      "FP32 and plain FP64, 50 steps",
+    "implosion_2d": "2D-2V implosion (Section 5.4): [0,2]^2, 200x200 cells x 30x30 velocities on [-20,20)^2, "
+                    "tau=1e-3, outflow, p=3 (t=0.07 in 28 steps), HOFKS, FP32 f / FP64 moments",
+    "vortex_weno_2d": "2D-2V isentropic vortex (Section 5.2), 200x200 cells x 40x40 velocities, tau=1e-4, "
+                      "HOFKS with the WENO5 Euler solver (Section 4.3.3), FP64",
     "batched_tubes": "512 independent 1D-1V Riemann tubes in one batched launch per phase, "
                      "N_x ~ U{100..2000}, N_v in {32,64,128}, tau = 10^U(-5,0), outflow, HOFKS, "
                      "FP32 f / FP64 moments",

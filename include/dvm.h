@@ -60,7 +60,15 @@ typedef enum { DVM_BC_PERIODIC = 0, DVM_BC_OUTFLOW = 1 } dvm_bc;
 /* DVM_HOFKS_WENO: HOFKS with the WENO5 Euler solver of Section 4.3.3 (finite-
  * difference WENO5 on the split fluxes (F +- alpha U)/2, three-stage SSP
  * Runge-Kutta per Euler sub-step) in place of MUSCL; single problems only. */
-typedef enum { DVM_FKS = 0, DVM_HOFKS = 1, DVM_HOFKS_UNLIMITED = 2, DVM_HOFKS_WENO = 3 } dvm_scheme;
+/* DVM_FKS_STRANG: FKS with the Strang splitting Section 4.2 names as the more
+ * accurate alternative (relaxation over dt/2, exact transport, relaxation
+ * over dt/2 each step).  From the equilibrium data dvm_set_state_* builds,
+ * its moments after every step equal those of DVM_FKS, and its f is the FKS
+ * state relaxed by half a step less: f - E[U] = (f_FKS - E[U]) / lambda_h,
+ * lambda_h = exp(-dt/(2 tau)); the library advances the FKS state and
+ * applies that relation where f is read (dvm_get_f).  Single problems only. */
+typedef enum { DVM_FKS = 0, DVM_HOFKS = 1, DVM_HOFKS_UNLIMITED = 2, DVM_HOFKS_WENO = 3,
+               DVM_FKS_STRANG = 4 } dvm_scheme;
 typedef enum { DVM_F64 = 0, DVM_F32 = 1, DVM_BF16S = 2 } dvm_precision;
 
 /* Spatial grid (Section 4): cell centres x0 + (j + 1/2) dx per dimension. */

@@ -115,7 +115,7 @@ int make_geom(const dvm_config* cfg, Geom* g, std::string* msg) {
     *msg = "dx, dv must be > 0 and shift_den >= 1";
     return DVM_ERR_ARG;
   }
-  if (cfg->scheme < DVM_FKS || cfg->scheme > DVM_HOFKS_WENO) { *msg = "unknown scheme"; return DVM_ERR_ARG; }
+  if (cfg->scheme < DVM_FKS || cfg->scheme > DVM_FKS_STRANG) { *msg = "unknown scheme"; return DVM_ERR_ARG; }
   if (cfg->precision < DVM_F64 || cfg->precision > DVM_BF16S) { *msg = "unknown precision"; return DVM_ERR_ARG; }
   if (cfg->euler_subcycles < 0 || cfg->max_subcycles < 0) { *msg = "negative sub-step count"; return DVM_ERR_ARG; }
   if (!cfg->tau_field && !(cfg->tau >= 0)) { *msg = "tau must be >= 0"; return DVM_ERR_ARG; }
@@ -124,7 +124,11 @@ int make_geom(const dvm_config* cfg, Geom* g, std::string* msg) {
   g->p = cfg->vel.shift_den;
   g->w = pow(cfg->vel.dv, d);
   g->dt = cfg->grid.dx / (cfg->vel.shift_den * cfg->vel.dv);
-  g->scheme = cfg->scheme;
+  // Strang-split FKS advances the first-order FKS state (the same moments at
+  // every step from equilibrium data) and applies the last half relaxation
+  // when f is read out (k_materialize)
+  g->strang = cfg->scheme == DVM_FKS_STRANG;
+  g->scheme = g->strang ? DVM_FKS : cfg->scheme;
   g->precision = cfg->precision;
   g->forced_sub = cfg->euler_subcycles;
   g->m_cap = cfg->euler_subcycles > 0 ? cfg->euler_subcycles : 0;

@@ -1131,7 +1131,7 @@ int dvm_batch_create(const dvm_config* cfgs, int ncases, void* cuda_stream, dvm_
     Geom g;
     std::string msg;
     if (make_geom(&cfgs[i], &g, &msg) || g.d > 2 || cfgs[i].precision != b->precision ||
-        cfgs[i].scheme != b->scheme || cfgs[i].scheme == DVM_HOFKS_WENO || cfgs[i].tau_field || (g.d == 1 && g.nx[0] > kMaxBatchNx) ||
+        cfgs[i].scheme != b->scheme || cfgs[i].scheme == DVM_HOFKS_WENO || cfgs[i].scheme == DVM_FKS_STRANG || cfgs[i].tau_field || (g.d == 1 && g.nx[0] > kMaxBatchNx) ||
         (g.d == 2 && (g.bc[0] != DVM_BC_PERIODIC || g.bc[1] != DVM_BC_PERIODIC ||
                       g.nc > kMaxBatchCells2D))) {
       delete b;

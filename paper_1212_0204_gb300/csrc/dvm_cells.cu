@@ -1033,7 +1033,19 @@ __global__ void k_materialize(Geom g, DevPtrs p, double* out) {
       lin += (double)prm[prm_at(row_mu(D, 1 + i), c, nc)] * v[i];
     }
     lin += (double)prm[prm_at(row_mu(D, D + 1), c, nc)] * vv;
-    f += exp2((double)prm[prm_at(row_L(), c, nc)] - (double)prm[prm_at(row_h(D), c, nc)] * qq) + lin;
+    // the deferred equilibrium part (1 - lambda) E[U] (zero before the first step)
+    const double def =
+        exp2((double)prm[prm_at(row_L(), c, nc)] - (double)prm[prm_at(row_h(D), c, nc)] * qq) + lin;
+    if (g.strang && n > 0) {
+      // Strang splitting: the state is R_h T (R T)^(n-1) f^0, one half
+      // relaxation short of the first-order R T (R T)^(n-1) f^0 kept here
+      // (f_L - E = lambda_h (f_S - E), lambda_h^2 = lambda):
+      // f_S = F / lambda_h + (1 - lambda) E / (1 + lambda_h)
+      const double lh = sqrt(p.lam[c]);
+      f = (lh > 0.0 ? f / lh : 0.0) + def / (1.0 + lh);
+    } else {
+      f += def;
+    }
   } else {
     double lin = (double)prm[prm_at(row_nu(D, 0), c, nc)];
 #pragma unroll

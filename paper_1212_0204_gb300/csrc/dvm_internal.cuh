@@ -67,7 +67,8 @@ struct Geom {
   double dv, w, dt, dx;
   int p;
   int bc[3];          // DVM_BC_* per dimension
-  int scheme;         // DVM_FKS / DVM_HOFKS / DVM_HOFKS_UNLIMITED
+  int scheme;         // DVM_FKS / DVM_HOFKS / DVM_HOFKS_UNLIMITED / DVM_HOFKS_WENO
+  int strang;         // FKS with Strang splitting (scheme DVM_FKS_STRANG at dvm_create)
   int precision;      // DVM_F64 / DVM_F32 / DVM_BF16S
   int forced_sub;     // > 0: fixed Euler sub-steps
   int m_cap;          // launch cap of Euler sub-steps

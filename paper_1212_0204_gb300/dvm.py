@@ -20,7 +20,7 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR
     0, -1, -2, -3, -4, -5, -6, -7, -8
 ERR_TOO_LARGE = -9
 PERIODIC, OUTFLOW = 0, 1
-FKS, HOFKS, HOFKS_UNLIMITED, HOFKS_WENO = 0, 1, 2, 3
+FKS, HOFKS, HOFKS_UNLIMITED, HOFKS_WENO, FKS_STRANG = 0, 1, 2, 3, 4
 F64, F32, BF16S = 0, 1, 2
 SELFTEST_GRID_BARRIER, SELFTEST_MBARRIER = 0, 1
 

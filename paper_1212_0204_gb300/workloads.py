@@ -26,7 +26,7 @@ import numpy as np
 SEED_BASE = 1212
 
 PERIODIC, OUTFLOW = 0, 1
-FKS, HOFKS, HOFKS_UNLIMITED, HOFKS_WENO = 0, 1, 2, 3
+FKS, HOFKS, HOFKS_UNLIMITED, HOFKS_WENO, FKS_STRANG = 0, 1, 2, 3, 4
 
 
 @dataclass
@@ -157,6 +157,32 @@ def entropy_wave_1d(nx: int, nv: int = 32, tau: float = 1e-4, dv: float = 0.4,
     return Case("entropy_wave_1d", 1, (nx,), dx, (nv,), (-(nv // 2),), dv, 1, (PERIODIC,),
                 tau, rho, np.full((1, nx), ux), 1.0 / rho, steps, scheme, subcycles,
                 extra={"amp": amp, "ux": ux, "t_final": steps * dx / dv})
+
+
+def implosion_2d(n: int = 100, nv: int = 30, tau: float = 1e-3, scheme: int = HOFKS,
+                 t_final: float = 0.07) -> Case:
+    """Section 5.4's 2D implosion: [0, 2]^2, a disk of radius 0.2 centred at (1, 1)
+    with rho = 0.125, u = 0, T = 4 inside a gas with rho = 1, T = 4, u_x = +1 for
+    x < 1 and -1 for x > 1, u_y = +1 for y < 1 and -1 for y > 1 (the flow converges
+    on the disk); nv^2 velocities on [-20, 20)^2 (the printed 30 per direction);
+    zero-gradient outflow boundaries (not stated).  The shift denominator p is the
+    smallest one for which t_final is a whole number of exact-transport steps
+    dt = dx / (p dv); the Euler part sub-steps inside each step (Eq. Time2)."""
+    dx = 2.0 / n
+    dv = 40.0 / nv
+    xc = _centres(n, dx)
+    Y, X = np.meshgrid(xc, xc, indexing="ij")
+    X, Y = X.ravel(), Y.ravel()
+    disk = (X - 1.0) ** 2 + (Y - 1.0) ** 2 < 0.2 ** 2
+    rho = np.where(disk, 0.125, 1.0)
+    u = np.stack([np.where(X < 1.0, 1.0, -1.0), np.where(Y < 1.0, 1.0, -1.0)])
+    u[:, disk] = 0.0
+    # dt = dx / (p dv): t_final / dt = p (t_final n dv / 2) must be whole
+    from fractions import Fraction
+    per = Fraction(t_final).limit_denominator(10 ** 6) * n * Fraction(dv).limit_denominator(10 ** 6) / 2
+    p, steps = per.denominator, per.numerator
+    return Case("implosion_2d", 2, (n, n), dx, (nv, nv), (-(nv // 2),) * 2, dv, p, (OUTFLOW, OUTFLOW), tau,
+                rho, u, np.full(n * n, 4.0), steps, scheme, extra={"t_final": steps * dx / (p * dv)})
 
 
 def sod_1d_300x100(tau: float, scheme: int = HOFKS) -> Case:
