@@ -44,6 +44,7 @@ WORKLOADS = {
     "density_wave_3d_64": (lambda: W.density_wave_3d(n=64, nv=24, tau=1e-4, steps=100), "f32"),
     "quadrant_2d_f64": (lambda: W.quadrant_2d(n=256, nv=32, tau=1e-3, steps=500), "f64"),
     "quadrant_2d_bf16": (lambda: W.quadrant_2d(n=256, nv=32, tau=1e-3, steps=500), "bf16"),
+    "density_wave_3d_bf16": (lambda: W.density_wave_3d(n=96, nv=24, tau=1e-4, steps=100), "bf16"),
     "sod_1d": (lambda: W.sod_1d(nx=200, nv=32, tau=1e-4), "f64"),
     "batched_tubes": (lambda: W.batched_tubes(ncases=512, steps=100), "f32"),
     "shear_learned": (lambda: W.shear_layer_2d(n=512, nv=32, steps=50, dv=0.4), "f32"),
@@ -59,6 +60,8 @@ DESCR = {
                           "FP32 f / FP64 moments",
     "quadrant_2d_f64": "2D-2V four-quadrant Riemann problem, 256^2 x 32^2, HOFKS, FP64 f",
     "quadrant_2d_bf16": "2D-2V four-quadrant Riemann problem, 256^2 x 32^2, HOFKS, BF16 f storage",
+    "density_wave_3d_bf16": "3D-3V periodic density wave, 96^3 cells x 24^3 velocities, tau=1e-4, HOFKS, "
+                            "BF16 f storage / FP32 arithmetic / FP64 moments",
     "sod_1d": "1D-1V Sod tube, 200 cells x 32 velocities, tau=1e-4, outflow, HOFKS, FP64",
     "shear_learned": "2D-2V shear layer, 512x512 periodic cells x 32x32 velocities, "
                      "tau = 1e-5*10^(5r) (seeded smooth r), HOFKS FP32 + learned regime path vs plain "

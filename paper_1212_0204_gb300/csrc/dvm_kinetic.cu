@@ -283,10 +283,11 @@ void launch_window_a(const Geom& g, const DevPtrs& p, const WinLaunch& wl, cudaS
 
 template <typename TS, int D, bool HO>
 void launch_window_t(const Geom& g, const DevPtrs& p, const WinLaunch& wl, cudaStream_t s, bool prepare) {
-  if constexpr (sizeof(TS) == 4) {
-    if (prepare) launch_window_a<TS, D, HO, true>(g, p, wl, s, true);
-    else if (window_async(D)) return launch_window_a<TS, D, HO, true>(g, p, wl, s, false);
-  }
+  // staged f loads: FP32, and BF16 when N_x is even (a value's half of its
+  // staged 4-byte word is then the parity of its x piece)
+  if (prepare) launch_window_a<TS, D, HO, true>(g, p, wl, s, true);
+  else if (window_async(D) && (sizeof(TS) == 4 || g.nx[0] % 2 == 0))
+    return launch_window_a<TS, D, HO, true>(g, p, wl, s, false);
   launch_window_a<TS, D, HO, false>(g, p, wl, s, prepare);
 }
 

@@ -32,6 +32,19 @@ __device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
+// BF16 storage: the aligned 4-byte word holding the value (cp.async copies
+// 4, 8 or 16 bytes); the reader takes the half that the value's parity names.
+__device__ __forceinline__ void cp_async4(float* smem, const __nv_bfloat16* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const unsigned long long a = (unsigned long long)(uintptr_t)gmem & ~3ull;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(a) : "memory");
+}
+// value of a staged slot: FP32 as is, BF16 from the half of the staged word
+__device__ __forceinline__ float staged_value(const float* slot, int half, float*) { return *slot; }
+__device__ __forceinline__ float staged_value(const float* slot, int half, __nv_bfloat16*) {
+  const unsigned w = __float_as_uint(*slot);
+  return __uint_as_float((half ? w & 0xffff0000u : w << 16));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -185,7 +198,7 @@ __global__ void __launch_bounds__(32 * WinShape<D>::S, WinShape<D>::MINB)
   // FP32 storage: the F values of a block of Y velocities x Y targets go
   // through shared memory by cp.async, one block ahead of the arithmetic
   // (more loads in flight than registers allow; no register holds them)
-  static_assert(!ASYNC || sizeof(TS) == 4, "cp.async staging is for FP32 storage");
+  // (BF16 with N_x even: a value's word half is the parity of its x piece)
   float* s_fb = reinterpret_cast<float*>(s_mid + NA * Y);  // [2][Y][Y][kWinT]
   int stage = 0;
   auto issue = [&](int base_i, int kb_i, int st) {
@@ -199,8 +212,7 @@ __global__ void __launch_bounds__(32 * WinShape<D>::S, WinShape<D>::MINB)
       qz_i = z - s_oz[kz_i];
       if (qz_i < 0) qz_i += Nz;
     }
-    const float* Fb_i = reinterpret_cast<const float*>(F) +
-                        ((long long)kx_i + (long long)nvx * nvy * kz_i) * nc + qx_i + plane * qz_i;
+    const TS* Fb_i = F + ((long long)kx_i + (long long)nvx * nvy * kz_i) * nc + qx_i + plane * qz_i;
     // every address is a valid one (x clamped, rows wrapped): inactive
     // targets copy a value nobody reads instead of taking a predicate
     int rr[Y];
@@ -216,14 +228,14 @@ __global__ void __launch_bounds__(32 * WinShape<D>::S, WinShape<D>::MINB)
     if (nowrap) {  // no periodic wrap among the rows of the block (CTA-uniform)
 #pragma unroll
       for (int jj = 0; jj < Y; ++jj) {
-        const float* Fr = Fb_i + (long long)(kb_i - jj) * kystep + rr[jj] * Nx;
+        const TS* Fr = Fb_i + (long long)(kb_i - jj) * kystep + rr[jj] * Nx;
 #pragma unroll
         for (int j = 0; j < Y; ++j) cp_async4(dst + (jj * Y + j) * kWinT, Fr + j * Nx);
       }
     } else {
 #pragma unroll
       for (int jj = 0; jj < Y; ++jj) {
-        const float* Fk = Fb_i + (long long)(kb_i - jj) * kystep;
+        const TS* Fk = Fb_i + (long long)(kb_i - jj) * kystep;
         int r = rr[jj];
 #pragma unroll
         for (int j = 0; j < Y; ++j) {
@@ -329,7 +341,8 @@ __global__ void __launch_bounds__(32 * WinShape<D>::S, WinShape<D>::MINB)
           float fj[Y];
 #pragma unroll
           for (int j = 0; j < Y; ++j)
-            fj[j] = ASYNC ? s_fb[((stage * Y + jj) * Y + j) * kWinT + tid] : fv[ASYNC ? 0 : jj][j];
+            fj[j] = ASYNC ? staged_value(&s_fb[((stage * Y + jj) * Y + j) * kWinT + tid], qx & 1, (TS*)nullptr)
+                          : fv[ASYNC ? 0 : jj][j];
           const float vy = (g.kmin[1] + ky) * dv;
           const float vy2 = vy * vy;
           float fn[Y];

@@ -299,3 +299,40 @@ def test_3d_shape_compiled_pass_equals_runtime_pass_at_bench_sizes(n, monkeypatc
     assert np.array_equal(out[0][0], out[1][0])
     for a, b in zip(out[0][1], out[1][1]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("make", [
+    lambda: W.quadrant_2d(n=36, nv=16, tau=1e-3, steps=3, dv=0.7),
+    lambda: W.density_wave_3d(n=10, nv=8, tau=1e-2, steps=2, dv=1.2),
+], ids=["quadrant_36", "wave_3d_10"])
+def test_bf16_staged_loads_equal_direct_loads(make, monkeypatch):
+    """BF16 storage with N_x even stages the 4-byte word holding each value and
+    takes the half named by the parity of its x piece: the same values as the
+    direct 2-byte loads (DVM_WIN_ASYNC=0), so moments and f agree bit for bit;
+    and the error against the FP64 oracle stays within the BF16 bound."""
+    case = make()
+    out = []
+    for mode in ("1", "0"):
+        monkeypatch.setenv("DVM_WIN_ASYNC", mode)
+        s = gpu_run(case, case.steps, dvm.BF16S)
+        out.append((s.moments(), s.f()))
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    orc = oracle.Scheme(grid(case), tau=case.tau)
+    orc.set_moments(conserved(case))
+    orc.step(case.steps)
+    assert moment_err(out[0][0], orc.moments()) <= 8 * 2.0 ** -9
+
+
+def test_bf16_free_transport_with_staged_loads_is_bit_exact():
+    case = W.quadrant_2d(n=20, nv=8, tau=np.inf, steps=5, dv=0.9)
+    s = dvm.Solver.from_case(case, precision=dvm.BF16S)
+    s.set_moments(conserved(case))
+    f0 = s.f().reshape(case.nvel, 20, 20)
+    s.step(5)
+    kk = velocity_indices(grid(case))
+    expect = np.empty_like(f0)
+    for k in range(case.nvel):
+        ox, oy = oracle.offset(int(kk[0, k]), 5, 1), oracle.offset(int(kk[1, k]), 5, 1)
+        expect[k] = np.roll(np.roll(f0[k], oy, axis=0), ox, axis=1)
+    assert np.array_equal(s.f().reshape(expect.shape), expect)
