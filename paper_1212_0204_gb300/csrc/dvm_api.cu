@@ -144,7 +144,7 @@ int make_geom(const dvm_config* cfg, Geom* g, std::string* msg) {
 namespace {
 
 struct Layout {
-  size_t F, ghost, U, lam, W0, W1, Wt, acc, prm, wprm, eqp, UE, UM, Us, A, small, offs, total;
+  size_t F, ghost, U, lam, W0, W1, Wt, acc, prm, wprm, eqp, gtab, UE, UM, Us, A, small, offs, total;
 };
 
 Layout layout(const Geom& g) {
@@ -165,6 +165,9 @@ Layout layout(const Geom& g) {
   L.prm = take(tc * (size_t)prm_rows(g.d) * nc);
   L.wprm = take(g.d >= 2 && g.precision != DVM_F64 ? 4 * 16 * nc : 0);
   L.eqp = take(8 * (size_t)prm_rows(g.d) * nc);
+  L.gtab = take(g.precision == DVM_F64 ? 8 * nc * (size_t)(1 + g.nv[0] + (g.d > 1 ? g.nv[1] : 0) +
+                                                           (g.d > 2 ? g.nv[2] : 0))
+                                       : 0);
   L.UE = take(8 * nm * nc);
   L.UM = take(8 * nm * nc);
   L.Us = take(8 * nm * nc);
@@ -238,6 +241,7 @@ void bind(dvm_handle* h, char* base, const Layout& L) {
   p.prm = base + L.prm;
   p.wprm = (float*)(base + L.wprm);
   p.eqp = (double*)(base + L.eqp);
+  p.gtab = (double*)(base + L.gtab);
   p.UE = (double*)(base + L.UE);
   p.UM = (double*)(base + L.UM);
   p.Us = (double*)(base + L.Us);
@@ -804,7 +808,8 @@ int dvm_launches_per_step(dvm_handle* h, int* launches) {
   int n = 0;
   if (h->g.scheme != DVM_FKS && !h->g.skip_euler) n += 1;
   if (h->g.ghost_mode) n += 1;
-  n += kinetic_is_windowed(h->g) ? 2 : 1;  // (folded parameters +) kinetic pass
+  // (folded parameters or the FP64 Maxwellian factors +) kinetic pass
+  n += (kinetic_is_windowed(h->g) || h->g.precision == DVM_F64) ? 2 : 1;
   n += 1;                                  // end-of-step kernel
   *launches = n;
   return 0;

@@ -91,6 +91,7 @@ struct DevPtrs {
   void* prm;          // NP x nc, compute type
   float* wprm;        // 16 x nc, the window pass's per-cell parameters (FP32 tiers, d >= 2)
   double* eqp;        // NP x nc, FP64 parameters of E[U] (initial state only)
+  double* gtab;       // FP64 build: (1 + sum_i nv_i) x nc separable Maxwellian factors (k_gauss_tables)
   double* UE;         // nm x nc, last step's U_E (FP64 copy)
   double* UM;         // nm x nc, last step's U_M
   double* Us;         // nm x nc, last step's U_*

@@ -114,14 +114,26 @@ __global__ void __launch_bounds__(kThreads) k_kpass_generic(Geom g, DevPtrs p) {
         qs[i] = wrap((long long)s[i] - s_slot[i][kk[i]] + s_delta[i][kk[i]], g.nx[i]);
       fv = StoreT<TS>::load(G + k * nc + qs[0] + (long long)g.nx[0] * (qs[1] + (long long)g.nx[1] * qs[2]));
     }
-    // parameters of the source cell
-    TC qq = TC(0);
+    // parameters of the source cell; the Maxwellian (Eq. M) from its
+    // separable factors in the FP64 build (k_gauss_tables), else one exp2
+    TC M;
+    if constexpr (sizeof(TC) == 8) {
+      M = p.gtab[src];
+      int off = 1;
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-      const TC du = v[i] - prm[prm_at(row_u(i), src, nc)];
-      qq += du * du;
+      for (int i = 0; i < D; ++i) {
+        M *= p.gtab[(long long)(off + kk[i]) * nc + src];
+        off += g.nv[i];
+      }
+    } else {
+      TC qq = TC(0);
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        const TC du = v[i] - prm[prm_at(row_u(i), src, nc)];
+        qq += du * du;
+      }
+      M = fexp2<TC>(prm[prm_at(row_L(), src, nc)] - prm[prm_at(row_h(D), src, nc)] * qq);
     }
-    const TC M = fexp2<TC>(prm[prm_at(row_L(), src, nc)] - prm[prm_at(row_h(D), src, nc)] * qq);
     TC lin_mu = prm[prm_at(row_mu(D, 0), src, nc)] + prm[prm_at(row_mu(D, D + 1), src, nc)] * (vv + vv);
 #pragma unroll
     for (int i = 0; i < D; ++i) lin_mu += prm[prm_at(row_mu(D, 1 + i), src, nc)] * v[i];
@@ -162,6 +174,30 @@ __global__ void __launch_bounds__(kThreads) k_kpass_generic(Geom g, DevPtrs p) {
   double* out = p.acc + (long long)blockIdx.y * 2 * NM * nc + c;
 #pragma unroll
   for (int j = 0; j < NACC; ++j) out[j * nc] = acc[j] + (double)racc[j];
+}
+
+// FP64 build: the separable factors of every cell's Maxwellian (Eq. M),
+// 2^L and exp2(-h (v_k - u_i)^2) per dimension i and velocity index k, from
+// the parameters the kinetic pass is about to use (the Gaussian of |v - u|^2
+// is the product of its per-dimension factors): the pass then forms M with
+// d multiplications instead of an FP64 exp2 per phase-space point.
+template <int D>
+__global__ void __launch_bounds__(256) k_gauss_tables(Geom g, DevPtrs p) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nc = g.nc;
+  if (c >= nc) return;
+  const double* prm = (const double*)p.prm;
+  const double h = prm[prm_at(row_h(D), c, nc)];
+  p.gtab[c] = exp2(prm[prm_at(row_L(), c, nc)]);
+  long long row = 1;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const double u = prm[prm_at(row_u(i), c, nc)];
+    for (int k = 0; k < g.nv[i]; ++k, ++row) {
+      const double du = (double)(g.kmin[i] + k) * g.dv - u;
+      p.gtab[row * nc + c] = exp2(-h * (du * du));
+    }
+  }
 }
 
 // One thread per cell: the parameter rows folded into the window layout of
@@ -355,8 +391,15 @@ int launch_kinetic_pass(const Geom& g, const DevPtrs& p, cudaStream_t s) {
     else launch_window<__nv_bfloat16>(g, p, s);
     return 2;
   }
-  if (g.precision == DVM_F64) launch_generic<double, double>(g, p, s);
-  else if (g.precision == DVM_F32) launch_generic<float, float>(g, p, s);
+  if (g.precision == DVM_F64) {
+    const unsigned nb = (unsigned)((g.nc + 255) / 256);
+    if (g.d == 1) k_gauss_tables<1><<<nb, 256, 0, s>>>(g, p);
+    else if (g.d == 2) k_gauss_tables<2><<<nb, 256, 0, s>>>(g, p);
+    else k_gauss_tables<3><<<nb, 256, 0, s>>>(g, p);
+    launch_generic<double, double>(g, p, s);
+    return 2;
+  }
+  if (g.precision == DVM_F32) launch_generic<float, float>(g, p, s);
   else launch_generic<__nv_bfloat16, float>(g, p, s);
   return 1;
 }
