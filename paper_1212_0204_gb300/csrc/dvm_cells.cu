@@ -897,6 +897,179 @@ __global__ void __launch_bounds__(GTile<D, TF>::THREADS, 4) k_euler_g(Geom g, De
   }
 }
 
+// The same sub-steps in two phases per tile: (1) one thread per cell stages
+// the tile and its halo (rounds over the staged cells) and computes the split
+// fluxes of every staged cell it loaded, (2) every thread updates its own
+// cell from the four (2D; two in 1D) faces it computes itself from the split
+// fluxes.  Two block barriers per sub-step instead of four, every thread busy
+// in both phases; the faces between two cells are computed twice.
+template <int D, typename TF>
+struct G2Tile {
+  static constexpr int TX = D == 1 ? 128 : 32;
+  static constexpr int TY = D == 1 ? 1 : 4;
+  static constexpr int SX = TX + 4;
+  static constexpr int SY = D >= 2 ? TY + 4 : 1;
+  static constexpr int NS = SX * SY;
+  static constexpr int CELLS = TX * TY;
+  static constexpr int THREADS = CELLS;
+  static constexpr size_t SMEM = (size_t)(D + 2) * (NS + 2 * D * NS) * sizeof(TF);
+};
+
+// psi_{j+1/2} of component i along a direction from the split fluxes of the
+// staged cells c - st .. c + 2 st (cell j at c)
+template <typename TF, bool LIMITED>
+__device__ inline TF face_g(const TF* __restrict__ gp, const TF* __restrict__ gm, int c, int st) {
+  const TF p0 = gp[c - st], p1 = gp[c], p2 = gp[c + st];
+  const TF m1 = gm[c], m2 = gm[c + st], m3 = gm[c + 2 * st];
+  const TF sp = slope<TF, LIMITED>(p1 - p0, p2 - p1);
+  const TF sm = slope<TF, LIMITED>(m2 - m1, m3 - m2);
+  return TF(0.5) * (p1 + m2) + TF(0.25) * (sp - sm);
+}
+
+template <typename TF, bool LIMITED, int D>
+__global__ void __launch_bounds__(G2Tile<D, TF>::THREADS) k_euler_g2(Geom g, DevPtrs p) {
+  using T = G2Tile<D, TF>;
+  constexpr int NM = D + 2;
+  extern __shared__ unsigned char s_raw[];
+  __shared__ TF s_amax[3][T::THREADS / 32];
+  TF* sw = reinterpret_cast<TF*>(s_raw);  // [NM][SY][SX]
+  TF* sg = sw + NM * T::NS;               // [D][2][NM][SY][SX]
+  const int Nx = g.nx[0], Ny = g.nx[1];
+  const long long nc = g.nc;
+  const int ntx = (Nx + T::TX - 1) / T::TX, nty = (Ny + T::TY - 1) / T::TY;
+  const int ntiles = ntx * nty;
+  const int tid = threadIdx.x;
+  __shared__ double s_dtE;
+  __shared__ TF s_k, s_al[3];
+  __shared__ int s_last, s_bad;
+  double t = 0.0, a0[3] = {0.0, 0.0, 0.0};
+  int s = 0;
+  for (;; ++s) {
+    const TF* src = (const TF*)((s & 1) ? p.W1 : p.W0);
+    TF* dst = (TF*)((s & 1) ? p.W0 : p.W1);
+    if (tid == 0) {
+      double ad[3], asum = 0.0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) ad[d] = __longlong_as_double((long long)__ldcg(p.aslot + (s % 3) * 3 + d));
+#pragma unroll
+      for (int d = 0; d < D; ++d) asum = __dadd_rn(asum, ad[d]);
+      if (s == 0) a0[0] = ad[0], a0[1] = ad[1], a0[2] = ad[2];
+      if (blockIdx.x == 0)
+        for (int d = 0; d < 3; ++d) p.aslot[((s + 2) % 3) * 3 + d] = 0ull;
+      double dtE = 0.0;
+      int last = 0, bad = 0;
+      if (g.forced_sub > 0) {
+        dtE = g.dt / g.forced_sub;
+        last = s + 1 == g.forced_sub;
+      } else if (!(asum > 0.0)) {
+        bad = 1;
+      } else {
+        const double cfl = sizeof(TF) == 8 ? __ddiv_rn(__dmul_rn(0.5, g.dx), asum)
+                                           : (double)__fdiv_rn(0.5f * (float)g.dx, (float)asum);
+        const double rem = __dsub_rn(g.dt, t);
+        last = cfl >= rem;
+        dtE = last ? rem : cfl;
+      }
+      s_dtE = dtE;
+      s_k = sizeof(TF) == 8 ? (TF)(dtE / g.dx) : (TF)((float)dtE / (float)g.dx);
+      for (int d = 0; d < 3; ++d) s_al[d] = (TF)ad[d];
+      s_last = last;
+      s_bad = bad;
+      if (bad && blockIdx.x == 0) set_status(p.status, DVM_ERR_NONPHYSICAL);
+    }
+    __syncthreads();
+    if (s_bad) return;
+    const bool last = s_last != 0;
+    const TF k = s_k;
+    TF al[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) al[d] = s_al[d];
+    TF amax[3] = {TF(0), TF(0), TF(0)};
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const int x0 = (tile % ntx) * T::TX;
+      const int y0 = (tile / ntx) * T::TY;
+      // phase 1: stage the tile and its two-cell halo, and the split fluxes
+      // of every staged cell and direction
+      for (int i = tid; i < T::NS; i += T::THREADS) {
+        const int lx = i % T::SX, ly = i / T::SX;
+        const int gx = bc_index(x0 - 2 + lx, Nx, g.bc[0]);
+        const int gy = D >= 2 ? bc_index(y0 - 2 + ly, Ny, g.bc[1]) : 0;
+        const long long cc = gx + (long long)Nx * gy;
+        TF U[NM], F[NM];
+#pragma unroll
+        for (int c = 0; c < NM; ++c) {
+          U[c] = __ldcg(src + c * nc + cc);
+          sw[c * T::NS + i] = U[c];
+        }
+#pragma unroll
+        for (int dir = 0; dir < D; ++dir) {
+          euler_flux<TF, D>(U, dir, F);
+#pragma unroll
+          for (int c = 0; c < NM; ++c) {
+            sg[((dir * 2 + 0) * NM + c) * T::NS + i] = F[c] + al[dir] * U[c];
+            sg[((dir * 2 + 1) * NM + c) * T::NS + i] = F[c] - al[dir] * U[c];
+          }
+        }
+      }
+      __syncthreads();
+      // phase 2: every thread its cell, from its own faces
+      const int tx = tid % T::TX, ty = tid / T::TX;
+      const int gx = x0 + tx, gy = y0 + ty;
+      if (gx < Nx && gy < (D >= 2 ? Ny : 1)) {
+        const int ctr = tx + 2 + T::SX * (D >= 2 ? ty + 2 : 0);
+        const long long cell = gx + (long long)Nx * gy;
+        TF Wn[NM];
+#pragma unroll
+        for (int c = 0; c < NM; ++c) {
+          TF acc = TF(0);
+#pragma unroll
+          for (int dir = 0; dir < D; ++dir) {
+            const int st = dir == 0 ? 1 : T::SX;
+            const TF* gp = sg + ((dir * 2 + 0) * NM + c) * T::NS;
+            const TF* gm = sg + ((dir * 2 + 1) * NM + c) * T::NS;
+            acc += face_g<TF, LIMITED>(gp, gm, ctr, st) - face_g<TF, LIMITED>(gp, gm, ctr - st, st);
+          }
+          Wn[c] = sw[c * T::NS + ctr] - k * acc;
+          dst[c * nc + cell] = Wn[c];
+        }
+        if (!last) {
+          TF an[3];
+          state_alpha_of<D>(Wn, an);
+#pragma unroll
+          for (int d = 0; d < 3; ++d) amax[d] = amax[d] > an[d] ? amax[d] : an[d];
+        }
+      }
+      __syncthreads();
+    }
+    if (tid == 0) t = __dadd_rn(t, s_dtE);
+    if (last) break;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      TF v = amax[d];
+      for (int o = 16; o > 0; o >>= 1) {
+        const TF w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = v > w ? v : w;
+      }
+      if ((tid & 31) == 0) s_amax[d][tid >> 5] = v;
+    }
+    __syncthreads();
+    if (tid < D) {
+      TF v = TF(0);
+      for (int w = 0; w < T::THREADS / 32; ++w) v = v > s_amax[tid][w] ? v : s_amax[tid][w];
+      atomicMax(p.aslot + ((s + 1) % 3) * 3 + tid, (unsigned long long)__double_as_longlong((double)v));
+    }
+    if (s + 1 >= g.m_cap) {
+      if (blockIdx.x == 0 && tid == 0) set_status(p.status, DVM_ERR_CFL);
+      break;
+    }
+    if (!grid_sync(p.gbar, p.status)) return;
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    *p.msub = s + 1;
+    for (int d = 0; d < 3; ++d) p.alpha[d] = a0[d];
+  }
+}
+
 // Outflow: snapshot of the boundary pieces of every velocity before the
 // in-place kinetic pass overwrites them (1D: cells 0 and N-1).
 template <typename TS>
@@ -1131,11 +1304,41 @@ cudaError_t launch_euler_weno(const Geom& g, const DevPtrs& p, cudaStream_t s, b
 }
 
 template <typename TF, bool LIM, int D>
+cudaError_t launch_euler_g2(const Geom& g, const DevPtrs& p, cudaStream_t s, bool prepare, int* blocks) {
+  using T = G2Tile<D, TF>;
+  if (prepare) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_euler_g2<TF, LIM, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_euler_g2<TF, LIM, D>, T::THREADS, T::SMEM);
+    const long long nb = (long long)sms * (per_sm < 1 ? 1 : per_sm);
+    const long long need = (long long)((g.nx[0] + T::TX - 1) / T::TX) * ((g.nx[1] + T::TY - 1) / T::TY);
+    *blocks = (int)(nb < need ? nb : need);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)g.euler_blocks);
+  cfg.blockDim = dim3(T::THREADS);
+  cfg.dynamicSmemBytes = T::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_euler_g2<TF, LIM, D>, g, p);
+}
+
+template <typename TF, bool LIM, int D>
 cudaError_t launch_euler_t(const Geom& g, const DevPtrs& p, cudaStream_t s, bool prepare,
                            int* blocks) {
   if constexpr (D <= 2) {
-    const char* e = getenv("DVM_EULER_TILED");  // 1: the per-face-flux kernel (comparison)
-    if (!(e && e[0] == '1')) return launch_euler_g<TF, LIM, D>(g, p, s, prepare, blocks);
+    // DVM_EULER_KERNEL: 1 the per-face-flux kernel, 2 the four-phase
+    // split-flux kernel (comparison runs); default the two-phase one
+    const char* e = getenv("DVM_EULER_KERNEL");
+    if (e && e[0] == '2') return launch_euler_g<TF, LIM, D>(g, p, s, prepare, blocks);
+    if (!(e && e[0] == '1')) return launch_euler_g2<TF, LIM, D>(g, p, s, prepare, blocks);
   }
   using T = ETile<D, TF>;
   if (prepare) {
@@ -1229,6 +1432,12 @@ void launch_alpha(const Geom& g, const DevPtrs& p, cudaStream_t s) {
 int euler_blocks(const Geom& g) {
   int blocks = 1;
   euler_dispatch(g, DevPtrs{}, nullptr, true, &blocks);
+  // DVM_EULER_BLOCKS caps the cooperative grid (launch-shape sweeps)
+  const char* e = getenv("DVM_EULER_BLOCKS");
+  if (e) {
+    const int cap = atoi(e);
+    if (cap > 0 && cap < blocks) blocks = cap;
+  }
   return blocks < 1 ? 1 : blocks;
 }
 
