@@ -86,6 +86,12 @@ constexpr int kBE = DVM_BATCH_EULER_THREADS;
 constexpr int kMaxBatchNx = 4096;      // 1D tube length (shared-memory Euler)
 constexpr int kMaxBatchCells2D = 1 << 20;
 constexpr int kMaxChunks = 4;          // velocity chunks of a case
+// unrolling of the 1D tubes' velocity loop (loads of several velocities in
+// flight; DVM_BATCH_UNROLL overrides it in launch-shape sweeps)
+#ifndef DVM_BATCH_UNROLL
+#define DVM_BATCH_UNROLL 2
+#endif
+constexpr int kBatchUnroll = DVM_BATCH_UNROLL;
 
 // mu of Eq. minimMax for one cell of a 1D case (separable sums: one axis).
 template <bool F64>
@@ -716,6 +722,7 @@ __global__ void k_b_kinetic(BPtrs p) {
       const TC lam_c = prm[prm_at(row_lam(), c, nc)];
       double acc[6] = {0, 0, 0, 0, 0, 0};
       TC r[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll kBatchUnroll
       for (int k = kb; k < ke; ++k) {
         int s = x - s_delta[0][k];
         bool clamped = false;
