@@ -40,6 +40,8 @@ UNIT = "updates/s"
 # name -> (case builder, precision, bytes of f per update: one read + one write)
 WORKLOADS = {
     "quadrant_2d": (lambda: W.quadrant_2d(n=256, nv=32, tau=1e-3, steps=500), "f32"),
+    "quadrant_2d_tau1e-5": (lambda: W.quadrant_2d(n=256, nv=32, tau=1e-5, steps=500), "f32"),
+    "quadrant_2d_tau1e-1": (lambda: W.quadrant_2d(n=256, nv=32, tau=1e-1, steps=500), "f32"),
     "density_wave_3d": (lambda: W.density_wave_3d(n=96, nv=24, tau=1e-4, steps=100), "f32"),
     "density_wave_3d_64": (lambda: W.density_wave_3d(n=64, nv=24, tau=1e-4, steps=100), "f32"),
     "quadrant_2d_f64": (lambda: W.quadrant_2d(n=256, nv=32, tau=1e-3, steps=500), "f64"),
@@ -54,6 +56,10 @@ WORKLOADS = {
 DESCR = {
     "quadrant_2d": "2D-2V four-quadrant Riemann problem, 256x256 periodic cells x 32x32 velocities, "
                    "tau=1e-3, HOFKS, FP32 f / FP64 moments",
+    "quadrant_2d_tau1e-5": "2D-2V four-quadrant Riemann problem, 256x256 periodic cells x 32x32 velocities, "
+                           "tau=1e-5, HOFKS, FP32 f / FP64 moments",
+    "quadrant_2d_tau1e-1": "2D-2V four-quadrant Riemann problem, 256x256 periodic cells x 32x32 velocities, "
+                           "tau=1e-1, HOFKS, FP32 f / FP64 moments",
     "density_wave_3d": "3D-3V periodic density wave, 96^3 cells x 24^3 velocities, tau=1e-4, HOFKS, "
                        "FP32 f / FP64 moments",
     "density_wave_3d_64": "3D-3V periodic density wave, 64^3 cells x 24^3 velocities, tau=1e-4, HOFKS, "
@@ -202,8 +208,10 @@ def oracle_sample(case, budget_points: float):
             if pts >= budget_points:
                 break
         return picked, f"the first {len(picked)} of {len(case)} tubes ({pts} points)"
-    if case.name == "quadrant_2d":
+    if case.name in ("quadrant_2d", "implosion_2d"):
         n = int(max(8, min(case.nx[0], round((budget_points / case.nvel) ** 0.5))))
+        if case.name == "implosion_2d":
+            return ([W.implosion_2d(n=n, nv=case.nv[0], tau=case.tau)], f"{n}x{n} cells x {case.nvel} velocities")
         return ([W.quadrant_2d(n=n, nv=case.nv[0], tau=case.tau, steps=1, dv=case.dv)],
                 f"{n}x{n} cells x {case.nvel} velocities")
     if case.name == "density_wave_3d":
