@@ -12,6 +12,7 @@
 #include <math.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "dvm_internal.cuh"
 #include "dvm_math.cuh"
@@ -52,8 +53,39 @@ __device__ void write_params(const Geom& g, TC* prm, long long c, double lam, do
   }
 }
 
+// The same parameters from FP32 primitives and corrections (FP32-storage
+// builds; the values the FP64 version rounds to FP32, up to a few ulp).
+template <int D>
+__device__ void write_params_f32(const Geom& g, float* prm, long long c, float lam, float weight,
+                                 float rho, const float u[3], float theta, const float* nu,
+                                 const float* mu) {
+  constexpr int NM = D + 2;
+  const long long nc = g.nc;
+  prm[prm_at(row_lam(), c, nc)] = lam;
+  prm[prm_at(row_L(), c, nc)] = log2f(weight) + log2f(rho) - 0.5f * D * log2f(6.283185307179586f * theta);
+#pragma unroll
+  for (int i = 0; i < D; ++i) prm[prm_at(row_u(i), c, nc)] = u[i];
+  prm[prm_at(row_h(D), c, nc)] = 0.72134752044448170f / theta;
+  const float w = (float)g.w;
+#pragma unroll
+  for (int i = 0; i < NM; ++i) {
+    const float e = i == NM - 1 ? 0.5f : 1.f;
+    prm[prm_at(row_nu(D, i), c, nc)] = nu ? e * w * nu[i] : 0.f;
+    prm[prm_at(row_mu(D, i), c, nc)] = e * weight * w * mu[i];
+  }
+}
+
+// (C C^T)^{-1} in FP32 in shared memory (one copy per block)
+template <int D>
+__device__ inline void stage_af(const DevPtrs& p, float* sA) {
+  if (threadIdx.x < (D + 2) * (D + 2)) sA[threadIdx.x] = (float)p.A[threadIdx.x];
+  __syncthreads();
+}
+
 template <typename TC, int D>
 __global__ void k_cell_params(Geom g, DevPtrs p, int mode, int initial) {
+  __shared__ float sA[kMaxM * kMaxM];
+  if (sizeof(TC) == 4 && mode != 0) stage_af<D>(p, sA);
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= g.nc) return;
   double Uc[kMaxM], mu[kMaxM], rho, u[3], theta;
@@ -69,14 +101,24 @@ __global__ void k_cell_params(Geom g, DevPtrs p, int mode, int initial) {
     write_params<double, D>(g, p.eqp, c, lam, 1.0, rho, u, theta, nullptr, mu);
     return;
   }
-  const int rc = cell_mu<D, sizeof(TC) == 8>(g, p.A, Uc, mu, rho, u, theta);
-  if (rc) {
-    set_status(p.status, rc);
-    return;
-  }
   // FKS: f^0 carries no deferred equilibrium yet
   const double weight = (g.scheme == DVM_FKS && initial) ? 0.0 : 1.0 - lam;
-  write_params<TC, D>(g, (TC*)p.prm, c, lam, weight, rho, u, theta, nullptr, mu);
+  if constexpr (sizeof(TC) == 4) {
+    float muf[kMaxM], rf, uf[3], tf;
+    const int rc = cell_mu_f32<D>(g, sA, Uc, muf, rf, uf, tf);
+    if (rc) {
+      set_status(p.status, rc);
+      return;
+    }
+    write_params_f32<D>(g, (float*)p.prm, c, (float)lam, (float)weight, rf, uf, tf, nullptr, muf);
+  } else {
+    const int rc = cell_mu<D, true>(g, p.A, Uc, mu, rho, u, theta);
+    if (rc) {
+      set_status(p.status, rc);
+      return;
+    }
+    write_params<TC, D>(g, (TC*)p.prm, c, lam, weight, rho, u, theta, nullptr, mu);
+  }
 }
 
 template <typename TS> struct ComputeOf { typedef float type; };
@@ -185,22 +227,24 @@ __global__ void k_prim_to_cons(Geom g, const double* rho, const double* u, const
 
 // Block max of alpha, atomically merged; the last block to finish publishes
 // the three maxima as the alpha of the first Euler sub-step (slot 0), clears
-// the other two slots and resets the reduction.
-template <int D>
-__device__ void alpha_reduce_publish(const Geom& g, const DevPtrs& p, const double a[3]) {
-  __shared__ double red[3][kBlock / 32];
+// the other two slots and resets the reduction.  FP32 values are reduced in
+// FP32: their maximum is one of them, so the published double is the same as
+// from a reduction in FP64.
+template <int D, typename TA>
+__device__ void alpha_reduce_publish(const Geom& g, const DevPtrs& p, const TA a[3]) {
+  __shared__ TA red[3][kBlock / 32];
   __shared__ bool last;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    double v = a[i];
+    TA v = a[i];
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     if ((threadIdx.x & 31) == 0) red[i][threadIdx.x >> 5] = v;
   }
   __syncthreads();
   if (threadIdx.x < 3) {
-    double v = 0.0;
+    TA v = 0;
     for (int w = 0; w < kBlock / 32; ++w) v = fmax(v, red[threadIdx.x][w]);
-    atomicMax(&p.alpha_bits[threadIdx.x], (unsigned long long)__double_as_longlong(v));
+    atomicMax(&p.alpha_bits[threadIdx.x], (unsigned long long)__double_as_longlong((double)v));
   }
   __threadfence();
   __syncthreads();
@@ -232,7 +276,7 @@ __global__ void __launch_bounds__(kBlock) k_alpha(Geom g, DevPtrs p) {
     }
     state_alpha_of<D>(W, a);
   }
-  alpha_reduce_publish<D>(g, p, a);
+  alpha_reduce_publish<D, double>(g, p, a);
 }
 
 // ---------------------------------------------------------------- MUSCL
@@ -1093,12 +1137,19 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Geom g, DevPtrs p) {
   constexpr int NM = D + 2;
   constexpr bool HO = SCHEME != DVM_FKS;
   constexpr int NACC = HO ? 2 * NM : NM;
+  // FP32-storage builds: moments combined in FP64 (the partial sums, U^{n+1}
+  // = U_* + U_E, U_E - U_M, U - C M[U]), the rest of the per-cell arithmetic
+  // in FP32 (GB300's FP64 rate bounds this kernel otherwise)
+  constexpr bool F32 = sizeof(TC) == 4;
+  using TA = typename std::conditional<F32, float, double>::type;
+  __shared__ float sA[kMaxM * kMaxM];
+  if (F32) stage_af<D>(p, sA);
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c == 0) *p.step += 1;
   const long long nc = g.nc;
-  double a[3] = {0.0, 0.0, 0.0};
+  TA a[3] = {0, 0, 0};
   if (c < nc) {
-    double Un[kMaxM], nu[kMaxM];
+    double Un[kMaxM], r[kMaxM] = {0.0, 0.0, 0.0, 0.0, 0.0};
     double sums[2 * kMaxM];
 #pragma unroll
     for (int j = 0; j < NACC; ++j) {
@@ -1108,7 +1159,6 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Geom g, DevPtrs p) {
     }
     if (HO) {
       const TW* UE = (const TW*)((*p.msub & 1) ? p.W1 : p.W0);
-      double r[kMaxM];
 #pragma unroll
       for (int i = 0; i < NM; ++i) {
         const double ue = g.skip_euler ? 0.0 : (double)UE[i * nc + c];
@@ -1118,17 +1168,6 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Geom g, DevPtrs p) {
         p.Us[i * nc + c] = sums[i];
         p.UM[i * nc + c] = sums[NM + i];
       }
-#pragma unroll
-      for (int i = 0; i < NM; ++i) {
-        double s = 0.0;
-#pragma unroll
-        for (int j = 0; j < NM; ++j) s += p.A[i * NM + j] * r[j];
-        nu[i] = s;
-      }
-      // learned path: a flagged cell's f^{n+1} is E[U^{n+1}], no correction
-      if (g.learn && p.lflag[c])
-#pragma unroll
-        for (int i = 0; i < NM; ++i) nu[i] = 0.0;
     } else {
 #pragma unroll
       for (int i = 0; i < NM; ++i) {
@@ -1138,26 +1177,49 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Geom g, DevPtrs p) {
     }
 #pragma unroll
     for (int i = 0; i < NM; ++i) p.U[i * nc + c] = Un[i];
-    double mu[kMaxM], rho, u[3], theta;
-    const int rc = cell_mu<D, sizeof(TC) == 8>(g, p.A, Un, mu, rho, u, theta);
+    // the HOFKS correction nu = A (U_E - U_M); a flagged cell of the learned
+    // path has f^{n+1} = E[U^{n+1}], no correction
+    const bool no_nu = !HO || (g.learn && p.lflag[c]);
+    const double lam = p.lam[c];
+    int rc;
+    if constexpr (F32) {
+      float nu[kMaxM], mu[kMaxM], rho, u[3], theta;
+#pragma unroll
+      for (int i = 0; i < NM; ++i) {
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < NM; ++j) s = fmaf(sA[i * NM + j], (float)r[j], s);
+        nu[i] = no_nu ? 0.f : s;
+      }
+      rc = cell_mu_f32<D>(g, sA, Un, mu, rho, u, theta);
+      if (!rc) write_params_f32<D>(g, (float*)p.prm, c, (float)lam, (float)(1.0 - lam), rho, u, theta,
+                                   HO ? nu : nullptr, mu);
+    } else {
+      double nu[kMaxM], mu[kMaxM], rho, u[3], theta;
+#pragma unroll
+      for (int i = 0; i < NM; ++i) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < NM; ++j) s += p.A[i * NM + j] * r[j];
+        nu[i] = no_nu ? 0.0 : s;
+      }
+      rc = cell_mu<D, true>(g, p.A, Un, mu, rho, u, theta);
+      if (!rc) write_params<TC, D>(g, (TC*)p.prm, c, lam, 1.0 - lam, rho, u, theta, HO ? nu : nullptr, mu);
+    }
     if (rc) {
       set_status(p.status, rc);
-    } else {
-      const double lam = p.lam[c];
-      write_params<TC, D>(g, (TC*)p.prm, c, lam, 1.0 - lam, rho, u, theta, HO ? nu : nullptr, mu);
-      if (HO) {
-        TW W[kMaxM];
-        const double w = 1.0 - lam;
+    } else if (HO) {
+      TW W[kMaxM];
+      const double w = 1.0 - lam;
 #pragma unroll
-        for (int i = 0; i < NM; ++i) {
-          W[i] = (TW)(w * Un[i]);
-          ((TW*)p.W0)[i * nc + c] = W[i];
-        }
-        state_alpha_of<D>(W, a);
+      for (int i = 0; i < NM; ++i) {
+        W[i] = (TW)(w * Un[i]);
+        ((TW*)p.W0)[i * nc + c] = W[i];
       }
+      state_alpha_of<D>(W, a);
     }
   }
-  if (HO) alpha_reduce_publish<D>(g, p, a);
+  if (HO) alpha_reduce_publish<D, TA>(g, p, a);
 }
 
 // f at the cell centres: stored piece value plus the deferred term.

@@ -265,5 +265,74 @@ __device__ int cell_mu(const Geom& g, const double* A, const double* Uc, double 
   return 0;
 }
 
+// FP32-storage builds: the same mu with the primitives, the Gaussian sums
+// and C M[U] in FP32 (the accuracy of the FP32 Maxwellian samples the kinetic
+// pass draws from these parameters) and only U - C M[U], the difference of
+// two nearly equal moment vectors, in FP64; Af is (C C^T)^{-1} in FP32.
+// GB300's FP64 rate is about 1/64 of its FP32 rate and the end-of-step kernel
+// is bound by it otherwise.  A theta that rounds to <= 0 in FP32 is
+// recomputed in FP64 before the cell is declared non-physical.
+template <int D>
+__device__ int cell_mu_f32(const Geom& g, const float* Af, const double* Uc, float mu[kMaxM],
+                           float& rho, float u[3], float& theta) {
+  constexpr int NM = D + 2;
+#pragma unroll
+  for (int i = 0; i < NM; ++i)
+    if (!isfinite(Uc[i])) return DVM_ERR_NONFINITE;
+  if (!(Uc[0] > 0.0)) return DVM_ERR_NONPHYSICAL;
+  rho = (float)Uc[0];
+  const float ir = 1.f / rho;
+  float u2 = 0.f;
+  u[0] = u[1] = u[2] = 0.f;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    u[i] = (float)Uc[1 + i] * ir;
+    u2 = fmaf(u[i], u[i], u2);
+  }
+  theta = (2.f * (float)Uc[D + 1] * ir - u2) * (1.f / D);
+  if (!(theta > 0.f) || !(rho > 0.f)) {
+    double rd, ud[3], td;
+    primitives<D>(Uc, rd, ud, td);
+    if (!(rd > 0.0) || !(td > 0.0)) return DVM_ERR_NONPHYSICAL;
+    rho = (float)rd;
+    theta = (float)td;
+    for (int i = 0; i < 3; ++i) u[i] = (float)ud[i];
+    if (!(theta > 0.f) || !(rho > 0.f)) return DVM_ERR_NONPHYSICAL;
+  }
+  // C M[U] in FP64 from the FP32 Gaussian sums: any rounding of it would
+  // enter E[U]'s moments (through mu) and accumulate step by step
+  double G0[3], G1[3], G2[3];
+#pragma unroll
+  for (int i = 0; i < D; ++i) gauss_axis_sums_f32(g.nv[i], g.kmin[i], (float)g.dv, u[i], theta, G0[i], G1[i], G2[i]);
+  const double pref = g.w * (double)rho * (double)powf(6.283185307179586f * theta, -0.5f * D);
+  double CM[kMaxM];
+  double all = 1.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) all *= G0[i];
+  CM[0] = pref * all;
+  double e = 0.0;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    double other = 1.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+      if (i != j) other *= G0[i];
+    CM[1 + j] = pref * G1[j] * other;
+    e += G2[j] * other;
+  }
+  CM[D + 1] = 0.5 * pref * e;
+  float r[kMaxM];
+#pragma unroll
+  for (int i = 0; i < NM; ++i) r[i] = (float)(Uc[i] - CM[i]);
+#pragma unroll
+  for (int i = 0; i < NM; ++i) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < NM; ++j) s = fmaf(Af[i * NM + j], r[j], s);
+    mu[i] = s;
+  }
+  return 0;
+}
+
 }  // namespace
 }  // namespace dvm
