@@ -947,10 +947,19 @@ __global__ void __launch_bounds__(GTile<D, TF>::THREADS, 4) k_euler_g(Geom g, De
 // cell from the four (2D; two in 1D) faces it computes itself from the split
 // fluxes.  Two block barriers per sub-step instead of four, every thread busy
 // in both phases; the faces between two cells are computed twice.
-template <int D, typename TF>
+//
+// Tile shapes: 128 cells (1D), 32 x 4 (2D) and, for FP32 2D grids of at most
+// one tile per two SMs, 32 x 32 ("tall"): a 1024-thread CTA takes 48K of an
+// SM's 64K registers, so no CTA of the concurrent kinetic pass (32K) fits
+// beside it and the Euler sub-steps run on SMs of their own while the kinetic
+// pass keeps full occupancy on the others.  With 32 x 4 tiles (3-4 CTAs per
+// SM) the block scheduler spreads them over every SM; each SM then also holds
+// one kinetic CTA, and the Euler sub-steps, slowed by the kinetic pass's
+// memory traffic on the same SMs, become the critical path of the step.
+template <int D, typename TF, bool TALL = false>
 struct G2Tile {
   static constexpr int TX = D == 1 ? 128 : 32;
-  static constexpr int TY = D == 1 ? 1 : 4;
+  static constexpr int TY = D == 1 ? 1 : (TALL ? 32 : 4);
   static constexpr int SX = TX + 4;
   static constexpr int SY = D >= 2 ? TY + 4 : 1;
   static constexpr int NS = SX * SY;
@@ -970,9 +979,9 @@ __device__ inline TF face_g(const TF* __restrict__ gp, const TF* __restrict__ gm
   return TF(0.5) * (p1 + m2) + TF(0.25) * (sp - sm);
 }
 
-template <typename TF, bool LIMITED, int D>
-__global__ void __launch_bounds__(G2Tile<D, TF>::THREADS) k_euler_g2(Geom g, DevPtrs p) {
-  using T = G2Tile<D, TF>;
+template <typename TF, bool LIMITED, int D, bool TALL>
+__global__ void __launch_bounds__(G2Tile<D, TF, TALL>::THREADS) k_euler_g2(Geom g, DevPtrs p) {
+  using T = G2Tile<D, TF, TALL>;
   constexpr int NM = D + 2;
   extern __shared__ unsigned char s_raw[];
   __shared__ TF s_amax[3][T::THREADS / 32];
@@ -1365,15 +1374,15 @@ cudaError_t launch_euler_weno(const Geom& g, const DevPtrs& p, cudaStream_t s, b
   return cudaLaunchKernelEx(&cfg, k_euler_weno<TF, D>, g, p);
 }
 
-template <typename TF, bool LIM, int D>
-cudaError_t launch_euler_g2(const Geom& g, const DevPtrs& p, cudaStream_t s, bool prepare, int* blocks) {
-  using T = G2Tile<D, TF>;
+template <typename TF, bool LIM, int D, bool TALL>
+cudaError_t launch_euler_g2_t(const Geom& g, const DevPtrs& p, cudaStream_t s, bool prepare, int* blocks) {
+  using T = G2Tile<D, TF, TALL>;
   if (prepare) {
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_euler_g2<TF, LIM, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_euler_g2<TF, LIM, D>, T::THREADS, T::SMEM);
+    cudaFuncSetAttribute(k_euler_g2<TF, LIM, D, TALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_euler_g2<TF, LIM, D, TALL>, T::THREADS, T::SMEM);
     const long long nb = (long long)sms * (per_sm < 1 ? 1 : per_sm);
     const long long need = (long long)((g.nx[0] + T::TX - 1) / T::TX) * ((g.nx[1] + T::TY - 1) / T::TY);
     *blocks = (int)(nb < need ? nb : need);
@@ -1389,7 +1398,27 @@ cudaError_t launch_euler_g2(const Geom& g, const DevPtrs& p, cudaStream_t s, boo
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_euler_g2<TF, LIM, D>, g, p);
+  return cudaLaunchKernelEx(&cfg, k_euler_g2<TF, LIM, D, TALL>, g, p);
+}
+
+// 32 x 32 tiles: FP32 2D grids of at most one such tile per two SMs
+// (DVM_EULER_TALL=0 keeps the 32 x 4 tiles, for comparison runs)
+bool euler_tall(const Geom& g) {
+  if (g.d != 2 || g.precision == DVM_F64) return false;
+  const char* e = getenv("DVM_EULER_TALL");
+  if (e && e[0] == '0') return false;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return false;
+  const long long tiles = (long long)((g.nx[0] + 31) / 32) * ((g.nx[1] + 31) / 32);
+  return 2 * tiles <= sms;
+}
+
+template <typename TF, bool LIM, int D>
+cudaError_t launch_euler_g2(const Geom& g, const DevPtrs& p, cudaStream_t s, bool prepare, int* blocks) {
+  if constexpr (D == 2 && sizeof(TF) == 4)
+    if (euler_tall(g)) return launch_euler_g2_t<TF, LIM, D, true>(g, p, s, prepare, blocks);
+  return launch_euler_g2_t<TF, LIM, D, false>(g, p, s, prepare, blocks);
 }
 
 template <typename TF, bool LIM, int D>

@@ -344,15 +344,18 @@ def test_bf16_free_transport_with_staged_loads_is_bit_exact():
 ], ids=["quadrant_2d", "sod_1d"])
 @pytest.mark.parametrize("precision", [dvm.F64, dvm.F32])
 def test_euler_kernels_agree_bit_for_bit(make, precision, monkeypatch):
-    """The two-phase Euler kernel (each cell computes its own faces) and the
-    four-phase one (faces computed once, shared) evaluate the same expressions:
-    bit-identical U_E and moments."""
+    """The two-phase Euler kernel (each cell computes its own faces) with 32 x 32
+    tiles (the default for FP32 2D grids this small) and with 32 x 4 tiles, and
+    the four-phase one (faces computed once, shared) evaluate the same
+    expressions: bit-identical U_E and moments (45 x 45 cells: ragged tiles)."""
     case = make()
     out = []
-    for mode in ("0", "2"):
-        monkeypatch.setenv("DVM_EULER_KERNEL", mode)
+    for kernel, tall in (("0", "1"), ("0", "0"), ("2", "1")):
+        monkeypatch.setenv("DVM_EULER_KERNEL", kernel)
+        monkeypatch.setenv("DVM_EULER_TALL", tall)
         s = gpu_run(case, 3, precision)
         out.append((s.moments(), s.parts()[0], s.info()["m"]))
         s.close()
-    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
-    assert out[0][2] == out[1][2]
+    for o in out[1:]:
+        assert np.array_equal(out[0][0], o[0]) and np.array_equal(out[0][1], o[1])
+        assert out[0][2] == o[2]
