@@ -51,6 +51,8 @@ struct dvm_handle {
   long long checks_run = 0;
   cudaGraph_t graph_chk = nullptr; // step with the periodic check
   cudaGraphExec_t exec_chk = nullptr;
+  cudaGraph_t graph_multi = nullptr;  // kGraphSteps steps in one graph
+  cudaGraphExec_t exec_multi = nullptr;
   float* scratch = nullptr;        // read-back staging (features, labels)
   size_t scratch_bytes = 0;
   dvm::ReadBack rb;                // dvm_moments_async / dvm_moments_wait
@@ -325,21 +327,33 @@ void drop_graph(dvm_handle* h) {
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->exec_chk) cudaGraphExecDestroy(h->exec_chk);
   if (h->graph_chk) cudaGraphDestroy(h->graph_chk);
+  if (h->exec_multi) cudaGraphExecDestroy(h->exec_multi);
+  if (h->graph_multi) cudaGraphDestroy(h->graph_multi);
   h->exec = nullptr;
   h->graph = nullptr;
   h->exec_chk = nullptr;
   h->graph_chk = nullptr;
+  h->exec_multi = nullptr;
+  h->graph_multi = nullptr;
 }
 
-// Captures one step (check = 0) or one step with the periodic check (1).
+// Steps per launch of the multi-step graph: consecutive steps of one call
+// run as one graph, without the gap between two graph launches.
+constexpr int kGraphSteps = 4;
+
+// Captures one step (check = 0), one step with the periodic check (1), or
+// kGraphSteps plain steps (2).
 int ensure_graph(dvm_handle* h, int check = 0) {
-  cudaGraphExec_t* ex = check ? &h->exec_chk : &h->exec;
-  cudaGraph_t* gr = check ? &h->graph_chk : &h->graph;
+  cudaGraphExec_t* ex = check == 2 ? &h->exec_multi : (check ? &h->exec_chk : &h->exec);
+  cudaGraph_t* gr = check == 2 ? &h->graph_multi : (check ? &h->graph_chk : &h->graph);
   if (!h->use_graph || *ex) return 0;
   int rc = cuda_check(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal),
                       "begin capture");
   if (rc) return rc;
-  rc = enqueue_step(h, h->cap, nullptr, nullptr, check);
+  if (check == 2)
+    for (int i = 0; i < kGraphSteps && !rc; ++i) rc = enqueue_step(h, h->cap, nullptr, nullptr, 0);
+  else
+    rc = enqueue_step(h, h->cap, nullptr, nullptr, check);
   cudaGraph_t graph = nullptr;
   const cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
   if (rc) return rc;
@@ -592,6 +606,12 @@ int dvm_step_async(dvm_handle* h, int nsteps) {
   if (h->g.learn && h->lcfg.mode == DVM_LEARN_MLP && !h->params_set)
     return fail(h, DVM_ERR_STATE, "network parameters not set");
   for (int i = 0; i < nsteps; ++i) {
+    if (!h->g.learn && h->use_graph && nsteps - i >= kGraphSteps) {
+      if ((rc = ensure_graph(h, 2))) return rc;
+      if ((rc = cuda_check(h, cudaGraphLaunch(h->exec_multi, h->stream), "graph launch"))) return rc;
+      i += kGraphSteps - 1;
+      continue;
+    }
     int check = 0;
     if (h->g.learn) {
       ++h->learn_steps;
