@@ -44,6 +44,7 @@ struct BCase {
   long long f_off, c_off, e_off;  // pieces, cells, Euler state (2D, TW elements)
   double dx, dv, dt, w;
   double A[16];      // (C C^T)^{-1}, (d + 2)^2
+  float Af[16];      // the same in FP32 (end-of-step arithmetic of FP32 builds)
 };
 
 struct BItem {
@@ -94,7 +95,6 @@ constexpr int kMaxChunks = 4;          // velocity chunks of a case
 constexpr int kBatchUnroll = DVM_BATCH_UNROLL;
 
 // mu of Eq. minimMax for one cell of a 1D case (separable sums: one axis).
-template <bool F64>
 __device__ int b_cell_mu(const BCase& bc, const double* Uc, double mu[3], double& rho, double& u,
                          double& theta) {
   for (int i = 0; i < 3; ++i)
@@ -104,10 +104,8 @@ __device__ int b_cell_mu(const BCase& bc, const double* Uc, double mu[3], double
   u = uu[0];
   if (!(rho > 0.0) || !(theta > 0.0)) return DVM_ERR_NONPHYSICAL;
   double G0, G1, G2;
-  if (F64) gauss_axis_sums(bc.nv, bc.kmin, bc.dv, u, theta, G0, G1, G2);
-  else gauss_axis_sums_f32(bc.nv, bc.kmin, (float)bc.dv, (float)u, (float)theta, G0, G1, G2);
-  const double pref = F64 ? bc.w * rho / sqrt(2.0 * M_PI * theta)
-                          : bc.w * rho * (double)rsqrtf(6.283185307179586f * (float)theta);
+  gauss_axis_sums(bc.nv, bc.kmin, bc.dv, u, theta, G0, G1, G2);
+  const double pref = bc.w * rho / sqrt(2.0 * M_PI * theta);
   const double CM[3] = {pref * G0, pref * G1, 0.5 * pref * G2};
   double r[3];
   for (int i = 0; i < 3; ++i) r[i] = Uc[i] - CM[i];
@@ -158,15 +156,68 @@ __device__ inline Geom b_geom2(const BCase& bc) {
 }
 
 // mu and the primitive variables of one cell of case bc (1D or 2D).
-template <bool F64>
 __device__ int b_any_mu(const BCase& bc, const double* A, const double* Uc, double* mu, double& rho,
                         double u[3], double& theta) {
   if (bc.d == 1) {
     u[1] = u[2] = 0.0;
-    return b_cell_mu<F64>(bc, Uc, mu, rho, u[0], theta);
+    return b_cell_mu(bc, Uc, mu, rho, u[0], theta);
   }
   const Geom g = b_geom2(bc);
-  return cell_mu<2, F64>(g, A, Uc, mu, rho, u, theta);
+  return cell_mu<2>(g, A, Uc, mu, rho, u, theta);
+}
+
+// FP32-storage builds: primitives, the Gaussian sums and mu = A (U - C M[U])
+// in FP32, C M[U] and U - C M[U] in FP64 (as cell_mu_f32 for one problem).
+__device__ int b_cell_mu_f32(const BCase& bc, const double* Uc, float mu[3], float& rho, float& u,
+                             float& theta) {
+  for (int i = 0; i < 3; ++i)
+    if (!isfinite(Uc[i])) return DVM_ERR_NONFINITE;
+  if (!(Uc[0] > 0.0)) return DVM_ERR_NONPHYSICAL;
+  rho = (float)Uc[0];
+  const float ir = 1.f / rho;
+  u = (float)Uc[1] * ir;
+  theta = 2.f * (float)Uc[2] * ir - u * u;
+  if (!(theta > 0.f) || !(rho > 0.f)) {
+    double rd, ud[3], td;
+    primitives<1>(Uc, rd, ud, td);
+    if (!(rd > 0.0) || !(td > 0.0)) return DVM_ERR_NONPHYSICAL;
+    rho = (float)rd, u = (float)ud[0], theta = (float)td;
+    if (!(theta > 0.f) || !(rho > 0.f)) return DVM_ERR_NONPHYSICAL;
+  }
+  double G0, G1, G2;
+  gauss_axis_sums_f32(bc.nv, bc.kmin, (float)bc.dv, u, theta, G0, G1, G2);
+  const double pref = bc.w * (double)rho * (double)rsqrtf(6.283185307179586f * theta);
+  const double CM[3] = {pref * G0, pref * G1, 0.5 * pref * G2};
+  float r[3];
+  for (int i = 0; i < 3; ++i) r[i] = (float)(Uc[i] - CM[i]);
+  for (int i = 0; i < 3; ++i) mu[i] = fmaf(bc.Af[3 * i], r[0], fmaf(bc.Af[3 * i + 1], r[1], bc.Af[3 * i + 2] * r[2]));
+  return 0;
+}
+
+__device__ int b_any_mu_f32(const BCase& bc, const double* Uc, float* mu, float& rho, float u[3],
+                            float& theta) {
+  if (bc.d == 1) {
+    u[1] = u[2] = 0.f;
+    return b_cell_mu_f32(bc, Uc, mu, rho, u[0], theta);
+  }
+  const Geom g = b_geom2(bc);
+  return cell_mu_f32<2>(g, bc.Af, Uc, mu, rho, u, theta);
+}
+
+template <int D>
+__device__ void b_write_params_f32(const BCase& bc, float* prm, long long c, long long nc, float lam,
+                                   float weight, float rho, const float* u, float theta, const float* nu,
+                                   const float* mu) {
+  prm[prm_at(row_lam(), c, nc)] = lam;
+  prm[prm_at(row_L(), c, nc)] = log2f(weight) + log2f(rho) - 0.5f * D * log2f(6.283185307179586f * theta);
+  for (int i = 0; i < D; ++i) prm[prm_at(row_u(i), c, nc)] = u[i];
+  prm[prm_at(row_h(D), c, nc)] = 0.72134752044448170f / theta;
+  const float w = (float)bc.w;
+  for (int i = 0; i < D + 2; ++i) {
+    const float e = i == D + 1 ? 0.5f : 1.f;  // energy row: coefficient of |v|^2
+    prm[prm_at(row_nu(D, i), c, nc)] = nu ? e * w * nu[i] : 0.f;
+    prm[prm_at(row_mu(D, i), c, nc)] = e * weight * w * mu[i];
+  }
 }
 
 template <typename TC>
@@ -179,17 +230,25 @@ __global__ void k_b_cell_params(BPtrs p, int mode, int initial) {
   for (int i = 0; i < nm; ++i) Uc[i] = p.U[i * p.ncells + c];
   const double lam = p.lam[c];
   if (mode == 0) {
-    const int rc = b_any_mu<true>(bc, bc.A, Uc, mu, rho, u, theta);
+    const int rc = b_any_mu(bc, bc.A, Uc, mu, rho, u, theta);
     if (rc) { set_status(p.status, rc); return; }
     if (bc.d == 1) b_write_params<1, double>(bc, p.eqp, c, p.ncells, lam, 1.0, rho, u, theta, nullptr, mu);
     else b_write_params<2, double>(bc, p.eqp, c, p.ncells, lam, 1.0, rho, u, theta, nullptr, mu);
     return;
   }
-  const int rc = b_any_mu<sizeof(TC) == 8>(bc, bc.A, Uc, mu, rho, u, theta);
-  if (rc) { set_status(p.status, rc); return; }
   const double weight = (p.scheme == DVM_FKS && initial) ? 0.0 : 1.0 - lam;
-  if (bc.d == 1) b_write_params<1, TC>(bc, (TC*)p.prm, c, p.ncells, lam, weight, rho, u, theta, nullptr, mu);
-  else b_write_params<2, TC>(bc, (TC*)p.prm, c, p.ncells, lam, weight, rho, u, theta, nullptr, mu);
+  if constexpr (sizeof(TC) == 4) {
+    float muf[4], rf, uf[3], tf;
+    const int rc = b_any_mu_f32(bc, Uc, muf, rf, uf, tf);
+    if (rc) { set_status(p.status, rc); return; }
+    if (bc.d == 1) b_write_params_f32<1>(bc, (float*)p.prm, c, p.ncells, (float)lam, (float)weight, rf, uf, tf, nullptr, muf);
+    else b_write_params_f32<2>(bc, (float*)p.prm, c, p.ncells, (float)lam, (float)weight, rf, uf, tf, nullptr, muf);
+  } else {
+    const int rc = b_any_mu(bc, bc.A, Uc, mu, rho, u, theta);
+    if (rc) { set_status(p.status, rc); return; }
+    if (bc.d == 1) b_write_params<1, TC>(bc, (TC*)p.prm, c, p.ncells, lam, weight, rho, u, theta, nullptr, mu);
+    else b_write_params<2, TC>(bc, (TC*)p.prm, c, p.ncells, lam, weight, rho, u, theta, nullptr, mu);
+  }
 }
 
 // f^0 = E[U^0] for the points of one case (grid: chunks x cases).
@@ -816,9 +875,8 @@ __global__ void k_b_finalize(BPtrs p) {
       if (HOFKS) sb[i] += a[(nmb + i) * nc];
     }
   }
-  double Un[4], nu[4];
+  double Un[4], r[4] = {0.0, 0.0, 0.0, 0.0};
   if (HOFKS) {
-    double r[4];
     for (int i = 0; i < nm; ++i) {
       const double us = bc.w * sa[i], um = bc.w * sb[i];
       const double ue = p.UE[i * nc + c];
@@ -827,11 +885,6 @@ __global__ void k_b_finalize(BPtrs p) {
       p.Us[i * nc + c] = us;
       p.UM[i * nc + c] = um;
     }
-    for (int i = 0; i < nm; ++i) {
-      double t = 0.0;
-      for (int j = 0; j < nm; ++j) t += bc.A[i * nm + j] * r[j];
-      nu[i] = t;
-    }
   } else {
     for (int i = 0; i < nm; ++i) {
       Un[i] = bc.w * sa[i];
@@ -839,14 +892,36 @@ __global__ void k_b_finalize(BPtrs p) {
     }
   }
   for (int i = 0; i < nm; ++i) p.U[i * nc + c] = Un[i];
-  double mu[4], rho, u[3], theta;
-  const int rc = b_any_mu<sizeof(TC) == 8>(bc, bc.A, Un, mu, rho, u, theta);
-  if (rc) { set_status(p.status, rc); return; }
   const double lam = p.lam[c];
-  if (bc.d == 1)
-    b_write_params<1, TC>(bc, (TC*)p.prm, c, nc, lam, 1.0 - lam, rho, u, theta, HOFKS ? nu : nullptr, mu);
-  else
-    b_write_params<2, TC>(bc, (TC*)p.prm, c, nc, lam, 1.0 - lam, rho, u, theta, HOFKS ? nu : nullptr, mu);
+  // nu = A (U_E - U_M); FP32-storage builds: nu, mu and the primitives in FP32
+  // (GB300's FP64 rate bounds this kernel otherwise), the moments in FP64
+  if constexpr (sizeof(TC) == 4) {
+    float nu[4], mu[4], rho, u[3], theta;
+    for (int i = 0; i < nm; ++i) {
+      float t = 0.f;
+      for (int j = 0; j < nm; ++j) t = fmaf(bc.Af[i * nm + j], (float)r[j], t);
+      nu[i] = t;
+    }
+    const int rc = b_any_mu_f32(bc, Un, mu, rho, u, theta);
+    if (rc) { set_status(p.status, rc); return; }
+    if (bc.d == 1)
+      b_write_params_f32<1>(bc, (float*)p.prm, c, nc, (float)lam, (float)(1.0 - lam), rho, u, theta, HOFKS ? nu : nullptr, mu);
+    else
+      b_write_params_f32<2>(bc, (float*)p.prm, c, nc, (float)lam, (float)(1.0 - lam), rho, u, theta, HOFKS ? nu : nullptr, mu);
+  } else {
+    double nu[4], mu[4], rho, u[3], theta;
+    for (int i = 0; i < nm; ++i) {
+      double t = 0.0;
+      for (int j = 0; j < nm; ++j) t += bc.A[i * nm + j] * r[j];
+      nu[i] = t;
+    }
+    const int rc = b_any_mu(bc, bc.A, Un, mu, rho, u, theta);
+    if (rc) { set_status(p.status, rc); return; }
+    if (bc.d == 1)
+      b_write_params<1, TC>(bc, (TC*)p.prm, c, nc, lam, 1.0 - lam, rho, u, theta, HOFKS ? nu : nullptr, mu);
+    else
+      b_write_params<2, TC>(bc, (TC*)p.prm, c, nc, lam, 1.0 - lam, rho, u, theta, HOFKS ? nu : nullptr, mu);
+  }
 }
 
 // f of one case at the cell centres (stored piece + deferred term), FP64.
@@ -1168,7 +1243,7 @@ int dvm_batch_create(const dvm_config* cfgs, int ncases, void* cuda_stream, dvm_
     c.w = g.w;
     double A[kMaxM * kMaxM];
     if (invert_moment_matrix(g, A)) { delete b; return DVM_ERR_ARG; }
-    for (int j = 0; j < g.nm * g.nm; ++j) c.A[j] = A[j];
+    for (int j = 0; j < g.nm * g.nm; ++j) c.A[j] = A[j], c.Af[j] = (float)A[j];
     const double l = exp(-g.dt / cfgs[i].tau);
     if (!(cfgs[i].tau >= 0)) { delete b; return DVM_ERR_ARG; }
     c.all_free = l == 1.0;

@@ -93,7 +93,7 @@ __global__ void k_cell_params(Geom g, DevPtrs p, int mode, int initial) {
   for (int i = 0; i < D + 2; ++i) Uc[i] = p.U[i * g.nc + c];
   const double lam = p.lam[c];
   if (mode == 0) {  // E[U] itself, in FP64, to build f^0
-    const int rc = cell_mu<D, true>(g, p.A, Uc, mu, rho, u, theta);
+    const int rc = cell_mu<D>(g, p.A, Uc, mu, rho, u, theta);
     if (rc) {
       set_status(p.status, rc);
       return;
@@ -112,7 +112,7 @@ __global__ void k_cell_params(Geom g, DevPtrs p, int mode, int initial) {
     }
     write_params_f32<D>(g, (float*)p.prm, c, (float)lam, (float)weight, rf, uf, tf, nullptr, muf);
   } else {
-    const int rc = cell_mu<D, true>(g, p.A, Uc, mu, rho, u, theta);
+    const int rc = cell_mu<D>(g, p.A, Uc, mu, rho, u, theta);
     if (rc) {
       set_status(p.status, rc);
       return;
@@ -1212,7 +1212,7 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Geom g, DevPtrs p) {
         for (int j = 0; j < NM; ++j) s += p.A[i * NM + j] * r[j];
         nu[i] = no_nu ? 0.0 : s;
       }
-      rc = cell_mu<D, true>(g, p.A, Un, mu, rho, u, theta);
+      rc = cell_mu<D>(g, p.A, Un, mu, rho, u, theta);
       if (!rc) write_params<TC, D>(g, (TC*)p.prm, c, lam, 1.0 - lam, rho, u, theta, HO ? nu : nullptr, mu);
     }
     if (rc) {

@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(kCheckBlock) k_learn_check(Geom g, DevPtrs p, 
     nu[i] = s;
   }
   double mu[kMaxM], rho, u[3], theta;
-  const int rc = cell_mu<D, true>(g, p.A, Un, mu, rho, u, theta);
+  const int rc = cell_mu<D>(g, p.A, Un, mu, rho, u, theta);
   double sums[2] = {0.0, 0.0};
   if (rc == 0) {
     const double pref = rho * pow(2.0 * M_PI * theta, -0.5 * D);
@@ -494,7 +494,7 @@ __global__ void k_noneq(Geom g, DevPtrs p, float* out) {
   double Uc[kMaxM], mu[kMaxM], rho, u[3], theta;
 #pragma unroll
   for (int i = 0; i < NM; ++i) Uc[i] = p.U[i * nc + c];
-  if (cell_mu<D, true>(g, p.A, Uc, mu, rho, u, theta)) {
+  if (cell_mu<D>(g, p.A, Uc, mu, rho, u, theta)) {
     out[c] = 0.f;
     return;
   }

@@ -219,7 +219,7 @@ __device__ inline long long cell_index(const Geom& g, const int x[3]) {
 
 // mu = (C C^T)^{-1} (U - C M[U]) of Eq. minimMax, with C M[U] from the
 // separable factors of the Maxwellian.  Returns 0 or an error code.
-template <int D, bool F64>
+template <int D>
 __device__ int cell_mu(const Geom& g, const double* A, const double* Uc, double mu[kMaxM],
                        double& rho, double u[3], double& theta) {
   constexpr int NM = D + 2;
@@ -230,12 +230,8 @@ __device__ int cell_mu(const Geom& g, const double* A, const double* Uc, double 
   if (!(rho > 0.0) || !(theta > 0.0)) return DVM_ERR_NONPHYSICAL;
   double G0[3], G1[3], G2[3];
 #pragma unroll
-  for (int i = 0; i < D; ++i) {
-    if (F64) gauss_axis_sums(g.nv[i], g.kmin[i], g.dv, u[i], theta, G0[i], G1[i], G2[i]);
-    else gauss_axis_sums_f32(g.nv[i], g.kmin[i], (float)g.dv, (float)u[i], (float)theta, G0[i], G1[i], G2[i]);
-  }
-  const double pref = F64 ? g.w * rho * pow(2.0 * M_PI * theta, -0.5 * D)
-                          : g.w * rho * (double)powf(6.283185307179586f * (float)theta, -0.5f * D);
+  for (int i = 0; i < D; ++i) gauss_axis_sums(g.nv[i], g.kmin[i], g.dv, u[i], theta, G0[i], G1[i], G2[i]);
+  const double pref = g.w * rho * pow(2.0 * M_PI * theta, -0.5 * D);
   double CM[kMaxM];
   double all = 1.0;
 #pragma unroll
