@@ -296,8 +296,9 @@ bool window_async(int d) {
 
 template <typename TS, int D, bool HO, bool AS>
 void launch_window_a(const Geom& g, const DevPtrs& p, const WinLaunch& wl, cudaStream_t s, bool prepare) {
-  if constexpr (std::is_same<TS, float>::value && HO && AS) {
-    // a configured shape: the kernel with compile-time extents
+  if constexpr (!std::is_same<TS, double>::value && HO && AS) {
+    // a configured shape: the kernel with compile-time extents (FP32; BF16
+    // staged, which the caller selects for an even N_x only)
     const bool fixed = launch_window_fixed(g, p, wl.splits, s, prepare);
     if (fixed && !prepare) return;
   }

@@ -3,7 +3,8 @@
 // time (2D 128^2, 256^2, 512^2 x 32^2; 3D 32^3, 64^3, 96^3 x 24^3): the index
 // and address arithmetic of the pass then works on constants (on GB300 about
 // a quarter of its instructions).  FP32 storage, HOFKS (2D also with the
-// learned path); every other configuration runs the same kernel with the extents read
+// learned path), and BF16 storage for the 2D 256^2 / 512^2 and 3D 64^3 / 96^3
+// shapes; every other configuration runs the same kernel with the extents read
 // at run time (dvm_kinetic.cu).
 #include <stdlib.h>
 
@@ -12,14 +13,16 @@
 namespace dvm {
 namespace {
 
-template <int D, int CX, int CY, int CZ, int CV, bool LE>
+template <int D, int CX, int CY, int CZ, int CV, bool LE, typename TS = float>
 bool try_shape(const Geom& g, const DevPtrs& p, int splits, cudaStream_t s, bool prepare) {
   if (g.nx[0] != CX || g.nx[1] != CY || (D == 3 && g.nx[2] != CZ)) return false;
   if (g.nv[0] != CV || g.nv[1] != CV || (D == 3 && g.nv[2] != CV)) return false;
   if (!prepare && (g.learn != 0) != LE) return false;
+  // (BF16 pieces are staged as aligned 4-byte words: N_x even)
+  static_assert(sizeof(TS) == 4 || CX % 2 == 0, "BF16 staging needs an even N_x");
   constexpr size_t sm = window_smem(D, true, true);
   constexpr int Y = WinShape<D>::Y;
-  auto* k = k_kpass_window<float, D, Y, true, true, LE, CX, CY, CZ, CV>;
+  auto* k = k_kpass_window<TS, D, Y, true, true, LE, CX, CY, CZ, CV>;
   if (prepare) {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     return true;
@@ -38,9 +41,20 @@ bool try_shape(const Geom& g, const DevPtrs& p, int splits, cudaStream_t s, bool
 // DVM_FIXED_SHAPES=0 runs the runtime-extent kernel for every shape (for
 // comparison runs and the test that both give the same result).
 bool launch_window_fixed(const Geom& g, const DevPtrs& p, int splits, cudaStream_t s, bool prepare) {
-  if (g.precision != DVM_F32 || g.scheme == DVM_FKS) return false;
+  if (g.precision == DVM_F64 || g.scheme == DVM_FKS) return false;
   const char* e = getenv("DVM_FIXED_SHAPES");
   if (e && e[0] == '0' && !prepare) return false;
+  if (g.precision == DVM_BF16S) {
+    // BF16 storage: the 2D 256^2 / 512^2 and 3D 64^3 / 96^3 shapes, no learned path
+    if (g.learn) return false;
+    if (g.d == 2)
+      return try_shape<2, 256, 256, 1, 32, false, __nv_bfloat16>(g, p, splits, s, prepare) ||
+             try_shape<2, 512, 512, 1, 32, false, __nv_bfloat16>(g, p, splits, s, prepare);
+    if (g.d == 3)
+      return try_shape<3, 64, 64, 64, 24, false, __nv_bfloat16>(g, p, splits, s, prepare) ||
+             try_shape<3, 96, 96, 96, 24, false, __nv_bfloat16>(g, p, splits, s, prepare);
+    return false;
+  }
   if (g.d == 2) {
     // with and without the learned path (both prepared at creation)
     bool hit = false;

@@ -302,6 +302,29 @@ def test_3d_shape_compiled_pass_equals_runtime_pass_at_bench_sizes(n, monkeypatc
 
 
 @pytest.mark.parametrize("make", [
+    lambda: W.quadrant_2d(n=256, nv=32, tau=1e-3, steps=2),
+    lambda: W.density_wave_3d(n=64, nv=24, tau=1e-2, steps=2, dv=0.5),
+], ids=["quadrant_256", "wave_3d_64"])
+def test_bf16_shape_compiled_pass_equals_runtime_pass(make, monkeypatch):
+    """BF16 storage at the configured shapes (2D 256^2 x 32^2, 3D 64^3 x 24^3): the
+    kernel compiled with the extents as constants gives moments (and f, in 2D)
+    bit-identical to the kernel with run-time extents over 2 steps."""
+    case = make()
+    out = []
+    for mode in ("1", "0"):
+        monkeypatch.setenv("DVM_FIXED_SHAPES", mode)
+        s = dvm.Solver.from_case(case, precision=dvm.BF16S)
+        s.set_moments(conserved(case))
+        s.step(case.steps)
+        out.append((s.moments(), s.f() if case.d == 2 else None))
+        s.close()
+        del s
+    assert np.array_equal(out[0][0], out[1][0])
+    if case.d == 2:
+        assert np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("make", [
     lambda: W.quadrant_2d(n=36, nv=16, tau=1e-3, steps=3, dv=0.7),
     lambda: W.density_wave_3d(n=10, nv=8, tau=1e-2, steps=2, dv=1.2),
 ], ids=["quadrant_36", "wave_3d_10"])
