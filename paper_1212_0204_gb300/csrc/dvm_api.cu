@@ -288,8 +288,13 @@ int enqueue_step(dvm_handle* h, cudaStream_t s, cudaEvent_t e0 = nullptr,
     ++n;
   }
   const bool euler = g.scheme != DVM_FKS && !g.skip_euler;
-  // profiled steps stay serial so that the events time the kinetic pass alone
-  const bool fork = euler && h->overlap && !check && !e0;
+  // profiled steps stay serial so that the events time the kinetic pass alone.
+  // 3D: serial as well -- the kinetic pass holds every SM's registers (3 CTAs
+  // of 168-register threads), so nothing runs beside it, and a cooperative
+  // Euler grid that finds the SMs taken waits at its grid barrier with part of
+  // its CTAs resident, holding shared memory the kinetic pass needs (measured:
+  // 64^3 step 7.17 ms serial, 9.78 ms forked)
+  const bool fork = euler && h->overlap && !check && !e0 && g.d < 3;
   if (euler) {
     cudaStream_t es = s;
     if (fork) {

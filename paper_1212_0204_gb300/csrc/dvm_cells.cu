@@ -1123,6 +1123,222 @@ __global__ void __launch_bounds__(G2Tile<D, TF, TALL>::THREADS) k_euler_g2(Geom 
   }
 }
 
+// 3D sub-steps marching along z.  A CTA owns a 32 x 4 column of cells over a
+// chunk of consecutive z planes.  Per plane it stages the plane's tile with its
+// two-cell x/y halo (whose x and y split fluxes G+- = F +- alpha W it
+// computes) and the tile's cells two planes ahead (their z split fluxes, kept
+// in a ring of five planes), then every thread updates its cell from its six
+// faces.  A cell's state is read ~3.3 times per sub-step (plus four ring planes
+// per chunk), against 11.25 with a 36 x 8 x 5 staging per 32 x 4 x 1 tile.
+// Face fluxes as in k_euler_g2: psi = (G+_j + G-_{j+1}) / 2 + (s+ - s-) / 4.
+template <typename TF>
+struct ZTile {
+  static constexpr int TX = 32, TY = 4, SX = TX + 4, SY = TY + 4;
+  static constexpr int NS = SX * SY;     // staged plane cells
+  static constexpr int CELLS = TX * TY;  // = threads
+  static constexpr int THREADS = CELLS;
+  static constexpr int NM = 5;
+  // W of the plane, G+- along x and y of the plane, G+- along z of five planes
+  static constexpr size_t SMEM = sizeof(TF) * ((size_t)NM * NS + 4 * NM * NS + 5 * 2 * NM * CELLS);
+};
+
+template <typename TF, bool LIMITED>
+__device__ inline TF face6(TF p0, TF p1, TF p2, TF m1, TF m2, TF m3) {
+  const TF sp = slope<TF, LIMITED>(p1 - p0, p2 - p1);
+  const TF sm = slope<TF, LIMITED>(m2 - m1, m3 - m2);
+  return TF(0.5) * (p1 + m2) + TF(0.25) * (sp - sm);
+}
+
+template <typename TF, bool LIMITED>
+__global__ void __launch_bounds__(ZTile<TF>::THREADS) k_euler_z(Geom g, DevPtrs p) {
+  using T = ZTile<TF>;
+  constexpr int NM = 5;
+  extern __shared__ unsigned char s_raw[];
+  __shared__ TF s_amax[3][T::THREADS / 32];
+  TF* sw = reinterpret_cast<TF*>(s_raw);  // [NM][NS]
+  TF* sg = sw + NM * T::NS;               // [dir x/y][+-][NM][NS]
+  TF* sz = sg + 4 * NM * T::NS;           // [ring 5][+-][NM][CELLS]
+  const int Nx = g.nx[0], Ny = g.nx[1], Nz = g.nx[2];
+  const long long nc = g.nc, plane = (long long)Nx * Ny;
+  const int ntx = (Nx + T::TX - 1) / T::TX, nty = (Ny + T::TY - 1) / T::TY;
+  const int ntxy = ntx * nty;
+  // z chunks: as many as the grid holds whole sets of column tiles
+  int chunks = (int)gridDim.x / ntxy;
+  chunks = chunks < 1 ? 1 : (chunks > Nz ? Nz : chunks);
+  const int zc_len = (Nz + chunks - 1) / chunks;
+  const int nitems = ntxy * chunks;
+  const int tid = threadIdx.x;
+  const int tx = tid % T::TX, ty = tid / T::TX;
+  const int ctr = (tx + 2) + T::SX * (ty + 2);
+  __shared__ double s_dtE;
+  __shared__ TF s_k, s_al[3];
+  __shared__ int s_last, s_bad;
+  double t = 0.0, a0[3] = {0.0, 0.0, 0.0};
+  int s = 0;
+  for (;; ++s) {
+    const TF* src = (const TF*)((s & 1) ? p.W1 : p.W0);
+    TF* dst = (TF*)((s & 1) ? p.W0 : p.W1);
+    if (tid == 0) {
+      double ad[3], asum = 0.0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) ad[d] = __longlong_as_double((long long)__ldcg(p.aslot + (s % 3) * 3 + d));
+#pragma unroll
+      for (int d = 0; d < 3; ++d) asum = __dadd_rn(asum, ad[d]);
+      if (s == 0) a0[0] = ad[0], a0[1] = ad[1], a0[2] = ad[2];
+      if (blockIdx.x == 0)
+        for (int d = 0; d < 3; ++d) p.aslot[((s + 2) % 3) * 3 + d] = 0ull;
+      double dtE = 0.0;
+      int last = 0, bad = 0;
+      if (g.forced_sub > 0) {
+        dtE = g.dt / g.forced_sub;
+        last = s + 1 == g.forced_sub;
+      } else if (!(asum > 0.0)) {
+        bad = 1;
+      } else {
+        const double cfl = sizeof(TF) == 8 ? __ddiv_rn(__dmul_rn(0.5, g.dx), asum)
+                                           : (double)__fdiv_rn(0.5f * (float)g.dx, (float)asum);
+        const double rem = __dsub_rn(g.dt, t);
+        last = cfl >= rem;
+        dtE = last ? rem : cfl;
+      }
+      s_dtE = dtE;
+      s_k = sizeof(TF) == 8 ? (TF)(dtE / g.dx) : (TF)((float)dtE / (float)g.dx);
+      for (int d = 0; d < 3; ++d) s_al[d] = (TF)ad[d];
+      s_last = last;
+      s_bad = bad;
+      if (bad && blockIdx.x == 0) set_status(p.status, DVM_ERR_NONPHYSICAL);
+    }
+    __syncthreads();
+    if (s_bad) return;
+    const bool last = s_last != 0;
+    const TF k = s_k;
+    const TF al0 = s_al[0], al1 = s_al[1], al2 = s_al[2];
+    TF amax[3] = {TF(0), TF(0), TF(0)};
+    // z split fluxes of the tile's cells on plane zz into ring slot zz mod 5
+    auto ring_plane = [&](int x0, int y0, int zz) {
+      const int gx = bc_index(x0 + tx, Nx, g.bc[0]);
+      const int gy = bc_index(y0 + ty, Ny, g.bc[1]);
+      const int gz = bc_index(zz, Nz, g.bc[2]);
+      const long long cc = gx + (long long)Nx * gy + plane * gz;
+      TF U[NM], F[NM];
+#pragma unroll
+      for (int c = 0; c < NM; ++c) U[c] = __ldcg(src + c * nc + cc);
+      euler_flux<TF, 3>(U, 2, F);
+      TF* r = sz + ((zz + 5) % 5) * 2 * NM * T::CELLS;
+#pragma unroll
+      for (int c = 0; c < NM; ++c) {
+        r[c * T::CELLS + tid] = F[c] + al2 * U[c];
+        r[(NM + c) * T::CELLS + tid] = F[c] - al2 * U[c];
+      }
+    };
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+      const int txy = item % ntxy, chunk = item / ntxy;
+      const int x0 = (txy % ntx) * T::TX, y0 = (txy / ntx) * T::TY;
+      const int z0 = chunk * zc_len;
+      const int z1 = z0 + zc_len < Nz ? z0 + zc_len : Nz;
+      if (z0 >= z1) continue;
+      for (int zz = z0 - 2; zz < z0 + 2; ++zz) ring_plane(x0, y0, zz);
+      for (int zc = z0; zc < z1; ++zc) {
+        // phase 1: the plane's tile and halo with its x and y split fluxes,
+        // and the z split fluxes two planes ahead
+        const int gz = bc_index(zc, Nz, g.bc[2]);
+        for (int i = tid; i < T::NS; i += T::THREADS) {
+          const int lx = i % T::SX, ly = i / T::SX;
+          const int gx = bc_index(x0 - 2 + lx, Nx, g.bc[0]);
+          const int gy = bc_index(y0 - 2 + ly, Ny, g.bc[1]);
+          const long long cc = gx + (long long)Nx * gy + plane * gz;
+          TF U[NM], F[NM];
+#pragma unroll
+          for (int c = 0; c < NM; ++c) {
+            U[c] = __ldcg(src + c * nc + cc);
+            sw[c * T::NS + i] = U[c];
+          }
+          euler_flux<TF, 3>(U, 0, F);
+#pragma unroll
+          for (int c = 0; c < NM; ++c) {
+            sg[(0 * NM + c) * T::NS + i] = F[c] + al0 * U[c];
+            sg[(1 * NM + c) * T::NS + i] = F[c] - al0 * U[c];
+          }
+          euler_flux<TF, 3>(U, 1, F);
+#pragma unroll
+          for (int c = 0; c < NM; ++c) {
+            sg[(2 * NM + c) * T::NS + i] = F[c] + al1 * U[c];
+            sg[(3 * NM + c) * T::NS + i] = F[c] - al1 * U[c];
+          }
+        }
+        ring_plane(x0, y0, zc + 2);
+        __syncthreads();
+        // phase 2: every thread its cell, from its six faces
+        const int gx = x0 + tx, gy = y0 + ty;
+        if (gx < Nx && gy < Ny) {
+          const long long cell = gx + (long long)Nx * gy + plane * zc;
+          const TF* r0 = sz + ((zc + 3) % 5) * 2 * NM * T::CELLS;  // zc - 2
+          const TF* r1 = sz + ((zc + 4) % 5) * 2 * NM * T::CELLS;  // zc - 1
+          const TF* r2 = sz + (zc % 5) * 2 * NM * T::CELLS;
+          const TF* r3 = sz + ((zc + 1) % 5) * 2 * NM * T::CELLS;
+          const TF* r4 = sz + ((zc + 2) % 5) * 2 * NM * T::CELLS;
+          TF Wn[NM];
+#pragma unroll
+          for (int c = 0; c < NM; ++c) {
+            TF acc = TF(0);
+            {
+              const TF* gp = sg + (0 * NM + c) * T::NS;
+              const TF* gm = sg + (1 * NM + c) * T::NS;
+              acc += face_g<TF, LIMITED>(gp, gm, ctr, 1) - face_g<TF, LIMITED>(gp, gm, ctr - 1, 1);
+            }
+            {
+              const TF* gp = sg + (2 * NM + c) * T::NS;
+              const TF* gm = sg + (3 * NM + c) * T::NS;
+              acc += face_g<TF, LIMITED>(gp, gm, ctr, T::SX) - face_g<TF, LIMITED>(gp, gm, ctr - T::SX, T::SX);
+            }
+            {
+              const int op = c * T::CELLS + tid, om = (NM + c) * T::CELLS + tid;
+              const TF hi = face6<TF, LIMITED>(r1[op], r2[op], r3[op], r2[om], r3[om], r4[om]);
+              const TF lo = face6<TF, LIMITED>(r0[op], r1[op], r2[op], r1[om], r2[om], r3[om]);
+              acc += hi - lo;
+            }
+            Wn[c] = sw[c * T::NS + ctr] - k * acc;
+            dst[c * nc + cell] = Wn[c];
+          }
+          if (!last) {
+            TF an[3];
+            state_alpha_of<3>(Wn, an);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) amax[d] = amax[d] > an[d] ? amax[d] : an[d];
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (tid == 0) t = __dadd_rn(t, s_dtE);
+    if (last) break;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      TF v = amax[d];
+      for (int o = 16; o > 0; o >>= 1) {
+        const TF w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = v > w ? v : w;
+      }
+      if ((tid & 31) == 0) s_amax[d][tid >> 5] = v;
+    }
+    __syncthreads();
+    if (tid < 3) {
+      TF v = TF(0);
+      for (int w = 0; w < T::THREADS / 32; ++w) v = v > s_amax[tid][w] ? v : s_amax[tid][w];
+      atomicMax(p.aslot + ((s + 1) % 3) * 3 + tid, (unsigned long long)__double_as_longlong((double)v));
+    }
+    if (s + 1 >= g.m_cap) {
+      if (blockIdx.x == 0 && tid == 0) set_status(p.status, DVM_ERR_CFL);
+      break;
+    }
+    if (!grid_sync(p.gbar, p.status)) return;
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    *p.msub = s + 1;
+    for (int d = 0; d < 3; ++d) p.alpha[d] = a0[d];
+  }
+}
+
 // Outflow: snapshot of the boundary pieces of every velocity before the
 // in-place kinetic pass overwrites them (1D: cells 0 and N-1).
 template <typename TS>
@@ -1421,15 +1637,46 @@ cudaError_t launch_euler_g2(const Geom& g, const DevPtrs& p, cudaStream_t s, boo
   return launch_euler_g2_t<TF, LIM, D, false>(g, p, s, prepare, blocks);
 }
 
+template <typename TF, bool LIM>
+cudaError_t launch_euler_z(const Geom& g, const DevPtrs& p, cudaStream_t s, bool prepare, int* blocks) {
+  using T = ZTile<TF>;
+  if (prepare) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_euler_z<TF, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_euler_z<TF, LIM>, T::THREADS, T::SMEM);
+    const long long nb = (long long)sms * (per_sm < 1 ? 1 : per_sm);
+    // one work item per (column tile, z plane) at most
+    const long long need = (long long)((g.nx[0] + T::TX - 1) / T::TX) * ((g.nx[1] + T::TY - 1) / T::TY) * g.nx[2];
+    *blocks = (int)(nb < need ? nb : need);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)g.euler_blocks);
+  cfg.blockDim = dim3(T::THREADS);
+  cfg.dynamicSmemBytes = T::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_euler_z<TF, LIM>, g, p);
+}
+
 template <typename TF, bool LIM, int D>
 cudaError_t launch_euler_t(const Geom& g, const DevPtrs& p, cudaStream_t s, bool prepare,
                            int* blocks) {
+  // DVM_EULER_KERNEL: 1 the per-face-flux kernel, 2 (1D/2D) the four-phase
+  // split-flux kernel (comparison runs); default the two-phase one (1D/2D)
+  // and the z-marching one (3D)
+  const char* e = getenv("DVM_EULER_KERNEL");
   if constexpr (D <= 2) {
-    // DVM_EULER_KERNEL: 1 the per-face-flux kernel, 2 the four-phase
-    // split-flux kernel (comparison runs); default the two-phase one
-    const char* e = getenv("DVM_EULER_KERNEL");
     if (e && e[0] == '2') return launch_euler_g<TF, LIM, D>(g, p, s, prepare, blocks);
     if (!(e && e[0] == '1')) return launch_euler_g2<TF, LIM, D>(g, p, s, prepare, blocks);
+  } else {
+    if (!(e && e[0] == '1')) return launch_euler_z<TF, LIM>(g, p, s, prepare, blocks);
   }
   using T = ETile<D, TF>;
   if (prepare) {
