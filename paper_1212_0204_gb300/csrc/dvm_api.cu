@@ -138,6 +138,10 @@ int make_geom(const dvm_config* cfg, Geom* g, std::string* msg) {
   for (int i = 0; i < d; ++i) outflow |= g->bc[i] == DVM_BC_OUTFLOW;
   g->ghost_mode = outflow ? (d == 1 ? 1 : 2) : 0;
   g->nsplit = kinetic_pass_splits(*g);
+  // 3D HOFKS on the windowed pass: one more split for the moments of the
+  // transported linear term (dvm_linmom.cu)
+  g->lin_slice = g->d == 3 && kinetic_is_windowed(*g) && g->scheme != DVM_FKS ? 1 : 0;
+  g->nsplit += g->lin_slice;
   return 0;
 }
 
@@ -146,7 +150,7 @@ int make_geom(const dvm_config* cfg, Geom* g, std::string* msg) {
 namespace {
 
 struct Layout {
-  size_t F, ghost, U, lam, W0, W1, Wt, acc, prm, wprm, eqp, gtab, UE, UM, Us, A, small, offs, total;
+  size_t F, ghost, U, lam, W0, W1, Wt, acc, prm, wprm, lin, eqp, gtab, UE, UM, Us, A, small, offs, total;
 };
 
 Layout layout(const Geom& g) {
@@ -166,6 +170,7 @@ Layout layout(const Geom& g) {
   L.acc = take(8 * (size_t)g.nsplit * 2 * nm * nc);
   L.prm = take(tc * (size_t)prm_rows(g.d) * nc);
   L.wprm = take(g.d >= 2 && g.precision != DVM_F64 ? 4 * 16 * nc : 0);
+  L.lin = take(g.lin_slice ? 4 * (size_t)linear_moment_arrays() * nc : 0);
   L.eqp = take(8 * (size_t)prm_rows(g.d) * nc);
   L.gtab = take(g.precision == DVM_F64 ? 8 * nc * (size_t)(1 + g.nv[0] + (g.d > 1 ? g.nv[1] : 0) +
                                                            (g.d > 2 ? g.nv[2] : 0))
@@ -242,6 +247,7 @@ void bind(dvm_handle* h, char* base, const Layout& L) {
   p.acc = (double*)(base + L.acc);
   p.prm = base + L.prm;
   p.wprm = (float*)(base + L.wprm);
+  p.lin = (float*)(base + L.lin);
   p.eqp = (double*)(base + L.eqp);
   p.gtab = (double*)(base + L.gtab);
   p.UE = (double*)(base + L.UE);
@@ -295,6 +301,7 @@ int enqueue_step(dvm_handle* h, cudaStream_t s, cudaEvent_t e0 = nullptr,
   // its CTAs resident, holding shared memory the kinetic pass needs (measured:
   // 64^3 step 7.17 ms serial, 9.78 ms forked)
   const bool fork = euler && h->overlap && !check && !e0 && g.d < 3;
+  const bool lin = g.lin_slice && kinetic_is_windowed(g);
   if (euler) {
     cudaStream_t es = s;
     if (fork) {
@@ -304,8 +311,11 @@ int enqueue_step(dvm_handle* h, cudaStream_t s, cudaEvent_t e0 = nullptr,
     }
     const int rc = cuda_check(h, launch_euler(g, h->p, es), "Euler launch");
     if (rc) return rc;
-    if (fork) cudaEventRecord(h->join, h->side);
     ++n;
+    // the moments of the transported linear term (windowed HOFKS) need only
+    // the parameters: beside the kinetic pass, after the Euler sub-steps
+    if (fork && lin) n += launch_linear_moments(g, h->p, h->side);
+    if (fork) cudaEventRecord(h->join, h->side);
   }
   if (g.ghost_mode) {
     launch_ghost(g, h->p, s);
@@ -318,6 +328,7 @@ int enqueue_step(dvm_handle* h, cudaStream_t s, cudaEvent_t e0 = nullptr,
     ++n;
   }
   if (e0) cudaEventRecord(e0, s);
+  if (lin && !fork) n += launch_linear_moments(g, h->p, s);
   n += launch_kinetic_pass(g, h->p, s);
   if (e1) cudaEventRecord(e1, s);
   if (fork) cudaStreamWaitEvent(s, h->join, 0);
@@ -835,6 +846,7 @@ int dvm_launches_per_step(dvm_handle* h, int* launches) {
   if (h->g.ghost_mode) n += 1;
   // (folded parameters or the FP64 Maxwellian factors +) kinetic pass
   n += (kinetic_is_windowed(h->g) || h->g.precision == DVM_F64) ? 2 : 1;
+  if (h->g.lin_slice && !h->g.learn) n += 3;  // linear-term moments
   n += 1;                                  // end-of-step kernel
   *launches = n;
   return 0;
@@ -848,7 +860,7 @@ int dvm_kinetic_kernel(const dvm_handle* h, int* kind) {
 
 int dvm_kinetic_splits(const dvm_handle* h, int* splits) {
   if (!h || !splits) return DVM_ERR_ARG;
-  *splits = h->g.nsplit;
+  *splits = h->g.nsplit - h->g.lin_slice;
   return 0;
 }
 

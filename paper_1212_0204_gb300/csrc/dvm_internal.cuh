@@ -72,7 +72,8 @@ struct Geom {
   int precision;      // DVM_F64 / DVM_F32 / DVM_BF16S
   int forced_sub;     // > 0: fixed Euler sub-steps
   int m_cap;          // launch cap of Euler sub-steps
-  int nsplit;         // velocity chunks of the kinetic pass
+  int nsplit;         // velocity chunks of the kinetic pass (+1: lin_slice)
+  int lin_slice;      // 1: the last chunk holds the linear-term moments (dvm_linmom.cu)
   int ghost_mode;     // 0 none, 1 two boundary pieces per velocity (1D), 2 full copy
   int skip_euler;     // every lambda == 1: U_E = 0, no Euler launch
   int euler_blocks;   // grid of the cooperative Euler launch (all co-resident)
@@ -90,6 +91,7 @@ struct DevPtrs {
   double* acc;        // nsplit x 2nm x nc partial moment sums
   void* prm;          // NP x nc, compute type
   float* wprm;        // 16 x nc, the window pass's per-cell parameters (FP32 tiers, d >= 2)
+  float* lin;         // linear_moment_arrays() x nc, 1D sums of the linear-term moments (3D)
   double* eqp;        // NP x nc, FP64 parameters of E[U] (initial state only)
   double* gtab;       // FP64 build: (1 + sum_i nv_i) x nc separable Maxwellian factors (k_gauss_tables)
   double* UE;         // nm x nc, last step's U_E (FP64 copy)
@@ -174,5 +176,10 @@ int launch_kinetic_pass(const Geom& g, const DevPtrs& p, cudaStream_t s);  // ke
 bool launch_window_fixed(const Geom& g, const DevPtrs& p, int splits, cudaStream_t s, bool prepare);
 void kinetic_pass_prepare(const Geom& g);
 int kinetic_pass_splits(const Geom& g);
+bool kinetic_is_windowed(const Geom& g);
+// dvm_linmom.cu (3D windowed HOFKS)
+int linear_moment_arrays();
+int launch_linear_moments(const Geom& g, const DevPtrs& p, cudaStream_t s);  // kernels launched
+void linear_moments_prepare(const Geom& g);
 
 }  // namespace dvm

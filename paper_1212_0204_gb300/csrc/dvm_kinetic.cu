@@ -239,6 +239,36 @@ __global__ void __launch_bounds__(256) k_window_fold(Geom g, DevPtrs p) {
   for (int q = 0; q < 4; ++q) wg[q * nc + c] = o[q];
 }
 
+// 3D HOFKS without the learned path: the same rows with the deferred and the
+// moment-matching quadratics summed, P = lambda nu' + mu'' (SlotP layout of
+// dvm_window.cuh).
+__global__ void __launch_bounds__(256) k_window_fold_p(Geom g, DevPtrs p) {
+  constexpr int D = 3;
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nc = g.nc;
+  if (c >= nc) return;
+  const float4* __restrict__ pg = (const float4*)p.prm;
+  float r[16];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float4 v = __ldg(pg + q * nc + c);
+    r[4 * q] = v.x, r[4 * q + 1] = v.y, r[4 * q + 2] = v.z, r[4 * q + 3] = v.w;
+  }
+  const float lam = r[row_lam()], L = r[row_L()], h = r[row_h(D)];
+  const float ux = r[row_u(0)], uy = r[row_u(1)], uz = r[row_u(2)];
+  const float u2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+  float P[5];
+#pragma unroll
+  for (int i = 0; i < D + 2; ++i) P[i] = fmaf(lam, r[row_nu(D, i)], r[row_mu(D, i)]);
+  float4 o[3];
+  o[0] = make_float4(lam, fmaf(-h, u2, L), h, 2.f * h * uy);
+  o[1] = make_float4(2.f * h * ux, 2.f * h * uz, P[0], P[1]);
+  o[2] = make_float4(P[2], P[3], P[4], 0.f);
+  float4* __restrict__ wg = (float4*)p.wprm;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) wg[q * nc + c] = o[q];
+}
+
 
 bool window_eligible(const Geom& g) {
   if (g.d < 2 || g.precision == DVM_F64 || g.p != 1) return false;
@@ -372,6 +402,7 @@ int kinetic_pass_splits(const Geom& g) {
 // stream capture): dynamic shared memory of the windowed pass.
 void kinetic_pass_prepare(const Geom& g) {
   if (!window_eligible(g)) return;
+  if (g.lin_slice) linear_moments_prepare(g);
   DevPtrs none{};
   if (g.precision == DVM_F32) launch_window<float>(g, none, nullptr, true);
   else launch_window<__nv_bfloat16>(g, none, nullptr, true);
@@ -386,8 +417,13 @@ bool kinetic_is_windowed(const Geom& g) {
 int launch_kinetic_pass(const Geom& g, const DevPtrs& p, cudaStream_t s) {
   if (kinetic_is_windowed(g)) {
     const unsigned nb = (unsigned)((g.nc + 255) / 256);
-    if (g.d == 2) k_window_fold<2><<<nb, 256, 0, s>>>(g, p);
-    else k_window_fold<3><<<nb, 256, 0, s>>>(g, p);
+    if (g.d == 3 && g.scheme != DVM_FKS && !g.learn) {
+      k_window_fold_p<<<nb, 256, 0, s>>>(g, p);
+    } else if (g.d == 2) {
+      k_window_fold<2><<<nb, 256, 0, s>>>(g, p);
+    } else {
+      k_window_fold<3><<<nb, 256, 0, s>>>(g, p);
+    }
     if (g.precision == DVM_F32) launch_window<float>(g, p, s);
     else launch_window<__nv_bfloat16>(g, p, s);
     return 2;

@@ -78,10 +78,46 @@ __device__ __forceinline__ Slot fold_slot(const RawSlot& r, float vx, float vz, 
   return s;
 }
 
+// 3D HOFKS without the learned path: the deferred term lambda nu'.m and the
+// moment-matching term mu''.m enter the stored value only as their sum, so
+// the window keeps one quadratic P = (Lambda + mu'').m (the moments of the
+// mu''.m part come per cell from dvm_linmom.cu).  Three groups:
+//   (lambda, L', h, h2_y) (h2_x, h2_z, P_0, P_x) (P_y, P_z, P_4, 0)
+struct SlotP {
+  // M = exp2(c0 + c1 vy + c2 vy^2); P = p0 + p1 vy + p2 vy^2
+  float lam, c0, c1, c2, p0, p1, p2;
+};
+
+template <int D>
+__device__ __forceinline__ SlotP fold_slot_p(const RawSlot& r, float vx, float vz, float vxz2) {
+  static_assert(D == 3, "the single-quadratic form is the 3D pass's");
+  const float4 g0 = r.g0, g1 = r.g1, g2 = r.g2;
+  SlotP s;
+  const float h = g0.z;
+  s.lam = g0.x;
+  s.c2 = -h;
+  s.c1 = g0.w;
+  s.c0 = fmaf(-h, vxz2, fmaf(vz, g1.y, fmaf(vx, g1.x, g0.y)));
+  s.p0 = fmaf(g2.z, vxz2, fmaf(g2.y, vz, fmaf(g1.w, vx, g1.z)));
+  s.p1 = g2.x;
+  s.p2 = g2.z;
+  return s;
+}
+
 template <int D>
 __device__ __forceinline__ Slot load_slot(const float4* __restrict__ pg, long long nc4, int src,
                                           float vx, float vz, float vxz2) {
   return fold_slot<D>(load_raw(pg, nc4, src), vx, vz, vxz2);
+}
+
+template <int D>
+__device__ __forceinline__ SlotP load_slot_p(const float4* __restrict__ pg, long long nc4, int src,
+                                             float vx, float vz, float vxz2) {
+  RawSlot r;
+  r.g0 = __ldg(pg + src);
+  r.g1 = __ldg(pg + nc4 + src);
+  r.g2 = __ldg(pg + 2 * nc4 + src);
+  return fold_slot_p<D>(r, vx, vz, vxz2);
 }
 
 }  // namespace dvm

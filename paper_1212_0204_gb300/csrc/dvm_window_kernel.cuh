@@ -73,9 +73,10 @@ struct WinLaunch {
 // Shape of the windowed pass per dimension, measured on GB300: warps per CTA
 // (each on every S-th velocity pair; their parameter loads share L1 lines),
 // resident CTAs per SM it is compiled for (register cap 65536 / (32 S MINB)),
-// how many of the four parameter groups of the next source row are loaded
-// a step ahead of their fold (the others at fold time: more in flight costs
-// registers), and the targets (consecutive y cells) per thread.  The DVM_W2_*
+// how many of the parameter groups of the next source row are loaded a step
+// ahead of their fold (the others at fold time: more in flight costs
+// registers; 3D loads all three groups of its single-quadratic form ahead),
+// and the targets (consecutive y cells) per thread.  The DVM_W2_*
 // / DVM_W3_* macros override them at compile time (shape sweeps).
 #ifndef DVM_W2_S
 #define DVM_W2_S 8
@@ -96,7 +97,7 @@ struct WinLaunch {
 #define DVM_W3_MINB 3
 #endif
 #ifndef DVM_W3_EARLY
-#define DVM_W3_EARLY 1
+#define DVM_W3_EARLY 3
 #endif
 #ifndef DVM_W3_Y
 #define DVM_W3_Y 4
@@ -125,6 +126,12 @@ __global__ void __launch_bounds__(32 * WinShape<D>::S, WinShape<D>::MINB)
   constexpr int S = WinShape<D>::S;
   constexpr int kWinT = 32 * S;
   constexpr int EARLY = WinShape<D>::EARLY;
+  // 3D HOFKS without the learned path keeps one quadratic per source (SlotP)
+  // and sums the new value and the Maxwellian part instead of the two parts
+  // a and b; U_* and U_M follow per cell with the moments of the transported
+  // mu''.m term (dvm_linmom.cu)
+  constexpr bool CP = HOFKS && !LEARN && D == 3;
+  using SlotT = typename std::conditional<CP, SlotP, Slot>::type;
   __shared__ int s_ox[kMaxV1], s_oy[kMaxV1], s_oz[kMaxV1];
   // dynamic: FP64 sums per (moment, target) and lane, shared by the S warps,
   // then each thread's FP32 sums of the current kz plane
@@ -271,11 +278,12 @@ __global__ void __launch_bounds__(32 * WinShape<D>::S, WinShape<D>::MINB)
     const int dst_base = qx + plane * qz;
     TS* __restrict__ Fb = F + ((long long)kx + (long long)nvx * nvy * kz) * nc + dst_base;
     // window: slot i holds source row (sy_first + i), wrapped
-    Slot win[Y];
+    SlotT win[Y];
     int rnext = sy_first;
 #pragma unroll
     for (int i = 0; i < Y; ++i) {
-      win[i] = load_slot<D>(pg, nc, src_base + Nx * rnext, vx, vz, vxz2);
+      if constexpr (CP) win[i] = load_slot_p<D>(pg, nc, src_base + Nx * rnext, vx, vz, vxz2);
+      else win[i] = load_slot<D>(pg, nc, src_base + Nx * rnext, vx, vz, vxz2);
       if (++rnext == Ny) rnext = 0;
     }
     float in0[NT][Y], in1[NT][Y], in2[NT][Y];
@@ -337,7 +345,7 @@ __global__ void __launch_bounds__(32 * WinShape<D>::S, WinShape<D>::MINB)
           raw.g0 = __ldg(pg + src_next);
           if (EARLY > 1) raw.g1 = __ldg(pg + nc + src_next);
           if (EARLY > 2) raw.g2 = __ldg(pg + 2 * nc + src_next);
-          if (EARLY > 3) raw.g3 = __ldg(pg + 3 * nc + src_next);
+          if (EARLY > 3 && !CP) raw.g3 = __ldg(pg + 3 * nc + src_next);
           float fj[Y];
 #pragma unroll
           for (int j = 0; j < Y; ++j)
@@ -348,10 +356,21 @@ __global__ void __launch_bounds__(32 * WinShape<D>::S, WinShape<D>::MINB)
           float fn[Y];
 #pragma unroll
           for (int j = 0; j < Y; ++j) {
-            const Slot& sl = win[(jj + j) % Y];
+            const SlotT& sl = win[(jj + j) % Y];
             const float M = ex2_ftz(fmaf(sl.c2, vy2, fmaf(sl.c1, vy, sl.c0)));
-            const float lm = fmaf(sl.b2, vy2, fmaf(sl.b1, vy, sl.b0));
-            if (HOFKS) {
+            if constexpr (CP) {
+              // new value lambda f + P + M; sums of it and of M
+              const float P = fmaf(sl.p2, vy2, fmaf(sl.p1, vy, sl.p0));
+              const float fv = fmaf(sl.lam, fj[j], P) + M;
+              fn[j] = fv;
+              in0[0][j] += fv;
+              in1[0][j] = fmaf(fv, vy, in1[0][j]);
+              in2[0][j] = fmaf(fv, vy2, in2[0][j]);
+              in0[1][j] += M;
+              in1[1][j] = fmaf(M, vy, in1[1][j]);
+              in2[1][j] = fmaf(M, vy2, in2[1][j]);
+            } else if constexpr (HOFKS) {
+              const float lm = fmaf(sl.b2, vy2, fmaf(sl.b1, vy, sl.b0));
               const float a = fmaf(sl.lam, fj[j], fmaf(sl.a2, vy2, fmaf(sl.a1, vy, sl.a0)));
               const float b = M + lm;  // T((1 - lambda) E^n)
               fn[j] = a + b;           // a = T(lambda f^n)
@@ -362,6 +381,7 @@ __global__ void __launch_bounds__(32 * WinShape<D>::S, WinShape<D>::MINB)
               in1[NT - 1][j] = fmaf(b, vy, in1[NT - 1][j]);
               in2[NT - 1][j] = fmaf(b, vy2, in2[NT - 1][j]);
             } else {
+              const float lm = fmaf(sl.b2, vy2, fmaf(sl.b1, vy, sl.b0));
               const float fs = fj[j] + M + lm;  // transported f
               fn[j] = lam_c[j] * fs;            // its lambda part; the rest is deferred
               in0[0][j] += fs;
@@ -387,8 +407,9 @@ __global__ void __launch_bounds__(32 * WinShape<D>::S, WinShape<D>::MINB)
           // slide: the slot just left by target 0 takes the next source row
           if (EARLY <= 1) raw.g1 = __ldg(pg + nc + src_next);
           if (EARLY <= 2) raw.g2 = __ldg(pg + 2 * nc + src_next);
-          if (EARLY <= 3) raw.g3 = __ldg(pg + 3 * nc + src_next);
-          win[jj % Y] = fold_slot<D>(raw, vx, vz, vxz2);
+          if (EARLY <= 3 && !CP) raw.g3 = __ldg(pg + 3 * nc + src_next);
+          if constexpr (CP) win[jj % Y] = fold_slot_p<D>(raw, vx, vz, vxz2);
+          else win[jj % Y] = fold_slot<D>(raw, vx, vz, vxz2);
           if (++rnext == Ny) rnext = 0;
         }
       };
@@ -437,7 +458,10 @@ __global__ void __launch_bounds__(32 * WinShape<D>::S, WinShape<D>::MINB)
     const int xx = blockIdx.x * 32 + l;
     if (xx >= Nx || y0 + j >= Ny) continue;
     const long long cell = xx + (long long)Nx * (y0 + j) + (long long)plane * z;
-    p.acc[((long long)split * 2 * NM + a) * nc + cell] = s_acc[e][l];
+    // combined form: the first part holds the sums of the new value, so
+    // U_* - (its mu''.m part) is that minus the Maxwellian part's sums
+    const double v = CP && a < NM ? s_acc[e][l] - s_acc[e + NM * Y][l] : s_acc[e][l];
+    p.acc[((long long)split * 2 * NM + a) * nc + cell] = v;
   }
 }
 
