@@ -301,6 +301,10 @@ int enqueue_step(dvm_handle* h, cudaStream_t s, cudaEvent_t e0 = nullptr,
   // its CTAs resident, holding shared memory the kinetic pass needs (measured:
   // 64^3 step 7.17 ms serial, 9.78 ms forked)
   const bool fork = euler && h->overlap && !check && !e0 && g.d < 3;
+  // 3D windowed HOFKS: the moments of the transported linear term, right
+  // before the kinetic pass (inside its events in profiled steps).  On a side
+  // stream beside the cooperative Euler grid they delayed its CTAs: 96^3 step
+  // 24.4 -> 35.7 ms
   const bool lin = g.lin_slice && kinetic_is_windowed(g);
   if (euler) {
     cudaStream_t es = s;
@@ -312,9 +316,6 @@ int enqueue_step(dvm_handle* h, cudaStream_t s, cudaEvent_t e0 = nullptr,
     const int rc = cuda_check(h, launch_euler(g, h->p, es), "Euler launch");
     if (rc) return rc;
     ++n;
-    // the moments of the transported linear term (windowed HOFKS) need only
-    // the parameters: beside the kinetic pass, after the Euler sub-steps
-    if (fork && lin) n += launch_linear_moments(g, h->p, h->side);
     if (fork) cudaEventRecord(h->join, h->side);
   }
   if (g.ghost_mode) {
@@ -328,7 +329,7 @@ int enqueue_step(dvm_handle* h, cudaStream_t s, cudaEvent_t e0 = nullptr,
     ++n;
   }
   if (e0) cudaEventRecord(e0, s);
-  if (lin && !fork) n += launch_linear_moments(g, h->p, s);
+  if (lin) n += launch_linear_moments(g, h->p, s);
   n += launch_kinetic_pass(g, h->p, s);
   if (e1) cudaEventRecord(e1, s);
   if (fork) cudaStreamWaitEvent(s, h->join, 0);
