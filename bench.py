@@ -439,11 +439,20 @@ def run_learned(args, case, descr, rank, local):
     net = learned.train_for_shear_layer(n=128, nv=case.nv[0], nsnap=200, warmup=10, dv=case.dv)
     mlp_prec = dvm.BF16S if args.mlp == "bf16" else dvm.F32
 
-    def run(precision, with_net):
+    # an ideal regime detector: the fluid zones themselves (lambda = exp(-dt/tau) <
+    # 5e-5, where the kinetic part lambda f of the update is below FP32 resolution
+    # of the new value), given as fixed flags instead of the network's
+    dt = case.dx / (case.p * case.dv)
+    fluid = np.exp(-dt / np.asarray(case.tau, dtype=np.float64)) < 5e-5
+
+    def run(precision, with_net, given=None):
         s = dvm.Solver.from_case(case, precision=precision)
         s.set_primitive(case.rho, case.u, case.T)
         if with_net:
             learned.enable(s, net, args.thr, mlp_precision=mlp_prec)
+        elif given is not None:
+            s.learn_enable(dvm.LEARN_GIVEN)
+            s.learn_set_flags(given)
         s.step(args.warmup)
         start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -454,7 +463,7 @@ def run_learned(args, case, descr, rank, local):
         s.sync_status()
         ms = start.elapsed_time(stop) / (args.steps - args.warmup)
         U = s.moments()
-        st = s.learn_stats() if with_net else None
+        st = s.learn_stats() if (with_net or given is not None) else None
         kin = None
         if precision == dvm.F32:
             s.profile_begin()
@@ -468,6 +477,7 @@ def run_learned(args, case, descr, rank, local):
         U64, ms64, _, _ = run(dvm.F64, False)
         U32, ms32, _, kin32 = run(dvm.F32, False)
         UL, msl, st, kinl = run(dvm.F32, True)
+        UI, msi, sti, kini = run(dvm.F32, False, given=fluid)
     l1 = lambda U: float(np.abs(U[0] - U64[0]).sum() / np.abs(U64[0]).sum())
     pts = case.points
     ups = lambda ms: pts / (ms * 1e-3)
@@ -492,6 +502,10 @@ def run_learned(args, case, descr, rank, local):
         "plain_fp32": {"updates_per_s": ups(ms32), "ms_per_step": ms32, "l1_vs_fp64": l1(U32),
                        "kinetic_ms": kin32},
         "plain_fp64": {"updates_per_s": ups(ms64), "ms_per_step": ms64},
+        "ideal_flags": {"what": "fixed flags on the fluid zones (lambda < 5e-5), no network: "
+                                "an upper bound on what a regime detector can skip here",
+                        "flagged_fraction": float(fluid.mean()), "updates_per_s": ups(msi),
+                        "ms_per_step": msi, "kinetic_ms": kini, "l1_vs_fp64": l1(UI)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "kinetic_pass (learned run)",
                      "peak_source": peak_kind, "kernel_ms": kinl},
