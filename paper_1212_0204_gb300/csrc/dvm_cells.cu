@@ -1127,10 +1127,14 @@ __global__ void __launch_bounds__(G2Tile<D, TF, TALL>::THREADS) k_euler_g2(Geom 
 // chunk of consecutive z planes.  Per plane it stages the plane's tile with its
 // two-cell x/y halo (whose x and y split fluxes G+- = F +- alpha W it
 // computes) and the tile's cells two planes ahead (their z split fluxes, kept
-// in a ring of five planes), then every thread updates its cell from its six
-// faces.  A cell's state is read ~3.3 times per sub-step (plus four ring planes
-// per chunk), against 11.25 with a 36 x 8 x 5 staging per 32 x 4 x 1 tile.
-// Face fluxes as in k_euler_g2: psi = (G+_j + G-_{j+1}) / 2 + (s+ - s-) / 4.
+// in a ring of four planes), then computes every face flux once and updates
+// each cell from its six faces.  A cell's state is read ~3.3 times per
+// sub-step (plus four ring planes per chunk), against 11.25 with a 36 x 8 x 5
+// staging per 32 x 4 x 1 tile.  Face fluxes as in k_euler_g2: psi = (G+_j +
+// G-_{j+1}) / 2 + (s+ - s-) / 4; a warp is one tile row, so a lane's left x
+// face is its left neighbour's right face (shuffled), the y faces go through
+// shared memory, and a cell's lower z face is the upper face of the cell
+// below, computed one plane earlier by the same thread.
 template <typename TF>
 struct ZTile {
   static constexpr int TX = 32, TY = 4, SX = TX + 4, SY = TY + 4;
@@ -1138,8 +1142,11 @@ struct ZTile {
   static constexpr int CELLS = TX * TY;  // = threads
   static constexpr int THREADS = CELLS;
   static constexpr int NM = 5;
-  // W of the plane, G+- along x and y of the plane, G+- along z of five planes
-  static constexpr size_t SMEM = sizeof(TF) * ((size_t)NM * NS + 4 * NM * NS + 5 * 2 * NM * CELLS);
+  static constexpr int RING = 4;
+  // W of the plane, G+- along x and y of the plane, G+- along z of four
+  // planes, the y face fluxes of the tile (TY + 1 rows)
+  static constexpr size_t SMEM =
+      sizeof(TF) * ((size_t)NM * NS + 4 * NM * NS + RING * 2 * NM * CELLS + NM * (TY + 1) * TX);
 };
 
 template <typename TF, bool LIMITED>
@@ -1157,7 +1164,8 @@ __global__ void __launch_bounds__(ZTile<TF>::THREADS) k_euler_z(Geom g, DevPtrs 
   __shared__ TF s_amax[3][T::THREADS / 32];
   TF* sw = reinterpret_cast<TF*>(s_raw);  // [NM][NS]
   TF* sg = sw + NM * T::NS;               // [dir x/y][+-][NM][NS]
-  TF* sz = sg + 4 * NM * T::NS;           // [ring 5][+-][NM][CELLS]
+  TF* sz = sg + 4 * NM * T::NS;           // [ring 4][+-][NM][CELLS]
+  TF* sfy = sz + T::RING * 2 * NM * T::CELLS;  // [NM][TY + 1][TX] y faces
   const int Nx = g.nx[0], Ny = g.nx[1], Nz = g.nx[2];
   const long long nc = g.nc, plane = (long long)Nx * Ny;
   const int ntx = (Nx + T::TX - 1) / T::TX, nty = (Ny + T::TY - 1) / T::TY;
@@ -1214,7 +1222,8 @@ __global__ void __launch_bounds__(ZTile<TF>::THREADS) k_euler_z(Geom g, DevPtrs 
     const TF k = s_k;
     const TF al0 = s_al[0], al1 = s_al[1], al2 = s_al[2];
     TF amax[3] = {TF(0), TF(0), TF(0)};
-    // z split fluxes of the tile's cells on plane zz into ring slot zz mod 5
+    // z split fluxes of the tile's cells on plane zz into ring slot zz mod 4
+    auto ring = [&](int zz) { return sz + ((zz + 2 * T::RING) % T::RING) * 2 * NM * T::CELLS; };
     auto ring_plane = [&](int x0, int y0, int zz) {
       const int gx = bc_index(x0 + tx, Nx, g.bc[0]);
       const int gy = bc_index(y0 + ty, Ny, g.bc[1]);
@@ -1224,7 +1233,7 @@ __global__ void __launch_bounds__(ZTile<TF>::THREADS) k_euler_z(Geom g, DevPtrs 
 #pragma unroll
       for (int c = 0; c < NM; ++c) U[c] = __ldcg(src + c * nc + cc);
       euler_flux<TF, 3>(U, 2, F);
-      TF* r = sz + ((zz + 5) % 5) * 2 * NM * T::CELLS;
+      TF* r = ring(zz);
 #pragma unroll
       for (int c = 0; c < NM; ++c) {
         r[c * T::CELLS + tid] = F[c] + al2 * U[c];
@@ -1238,6 +1247,17 @@ __global__ void __launch_bounds__(ZTile<TF>::THREADS) k_euler_z(Geom g, DevPtrs 
       const int z1 = z0 + zc_len < Nz ? z0 + zc_len : Nz;
       if (z0 >= z1) continue;
       for (int zz = z0 - 2; zz < z0 + 2; ++zz) ring_plane(x0, y0, zz);
+      // the face below the first plane (between z0 - 1 and z0); each thread
+      // reads only its own column of the ring
+      TF fzl[NM];
+      {
+        const TF *rm2 = ring(z0 - 2), *rm1 = ring(z0 - 1), *r0 = ring(z0), *r1 = ring(z0 + 1);
+#pragma unroll
+        for (int c = 0; c < NM; ++c) {
+          const int op = c * T::CELLS + tid, om = (NM + c) * T::CELLS + tid;
+          fzl[c] = face6<TF, LIMITED>(rm2[op], rm1[op], r0[op], rm1[om], r0[om], r1[om]);
+        }
+      }
       for (int zc = z0; zc < z1; ++zc) {
         // phase 1: the plane's tile and halo with its x and y split fluxes,
         // and the z split fluxes two planes ahead
@@ -1268,35 +1288,52 @@ __global__ void __launch_bounds__(ZTile<TF>::THREADS) k_euler_z(Geom g, DevPtrs 
         }
         ring_plane(x0, y0, zc + 2);
         __syncthreads();
-        // phase 2: every thread its cell, from its six faces
+        // phase 2: every face flux once.  x: lane tx its right face, the
+        // row's left boundary face from lanes 0..NM-1 (component = lane).
+        // y: every thread its upper face, the tile's lower boundary faces
+        // shared out, all into sfy.  z: the face above the plane.
+        TF fxr[NM], fxl[NM], fyt[NM], fzh[NM];
+        {
+          TF fb = TF(0);
+          if (tx < NM)
+            fb = face_g<TF, LIMITED>(sg + (0 * NM + tx) * T::NS, sg + (1 * NM + tx) * T::NS, ctr - tx - 1, 1);
+#pragma unroll
+          for (int c = 0; c < NM; ++c) {
+            fxr[c] = face_g<TF, LIMITED>(sg + (0 * NM + c) * T::NS, sg + (1 * NM + c) * T::NS, ctr, 1);
+            const TF up = __shfl_up_sync(0xffffffffu, fxr[c], 1);
+            const TF bnd = __shfl_sync(0xffffffffu, fb, c);
+            fxl[c] = tx == 0 ? bnd : up;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < NM; ++c) {
+          fyt[c] = face_g<TF, LIMITED>(sg + (2 * NM + c) * T::NS, sg + (3 * NM + c) * T::NS, ctr, T::SX);
+          sfy[(c * (T::TY + 1) + ty + 1) * T::TX + tx] = fyt[c];
+        }
+        for (int i = tid; i < NM * T::TX; i += T::THREADS) {
+          const int c = i / T::TX, xx = i % T::TX;
+          sfy[(c * (T::TY + 1)) * T::TX + xx] = face_g<TF, LIMITED>(
+              sg + (2 * NM + c) * T::NS, sg + (3 * NM + c) * T::NS, (xx + 2) + T::SX, T::SX);
+        }
+        {
+          const TF *rm1 = ring(zc - 1), *r0 = ring(zc), *r1 = ring(zc + 1), *r2 = ring(zc + 2);
+#pragma unroll
+          for (int c = 0; c < NM; ++c) {
+            const int op = c * T::CELLS + tid, om = (NM + c) * T::CELLS + tid;
+            fzh[c] = face6<TF, LIMITED>(rm1[op], r0[op], r1[op], r0[om], r1[om], r2[om]);
+          }
+        }
+        __syncthreads();
+        // phase 3: every thread its cell, from its six faces
         const int gx = x0 + tx, gy = y0 + ty;
         if (gx < Nx && gy < Ny) {
           const long long cell = gx + (long long)Nx * gy + plane * zc;
-          const TF* r0 = sz + ((zc + 3) % 5) * 2 * NM * T::CELLS;  // zc - 2
-          const TF* r1 = sz + ((zc + 4) % 5) * 2 * NM * T::CELLS;  // zc - 1
-          const TF* r2 = sz + (zc % 5) * 2 * NM * T::CELLS;
-          const TF* r3 = sz + ((zc + 1) % 5) * 2 * NM * T::CELLS;
-          const TF* r4 = sz + ((zc + 2) % 5) * 2 * NM * T::CELLS;
           TF Wn[NM];
 #pragma unroll
           for (int c = 0; c < NM; ++c) {
-            TF acc = TF(0);
-            {
-              const TF* gp = sg + (0 * NM + c) * T::NS;
-              const TF* gm = sg + (1 * NM + c) * T::NS;
-              acc += face_g<TF, LIMITED>(gp, gm, ctr, 1) - face_g<TF, LIMITED>(gp, gm, ctr - 1, 1);
-            }
-            {
-              const TF* gp = sg + (2 * NM + c) * T::NS;
-              const TF* gm = sg + (3 * NM + c) * T::NS;
-              acc += face_g<TF, LIMITED>(gp, gm, ctr, T::SX) - face_g<TF, LIMITED>(gp, gm, ctr - T::SX, T::SX);
-            }
-            {
-              const int op = c * T::CELLS + tid, om = (NM + c) * T::CELLS + tid;
-              const TF hi = face6<TF, LIMITED>(r1[op], r2[op], r3[op], r2[om], r3[om], r4[om]);
-              const TF lo = face6<TF, LIMITED>(r0[op], r1[op], r2[op], r1[om], r2[om], r3[om]);
-              acc += hi - lo;
-            }
+            TF acc = fxr[c] - fxl[c];
+            acc += fyt[c] - sfy[(c * (T::TY + 1) + ty) * T::TX + tx];
+            acc += fzh[c] - fzl[c];
             Wn[c] = sw[c * T::NS + ctr] - k * acc;
             dst[c * nc + cell] = Wn[c];
           }
@@ -1307,6 +1344,8 @@ __global__ void __launch_bounds__(ZTile<TF>::THREADS) k_euler_z(Geom g, DevPtrs 
             for (int d = 0; d < 3; ++d) amax[d] = amax[d] > an[d] ? amax[d] : an[d];
           }
         }
+#pragma unroll
+        for (int c = 0; c < NM; ++c) fzl[c] = fzh[c];
         __syncthreads();
       }
     }

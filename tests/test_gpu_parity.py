@@ -292,10 +292,26 @@ def _wave_3d_tau_field():
     return dataclasses.replace(case, tau=(10.0 ** (-4 + 4 * r)).ravel())
 
 
+def _odd_box_3d():
+    """37 x 6 x 5 periodic box (ragged x tile; N_y and N_z below the 8 velocities per
+    axis, so sources wrap more than once) with an off-centre velocity grid (k from
+    -3, -5, -4) and u = (0.3, -0.2, 0.1)."""
+    nx, dx = (37, 6, 5), 1.0 / 37
+    xs = [(np.arange(n) + 0.5) * dx for n in nx]
+    Z, Y, X = (a.ravel() for a in np.meshgrid(xs[2], xs[1], xs[0], indexing="ij"))
+    L = [n * dx for n in nx]
+    rho = 1 + 0.2 * np.sin(2 * np.pi * X / L[0]) * np.cos(2 * np.pi * Y / L[1]) * np.cos(2 * np.pi * Z / L[2])
+    u = np.stack([np.full_like(X, 0.3), np.full_like(X, -0.2), np.full_like(X, 0.1)])
+    T = 1 + 0.1 * np.sin(2 * np.pi * X / L[0])
+    return W.Case("odd_box_3d", 3, nx, dx, (8, 8, 8), (-3, -5, -4), 1.0, 1, (W.PERIODIC,) * 3, 0.05,
+                  rho, u, T, 3, W.HOFKS)
+
+
 @pytest.mark.parametrize("make", [
     lambda: W.density_wave_3d(n=12, nv=8, tau=0.05, steps=3, dv=1.0),
     _wave_3d_tau_field,
-], ids=["wave_3d_kinetic", "wave_3d_taufield"])
+    _odd_box_3d,
+], ids=["wave_3d_kinetic", "wave_3d_taufield", "odd_box_offset_velocities"])
 def test_windowed_3d_linear_term_moments_match_oracle(make):
     """3D HOFKS on the windowed pass keeps one quadratic per source for the deferred
     and the moment-matching terms together, sums the new value and the Maxwellian
@@ -303,7 +319,8 @@ def test_windowed_3d_linear_term_moments_match_oracle(make):
     per-axis passes over the cells; U_M and U_* follow from these.  Against the FP64
     oracle over 3 steps: moments, U_E, U_M and U_* at 1e-5 of the moment scale, f
     element by element at 1e-5 of max |f|; lambda = 0.19 everywhere, then a tau
-    field with lambda from 0 to 0.88."""
+    field with lambda from 0 to 0.88, then an odd-shaped box with an off-centre
+    velocity grid."""
     case = make()
     orc = oracle.Scheme(grid(case, dvm.HOFKS), tau=case.tau)
     orc.set_moments(conserved(case))
