@@ -1224,14 +1224,15 @@ __global__ void __launch_bounds__(ZTile<TF>::THREADS) k_euler_z(Geom g, DevPtrs 
     TF amax[3] = {TF(0), TF(0), TF(0)};
     // z split fluxes of the tile's cells on plane zz into ring slot zz mod 4
     auto ring = [&](int zz) { return sz + ((zz + 2 * T::RING) % T::RING) * 2 * NM * T::CELLS; };
-    auto ring_plane = [&](int x0, int y0, int zz) {
+    auto ring_cell = [&](int x0, int y0, int zz) {
       const int gx = bc_index(x0 + tx, Nx, g.bc[0]);
       const int gy = bc_index(y0 + ty, Ny, g.bc[1]);
       const int gz = bc_index(zz, Nz, g.bc[2]);
-      const long long cc = gx + (long long)Nx * gy + plane * gz;
-      TF U[NM], F[NM];
-#pragma unroll
-      for (int c = 0; c < NM; ++c) U[c] = __ldcg(src + c * nc + cc);
+      return gx + (long long)Nx * gy + plane * gz;
+    };
+    // from the state U of the thread's cell on plane zz
+    auto ring_store = [&](int zz, const TF* U) {
+      TF F[NM];
       euler_flux<TF, 3>(U, 2, F);
       TF* r = ring(zz);
 #pragma unroll
@@ -1239,6 +1240,36 @@ __global__ void __launch_bounds__(ZTile<TF>::THREADS) k_euler_z(Geom g, DevPtrs 
         r[c * T::CELLS + tid] = F[c] + al2 * U[c];
         r[(NM + c) * T::CELLS + tid] = F[c] - al2 * U[c];
       }
+    };
+    auto ring_plane = [&](int x0, int y0, int zz) {
+      const long long cc = ring_cell(x0, y0, zz);
+      TF U[NM];
+#pragma unroll
+      for (int c = 0; c < NM; ++c) U[c] = __ldcg(src + c * nc + cc);
+      ring_store(zz, U);
+    };
+    // the states phase 1 of plane zz reads (the thread's staged cells i = tid,
+    // tid + 128, tid + 256 and its cell two planes ahead), loaded one plane
+    // early so that their L2 round trip overlaps the previous plane's faces
+    constexpr int KS = (T::NS + T::THREADS - 1) / T::THREADS;
+    TF pre[KS][NM], pre_r[NM];
+    auto prefetch = [&](int x0, int y0, int zz) {
+      const int gz = bc_index(zz, Nz, g.bc[2]);
+#pragma unroll
+      for (int q = 0; q < KS; ++q) {
+        const int i = tid + q * T::THREADS;
+        if (i < T::NS) {
+          const int lx = i % T::SX, ly = i / T::SX;
+          const int gx = bc_index(x0 - 2 + lx, Nx, g.bc[0]);
+          const int gy = bc_index(y0 - 2 + ly, Ny, g.bc[1]);
+          const long long cc = gx + (long long)Nx * gy + plane * gz;
+#pragma unroll
+          for (int c = 0; c < NM; ++c) pre[q][c] = __ldcg(src + c * nc + cc);
+        }
+      }
+      const long long cr = ring_cell(x0, y0, zz + 2);
+#pragma unroll
+      for (int c = 0; c < NM; ++c) pre_r[c] = __ldcg(src + c * nc + cr);
     };
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
       const int txy = item % ntxy, chunk = item / ntxy;
@@ -1258,19 +1289,18 @@ __global__ void __launch_bounds__(ZTile<TF>::THREADS) k_euler_z(Geom g, DevPtrs 
           fzl[c] = face6<TF, LIMITED>(rm2[op], rm1[op], r0[op], rm1[om], r0[om], r1[om]);
         }
       }
+      prefetch(x0, y0, z0);
       for (int zc = z0; zc < z1; ++zc) {
         // phase 1: the plane's tile and halo with its x and y split fluxes,
         // and the z split fluxes two planes ahead
-        const int gz = bc_index(zc, Nz, g.bc[2]);
-        for (int i = tid; i < T::NS; i += T::THREADS) {
-          const int lx = i % T::SX, ly = i / T::SX;
-          const int gx = bc_index(x0 - 2 + lx, Nx, g.bc[0]);
-          const int gy = bc_index(y0 - 2 + ly, Ny, g.bc[1]);
-          const long long cc = gx + (long long)Nx * gy + plane * gz;
+#pragma unroll
+        for (int q = 0; q < KS; ++q) {
+          const int i = tid + q * T::THREADS;
+          if (i >= T::NS) continue;
           TF U[NM], F[NM];
 #pragma unroll
           for (int c = 0; c < NM; ++c) {
-            U[c] = __ldcg(src + c * nc + cc);
+            U[c] = pre[q][c];
             sw[c * T::NS + i] = U[c];
           }
           euler_flux<TF, 3>(U, 0, F);
@@ -1286,7 +1316,8 @@ __global__ void __launch_bounds__(ZTile<TF>::THREADS) k_euler_z(Geom g, DevPtrs 
             sg[(3 * NM + c) * T::NS + i] = F[c] - al1 * U[c];
           }
         }
-        ring_plane(x0, y0, zc + 2);
+        ring_store(zc + 2, pre_r);
+        if (zc + 1 < z1) prefetch(x0, y0, zc + 1);
         __syncthreads();
         // phase 2: every face flux once.  x: lane tx its right face, the
         // row's left boundary face from lanes 0..NM-1 (component = lane).
