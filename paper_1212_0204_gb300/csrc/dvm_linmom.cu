@@ -14,9 +14,10 @@
 // factor over the axes, so B is a sum of box correlations of the five fields
 // mu''_b, each computed as one 1D sum of N_v1 taps per axis (work N_c 3 N_v1
 // per monomial instead of N_c N_v): x-sums of the fields (17 arrays), y-sums
-// of those (32 arrays), then z-sums combined into B (46 terms).  Then U_M = sum_k m_k M_k + B and
-// U_* = sum_k m_k f^{n+1} - U_M; the last velocity split of the partial sums
-// holds (-B, +B), so the end-of-step kernel adds it like any other split.
+// of those (32 arrays), then z-sums combined into B (46 terms).  Then
+// U_M = sum_k m_k M_k + B and U_* = sum_k m_k f^{n+1} - U_M; the last velocity
+// split of the partial sums holds (-B, +B), so the end-of-step kernel adds it
+// like any other split.
 #include <map>
 #include <tuple>
 #include <type_traits>
