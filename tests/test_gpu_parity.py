@@ -282,6 +282,25 @@ def test_3d_bench_velocity_grid_with_velocity_splits_matches_oracle(scheme, tau)
             assert (np.abs(a - b).max(axis=1) / scale).max() <= 1e-5
 
 
+@pytest.mark.parametrize("tau", [1e-4, 0.1], ids=["fluid", "kinetic"])
+def test_3d_bf16_storage_at_the_bench_velocity_grid_is_bounded(tau):
+    """BF16 storage on the 3D pass at the benchmark's velocity grid (16^3 x 24^3,
+    several velocity splits, the single-quadratic form): after 2 steps the moments
+    stay within a few BF16 rounding units (2^-9 relative per store) of the FP64
+    oracle, and f within 4 x 2^-9 of max |f| (a stored value is rounded once per
+    step)."""
+    case = W.density_wave_3d(n=16, nv=24, tau=tau, steps=2, dv=0.5)
+    orc = oracle.Scheme(grid(case, dvm.HOFKS), tau=case.tau)
+    orc.set_moments(conserved(case))
+    orc.step(2)
+    g = gpu_run(case, 2, dvm.BF16S)
+    assert g.kinetic_kernel() == "window"
+    assert g.kinetic_splits() > 1
+    assert moment_err(g.moments(), orc.moments()) <= 8 * 2.0 ** -9
+    fo = orc.f()
+    assert np.abs(g.f() - fo).max() <= 4 * 2.0 ** -9 * np.abs(fo).max()
+
+
 def _wave_3d_tau_field():
     """12^3 x 8^3 density wave with tau = 10^(-4 + 4 r), r = (1 + sin 2pi x cos 2pi y
     cos 2pi z) / 2: lambda = exp(-dt/tau) from 0 to 0.88 across the box."""
