@@ -8,10 +8,32 @@
 // at run time (dvm_kinetic.cu).
 #include <stdlib.h>
 
-#include "dvm_window_kernel.cuh"
+#include "dvm_tile_kernel.cuh"
 
 namespace dvm {
 namespace {
+
+#ifndef DVM_TILE3
+#define DVM_TILE3 1
+#endif
+
+// 3D FP32 HOFKS without the learned path: the kernel with the CTA's source
+// rows folded once into shared memory (dvm_tile_kernel.cuh)
+template <int CX, int CY, int CZ, int CV>
+bool try_tile3(const Geom& g, const DevPtrs& p, int splits, cudaStream_t s, bool prepare) {
+  if (g.nx[0] != CX || g.nx[1] != CY || g.nx[2] != CZ) return false;
+  if (g.nv[0] != CV || g.nv[1] != CV || g.nv[2] != CV) return false;
+  constexpr size_t sm = tile_smem(CV);
+  auto* k = k_kpass_tile3<float, CX, CY, CZ, CV>;
+  if (prepare) {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    return true;
+  }
+  if (g.learn) return false;
+  const dim3 grid((unsigned)(CX / 32), (unsigned)(CY / kTileTY), (unsigned)(CZ * splits));
+  k<<<grid, 32 * kTileW, sm, s>>>(g, p, splits);
+  return true;
+}
 
 template <int D, int CX, int CY, int CZ, int CV, bool LE, typename TS = float>
 bool try_shape(const Geom& g, const DevPtrs& p, int splits, cudaStream_t s, bool prepare) {
@@ -66,6 +88,12 @@ bool launch_window_fixed(const Geom& g, const DevPtrs& p, int splits, cudaStream
            try_shape<2, 512, 512, 1, 32, true>(g, p, splits, s, prepare) ||
            try_shape<2, 128, 128, 1, 32, true>(g, p, splits, s, prepare);
     return hit;
+  }
+  if (DVM_TILE3 && g.d == 3 && g.scheme != DVM_FKS) {
+    // (32^3 x 8^3: the shape its oracle test runs)
+    bool hit = try_tile3<64, 64, 64, 24>(g, p, splits, s, prepare) || try_tile3<96, 96, 96, 24>(g, p, splits, s, prepare) ||
+               try_tile3<32, 32, 32, 24>(g, p, splits, s, prepare) || try_tile3<32, 32, 32, 8>(g, p, splits, s, prepare);
+    if (hit && (prepare ? false : !g.learn)) return true;
   }
   if (g.d == 3 && !g.learn)
     return try_shape<3, 64, 64, 64, 24, false>(g, p, splits, s, prepare) ||

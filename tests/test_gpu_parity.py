@@ -238,8 +238,10 @@ def test_edge_sizes_match_oracle(case, precision, tol):
 ])
 def test_shape_compiled_pass_equals_runtime_pass(make, monkeypatch):
     """The kinetic pass compiled for a configured shape (extents as constants)
-    gives bit-identical moments (and f, in 2D) to the same kernel with run-time
-    extents."""
+    gives bit-identical moments and f (2D) to the same kernel with run-time
+    extents.  In 3D the configured shapes run the CTA-shared-slot kernel, which
+    forms the same values but adds the moment sums in another order (FP32 over
+    the split's pairs): moments within 1e-6 of the moment scale."""
     case = make()
     out = []
     for mode in ("1", "0"):
@@ -249,9 +251,11 @@ def test_shape_compiled_pass_equals_runtime_pass(make, monkeypatch):
         s.step(case.steps)
         out.append((s.moments(), s.f() if case.d == 2 else None))
         s.close()
-    assert np.array_equal(out[0][0], out[1][0])
     if case.d == 2:
+        assert np.array_equal(out[0][0], out[1][0])
         assert np.array_equal(out[0][1], out[1][1])
+    else:
+        assert moment_err(out[0][0], out[1][0]) <= 1e-6
 
 
 @pytest.mark.parametrize("tau", [1e-4, 0.1], ids=["fluid", "kinetic"])
@@ -299,6 +303,34 @@ def test_3d_bf16_storage_at_the_bench_velocity_grid_is_bounded(tau):
     assert moment_err(g.moments(), orc.moments()) <= 8 * 2.0 ** -9
     fo = orc.f()
     assert np.abs(g.f() - fo).max() <= 4 * 2.0 ** -9 * np.abs(fo).max()
+
+
+@pytest.mark.parametrize("tau", [0.05, None], ids=["kinetic", "taufield"])
+def test_3d_shared_slot_kernel_matches_oracle(tau, monkeypatch):
+    """The 3D kinetic pass of the configured shapes (the CTA folds each pair's
+    source rows once into shared memory, four warps stacked in y share them, moment
+    sums in registers) at 32^3 x 8^3 against the FP64 oracle over 3 steps: moments,
+    U_E, U_M, U_* at 1e-5 of the moment scale, f element by element at 1e-5 of
+    max |f|; lambda = 0.54, then a tau field with lambda from 0 to 0.91."""
+    monkeypatch.setenv("DVM_FIXED_SHAPES", "1")
+    case = W.density_wave_3d(n=32, nv=8, tau=0.05 if tau else 1e-2, steps=3, dv=1.0)
+    if tau is None:
+        xc = (np.arange(32) + 0.5) / 32
+        Z, Y, X = np.meshgrid(xc, xc, xc, indexing="ij")
+        r = 0.5 * (1 + np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y) * np.cos(2 * np.pi * Z))
+        case = dataclasses.replace(case, tau=(10.0 ** (-4 + 4 * r)).ravel() * 0.375)
+    orc = oracle.Scheme(grid(case, dvm.HOFKS), tau=case.tau)
+    orc.set_moments(conserved(case))
+    orc.step(3)
+    g = gpu_run(case, 3, dvm.F32)
+    assert g.kinetic_kernel() == "window"
+    Uo = orc.moments()
+    assert moment_err(g.moments(), Uo) <= 1e-5
+    fo = orc.f()
+    assert np.abs(g.f() - fo).max() <= 1e-5 * np.abs(fo).max()
+    scale = np.maximum(np.abs(Uo).max(axis=1), np.abs(Uo[0]).max())
+    for a, b in zip(g.parts(), orc.parts()):
+        assert (np.abs(a - b).max(axis=1) / scale).max() <= 1e-5
 
 
 def _wave_3d_tau_field():
@@ -357,10 +389,11 @@ def test_windowed_3d_linear_term_moments_match_oracle(make):
 
 @pytest.mark.parametrize("n", [64, 96])
 def test_3d_shape_compiled_pass_equals_runtime_pass_at_bench_sizes(n, monkeypatch):
-    """The 3D kinetic pass compiled for the 64^3 and 96^3 x 24^3 shapes (the kernels
-    behind the 3D benchmark lines) gives moments bit-identical to the kernel with
-    run-time extents over 2 steps; f itself is compared through the moments (at
-    96^3 it is 49 GB)."""
+    """The 3D kinetic pass compiled for the 64^3 and 96^3 x 24^3 shapes (the
+    CTA-shared-slot kernel behind the 3D benchmark lines) agrees with the per-thread
+    window kernel with run-time extents over 2 steps: moments, U_E, U_M and U_*
+    within 1e-6 of the moment scale (the same values, moment sums added in another
+    order); f itself is compared through the moments (at 96^3 it is 49 GB)."""
     case = W.density_wave_3d(n=n, nv=24, tau=1e-4, steps=2, dv=0.5)
     out = []
     for mode in ("1", "0"):
@@ -371,9 +404,11 @@ def test_3d_shape_compiled_pass_equals_runtime_pass_at_bench_sizes(n, monkeypatc
         out.append((s.moments(), s.parts()))
         s.close()
         del s
-    assert np.array_equal(out[0][0], out[1][0])
+    U = out[1][0]
+    scale = np.maximum(np.abs(U).max(axis=1), np.abs(U[0]).max())
+    assert moment_err(out[0][0], U) <= 1e-6
     for a, b in zip(out[0][1], out[1][1]):
-        assert np.array_equal(a, b)
+        assert (np.abs(a - b).max(axis=1) / scale).max() <= 1e-6
 
 
 @pytest.mark.parametrize("n", [9, 21])
