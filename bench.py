@@ -107,7 +107,7 @@ def load_peaks():
 def kinetic_source_hash() -> str:
     h = hashlib.sha256()
     for f in ("dvm_kinetic.cu", "dvm_kinetic_shapes.cu", "dvm_window_kernel.cuh", "dvm_window.cuh",
-              "dvm_internal.cuh", "dvm_linmom.cu"):
+              "dvm_internal.cuh", "dvm_linmom.cu", "dvm_tile_kernel.cuh"):
         with open(os.path.join(ROOT, "paper_1212_0204_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -46,6 +46,13 @@ def test_recorded_traffic_only_for_the_current_kernel_source(monkeypatch, tmp_pa
 def test_kinetic_source_hash_covers_the_kernel_sources():
     h = bench.kinetic_source_hash()
     assert len(h) == 16 and int(h, 16) >= 0
+    # every source of the kinetic-pass kernels enters the key
+    import inspect
+    src = inspect.getsource(bench.kinetic_source_hash)
+    csrc = os.path.join(os.path.dirname(bench.__file__), "paper_1212_0204_gb300", "csrc")
+    for f in ("dvm_kinetic.cu", "dvm_kinetic_shapes.cu", "dvm_window_kernel.cuh", "dvm_window.cuh",
+              "dvm_tile_kernel.cuh", "dvm_linmom.cu"):
+        assert os.path.exists(os.path.join(csrc, f)) and f in src
 
 
 def test_oracle_sample_is_bounded_and_keeps_the_velocity_grid():
