@@ -1,21 +1,20 @@
-// dvm_kinetic_shapes.cu -- the windowed kinetic pass compiled with the grid
-// extents and velocity counts of the configured workloads fixed at compile
-// time (2D 128^2, 256^2, 512^2 x 32^2; 3D 32^3, 64^3, 96^3 x 24^3): the index
-// and address arithmetic of the pass then works on constants (on GB300 about
-// a quarter of its instructions).  FP32 storage, HOFKS (2D also with the
-// learned path), and BF16 storage for the 2D 256^2 / 512^2 and 3D 64^3 / 96^3
-// shapes; every other configuration runs the same kernel with the extents read
-// at run time (dvm_kinetic.cu).
+// dvm_kinetic_shapes.cu -- the kinetic pass compiled with the grid extents
+// and velocity counts of the configured workloads fixed at compile time (2D
+// 128^2, 256^2, 512^2 x 32^2; 3D 32^3, 64^3, 96^3 x 24^3): the index and
+// address arithmetic then works on constants (on GB300 about a quarter of the
+// per-thread window kernel's instructions).  2D FP32 HOFKS (also with the
+// learned path) and BF16 storage (2D 256^2 / 512^2, 3D 64^3 / 96^3) run the
+// per-thread window kernel (dvm_window_kernel.cuh); 3D FP32 HOFKS runs the
+// kernel whose CTA shares each pair's folded source rows (dvm_tile_kernel.cuh;
+// also at 32^3 x 8^3, the shape of its oracle test).  Every other
+// configuration runs the window kernel with the extents read at run time
+// (dvm_kinetic.cu).
 #include <stdlib.h>
 
 #include "dvm_tile_kernel.cuh"
 
 namespace dvm {
 namespace {
-
-#ifndef DVM_TILE3
-#define DVM_TILE3 1
-#endif
 
 // 3D FP32 HOFKS without the learned path: the kernel with the CTA's source
 // rows folded once into shared memory (dvm_tile_kernel.cuh)
@@ -89,16 +88,9 @@ bool launch_window_fixed(const Geom& g, const DevPtrs& p, int splits, cudaStream
            try_shape<2, 128, 128, 1, 32, true>(g, p, splits, s, prepare);
     return hit;
   }
-  if (DVM_TILE3 && g.d == 3 && g.scheme != DVM_FKS) {
-    // (32^3 x 8^3: the shape its oracle test runs)
-    bool hit = try_tile3<64, 64, 64, 24>(g, p, splits, s, prepare) || try_tile3<96, 96, 96, 24>(g, p, splits, s, prepare) ||
-               try_tile3<32, 32, 32, 24>(g, p, splits, s, prepare) || try_tile3<32, 32, 32, 8>(g, p, splits, s, prepare);
-    if (hit && (prepare ? false : !g.learn)) return true;
-  }
-  if (g.d == 3 && !g.learn)
-    return try_shape<3, 64, 64, 64, 24, false>(g, p, splits, s, prepare) ||
-           try_shape<3, 96, 96, 96, 24, false>(g, p, splits, s, prepare) ||
-           try_shape<3, 32, 32, 32, 24, false>(g, p, splits, s, prepare);
+  if (g.d == 3)  // (without the learned path: try_tile3 declines it)
+    return try_tile3<64, 64, 64, 24>(g, p, splits, s, prepare) || try_tile3<96, 96, 96, 24>(g, p, splits, s, prepare) ||
+           try_tile3<32, 32, 32, 24>(g, p, splits, s, prepare) || try_tile3<32, 32, 32, 8>(g, p, splits, s, prepare);
   return false;
 }
 
