@@ -174,6 +174,8 @@ int launch_kinetic_pass(const Geom& g, const DevPtrs& p, cudaStream_t s);  // ke
 // launches it (or, with prepare, sets its attributes) and returns true if g is
 // one of them (FP32, HOFKS; in 3D without the learned path)
 bool launch_window_fixed(const Geom& g, const DevPtrs& p, int splits, cudaStream_t s, bool prepare);
+// 3D FP32 HOFKS at a shape the tile kernel is compiled for (dvm_kinetic_shapes.cu)
+bool tile3_shape(const Geom& g);
 void kinetic_pass_prepare(const Geom& g);
 int kinetic_pass_splits(const Geom& g);
 bool kinetic_is_windowed(const Geom& g);

@@ -8,6 +8,8 @@
 //   * writes the new value back into the same piece (in place).
 // One read and one write of f per phase-space point.
 #include <math.h>
+
+#include <cmath>
 #include <stdlib.h>
 
 #include "dvm_internal.cuh"
@@ -296,6 +298,27 @@ int sm_count() {
 // ceil(tiles c / R) / c with R the resident CTAs, so that the last wave is
 // nearly full; ties go to the larger c (finer load balance).
 WinLaunch window_shape(const Geom& g) {
+  if (tile3_shape(g)) {
+    // the 3D tile kernel (32 x 16 targets per CTA, 3 CTAs per SM): its larger
+    // tiles make the last wave's fill matter more, and each split adds a pass
+    // of FP64 partial sums (written here, read by the end-of-step kernel,
+    // 160 B per cell against 8 N_v of f); the divisor c of N_v1 (<= 12) with
+    // the smallest ceil(waves) / waves x (1 + 20 c / N_v) (96^3: 6, 64^3: 8)
+    const long long tiles = (long long)(g.nx[0] / 32) * (g.nx[1] / 16) * g.nx[2];
+    const double resident = (double)sm_count() * 3;
+    int sp = 1;
+    double best = 1e30;
+    for (int c = 1; c <= 12 && c <= g.nv[2]; ++c) {
+      if (g.nv[2] % c || (c > 1 && 512LL * g.nvel / c < (1LL << 16))) continue;
+      const double waves = (double)(tiles * c) / resident;
+      const double cost = std::ceil(waves) / waves * (1.0 + 20.0 * c / (double)g.nvel);
+      if (cost < best) { best = cost; sp = c; }
+    }
+    WinLaunch wl;
+    wl.S = win_warps(g.d);
+    wl.splits = sp;
+    return wl;
+  }
   const int Y = win_y(g.d);
   const long long tiles = ((g.nx[0] + 31) / 32) * ((g.nx[1] + Y - 1) / Y) * g.nx[2];
   const long long resident = (long long)sm_count() * (g.d == 3 ? WinShape<3>::MINB : WinShape<2>::MINB);

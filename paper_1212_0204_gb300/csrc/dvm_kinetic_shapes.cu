@@ -59,6 +59,14 @@ bool try_shape(const Geom& g, const DevPtrs& p, int splits, cudaStream_t s, bool
 
 }  // namespace
 
+// 3D FP32 HOFKS at a shape with a tile kernel (the splits are chosen for it)
+bool tile3_shape(const Geom& g) {
+  if (g.d != 3 || g.precision != DVM_F32 || g.scheme == DVM_FKS) return false;
+  if (g.nx[0] != g.nx[1] || g.nx[1] != g.nx[2] || g.nv[0] != g.nv[1] || g.nv[1] != g.nv[2]) return false;
+  const int n = g.nx[0], v = g.nv[0];
+  return (v == 24 && (n == 32 || n == 64 || n == 96)) || (v == 8 && n == 32);
+}
+
 // DVM_FIXED_SHAPES=0 runs the runtime-extent kernel for every shape (for
 // comparison runs and the test that both give the same result).
 bool launch_window_fixed(const Geom& g, const DevPtrs& p, int splits, cudaStream_t s, bool prepare) {
