@@ -210,7 +210,8 @@ int dvm_launches_per_step(dvm_handle* h, int* launches);
 /* Which kinetic-pass kernel the handle's steps run (chosen at dvm_create
  * from the grid, precision and boundaries): DVM_KPASS_GENERIC (one thread
  * per cell, any configuration) or DVM_KPASS_WINDOW (FP32/BF16 storage,
- * periodic 2D/3D, p = 1: per-thread windows of source rows). */
+ * periodic 2D/3D, p = 1: windows of source rows that slide along the
+ * velocity; at the configured 3D FP32 shapes the CTA shares them). */
 enum { DVM_KPASS_GENERIC = 0, DVM_KPASS_WINDOW = 1 };
 int dvm_kinetic_kernel(const dvm_handle* h, int* kind);
 
@@ -219,6 +220,15 @@ int dvm_kinetic_kernel(const dvm_handle* h, int* kind);
  * many CTAs, each writing its own FP64 partial moment sums, which the
  * end-of-step kernel adds (Eq. DM summed in parts).  1 = no split. */
 int dvm_kinetic_splits(const dvm_handle* h, int* splits);
+
+/* The kinetic-pass plan dvm_create would choose for cfg, without creating
+ * anything or touching a GPU: the kernel kind (as dvm_kinetic_kernel) and
+ * its velocity chunks (as dvm_kinetic_splits), for the SM count of the
+ * current device, or 152 SMs (GB300) when no device is visible.  The split
+ * count follows the fill of the last wave of CTAs (Section 4.2's pass over
+ * the velocities, summed in parts).  Host only; DVM_ERR_ARG for an invalid
+ * configuration or a NULL output. */
+int dvm_plan(const dvm_config* cfg, int* kind, int* splits);
 
 /* Kinetic-pass timing.  Between dvm_profile_begin and dvm_profile_end the
  * steps are enqueued launch by launch (not through the graph) with a pair of

@@ -463,6 +463,17 @@ int dvm_workspace_bytes(const dvm_config* cfg, size_t* bytes) {
   return 0;
 }
 
+int dvm_plan(const dvm_config* cfg, int* kind, int* splits) {
+  Geom g;
+  std::string msg;
+  const int rc = make_geom(cfg, &g, &msg);
+  if (rc) return rc;
+  if (!kind || !splits) return DVM_ERR_ARG;
+  *kind = kinetic_is_windowed(g) ? DVM_KPASS_WINDOW : DVM_KPASS_GENERIC;
+  *splits = g.nsplit - g.lin_slice;
+  return 0;
+}
+
 int dvm_create(const dvm_config* cfg, void* workspace, void* cuda_stream, dvm_handle** out) {
   if (!out) return DVM_ERR_ARG;
   *out = nullptr;

@@ -29,7 +29,7 @@ EXPORTS = [
     "dvm_workspace_bytes", "dvm_create", "dvm_destroy", "dvm_set_stream", "dvm_last_error",
     "dvm_set_state_moments", "dvm_set_state_primitive", "dvm_step", "dvm_step_async",
     "dvm_sync_status", "dvm_moments", "dvm_moments_async", "dvm_moments_wait", "dvm_get_f", "dvm_last_parts", "dvm_info", "dvm_offsets",
-    "dvm_save", "dvm_load", "dvm_launches_per_step", "dvm_kinetic_kernel", "dvm_kinetic_splits", "dvm_profile_begin",
+    "dvm_save", "dvm_load", "dvm_launches_per_step", "dvm_kinetic_kernel", "dvm_kinetic_splits", "dvm_plan", "dvm_profile_begin",
     "dvm_profile_end",
     "dvm_equilibrium_noalloc", "dvm_selftest_timeout",
     "dvm_batch_create", "dvm_batch_destroy", "dvm_batch_last_error", "dvm_batch_sizes",
@@ -128,6 +128,7 @@ def lib():
         L.dvm_launches_per_step.argtypes = [vp, C.POINTER(C.c_int)]
         L.dvm_kinetic_kernel.argtypes = [vp, C.POINTER(C.c_int)]
         L.dvm_kinetic_splits.argtypes = [vp, C.POINTER(C.c_int)]
+        L.dvm_plan.argtypes = [C.POINTER(_Config), C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.dvm_profile_begin.argtypes = [vp]
         L.dvm_profile_end.argtypes = [vp, dp, C.POINTER(C.c_int)]
         L.dvm_equilibrium_noalloc.argtypes = [C.POINTER(_Config), vp, vp, vp]
@@ -234,6 +235,16 @@ def selftest_timeout(which: int, stream=None) -> int:
     if rc:
         raise DvmError(rc, "selftest launch failed")
     return st.value
+
+
+def plan(cfg) -> tuple:
+    """(kinetic-pass kernel "window"/"generic", velocity splits) that dvm_create would
+    choose for cfg; host only (no GPU needed)."""
+    kind, splits = C.c_int(), C.c_int()
+    rc = lib().dvm_plan(C.byref(cfg), C.byref(kind), C.byref(splits))
+    if rc:
+        raise DvmError(rc, "invalid configuration")
+    return ("generic", "window")[kind.value], splits.value
 
 
 def workspace_bytes(cfg) -> int:

@@ -88,3 +88,48 @@ def test_header_is_c99_and_a_c_program_links_and_calls_the_library(libdvm, tmp_p
     bad = {k: v[0] for k, v in rows.items() if k.startswith("bad_")}
     assert len(bad) == 13 and all(v == -1 for v in bad.values()), bad
     assert rows["max_velocities"][0] == 0
+
+
+def test_launch_plan_without_a_gpu(libdvm):
+    """dvm_plan reports the kinetic-pass kernel and its velocity splits host-side, for
+    152 SMs when no device is visible.  The configured 3D FP32 shapes (the
+    CTA-shared-slot kernel, 32 x 16 targets per CTA, 3 CTAs per SM) take the divisor
+    c <= 12 of N_v1 with the smallest ceil(w) / w (1 + 20 c / N_v), w = CTA waves: the
+    last wave nearly full at little partial-sum traffic; other windowed shapes keep
+    c <= 4; the FP64 tier runs the generic pass."""
+    import math
+
+    from paper_1212_0204_gb300 import dvm, workloads as W
+
+    def plan(case, prec):
+        cfg, keep = dvm.config_from_case(case, precision=prec)
+        return dvm.plan(cfg)
+
+    def tile_choice(n, v):
+        tiles, resident, nvel = (n // 32) * (n // 16) * n, 152 * 3, v ** 3
+        best = None
+        for c in range(1, 13):
+            if v % c or (c > 1 and 512 * nvel // c < 65536):
+                continue
+            w = tiles * c / resident
+            cost = math.ceil(w) / w * (1 + 20 * c / nvel)
+            if best is None or cost < best[0]:
+                best = (cost, c)
+        return best[1]
+
+    for n in (96, 64):
+        kind, sp = plan(W.density_wave_3d(n=n, nv=24, tau=1e-4, steps=1), dvm.F32)
+        assert kind == "window" and sp == tile_choice(n, 24) and 24 % sp == 0
+    assert plan(W.density_wave_3d(n=96, nv=24, tau=1e-4, steps=1), dvm.F32)[1] == 6
+    assert plan(W.density_wave_3d(n=64, nv=24, tau=1e-4, steps=1), dvm.F32)[1] == 8
+    # BF16 storage and unconfigured shapes: the per-thread window kernel's rule (c <= 4)
+    kind, sp = plan(W.density_wave_3d(n=16, nv=24, tau=1e-4, steps=1), dvm.BF16S)
+    assert kind == "window" and 1 <= sp <= 4 and 24 % sp == 0
+    assert plan(W.quadrant_2d(n=256, nv=32, tau=1e-3, steps=1), dvm.F32) == ("window", 2)
+    assert plan(W.quadrant_2d(n=256, nv=32, tau=1e-3, steps=1), dvm.F64)[0] == "generic"
+    assert plan(W.sod_1d(nx=200, nv=32, tau=1e-4), dvm.F32)[0] == "generic"
+    with pytest.raises(dvm.DvmError):
+        bad = W.sod_1d(nx=200, nv=32, tau=1e-4)
+        cfg, keep = dvm.config_from_case(bad, precision=dvm.F32)
+        cfg.grid.nx[0] = 0
+        dvm.plan(cfg)
